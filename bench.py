@@ -1,0 +1,423 @@
+"""Benchmark of the UPIR region runtime on B300.
+
+Headline workload: the 2D Jacobi 5-point region, a 4096 x 4096 FP32 grid
+(top edge 1, other edges 0, interior uniform[0,1) from seed 1), 100 sweeps, a
+per-sweep reduction(max) of |u_new - u| into its own variable, ping-pong
+buffers mapped once.  One step = one submission of that 100-loop region.
+Metric: parallel-loop HBM GB/s (algorithmic bytes: 8 B per interior point per
+sweep) against the measured HBM copy peak.  The other loop regions (AXPY with
+reductions, matvec, GEMM, batched regions) are measured after the headline
+and reported under "extra".
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank runs its own independent problem (weak scaling, no
+data-path collective); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import upir_inputs as I  # noqa: E402
+from paper_2209_10643_b300.sharding import aggregate_throughput, dist_env  # noqa: E402
+
+N_GRID = 4096
+SWEEPS = 100
+JACOBI_BYTES_PER_SWEEP = 8 * (N_GRID - 2) ** 2
+L2_FLUSH_BYTES = 256 << 20
+
+
+def peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "bf16_tflops": float(d["bf16_tflops"]),
+                "bf16_tflops_sustained": float(d.get("bf16_tflops_sustained", d["bf16_tflops"])),
+                "source": "measured"}
+    return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0, "source": "fallback"}
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples while the timed region runs."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "50"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.proc:
+            time.sleep(0.2)
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self) -> dict:
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (getattr(self, "out", "") or "").splitlines():
+            f = [v.strip() for v in line.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[3:7]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --------------------------------------------------------------------- ours --
+
+class Runtime:
+    def __init__(self, device: int):
+        import torch
+        import paper_2209_10643_b300 as U
+        self.U, self.torch = U, torch
+        torch.cuda.set_device(device)
+        # enqueue on torch's current stream so torch events bracket the launches
+        self.ctx = U.upir_init(device, torch.cuda.current_stream().cuda_stream)
+        self.flush_buf = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+        self.host = []
+
+    def map(self, arr, kind):
+        self.host.append(arr)
+        return self.U.upir_data_map(self.ctx, arr.ctypes.data, arr.nbytes, kind)
+
+    def flush_l2(self):
+        self.flush_buf.fill_(1.0)
+        self.torch.cuda.synchronize()
+
+    def region(self, loops, teams=0, units=0):
+        r = self.U.upir_spmd_region(self.ctx, teams, units)
+        for lp in loops:
+            self.U.upir_loop_checked(self.ctx, r, self.U.make_loop_desc(**lp))
+        return r
+
+    def timed_submits(self, submit, reps, warmup=3, flush=True):
+        """Median per-rep device time (ms) of ``submit()``, measured with the
+        library's per-launch CUDA events; also the per-launch records."""
+        U = self.U
+        for _ in range(warmup):
+            submit()
+        U.upir_ctx_wait(self.ctx)
+        U.upir_ctx_timings(self.ctx)
+        per_rep = []
+        launches = []
+        for _ in range(reps):
+            if flush:
+                self.flush_l2()
+            U.upir_ctx_set_timing(self.ctx, True)
+            submit()
+            U.upir_ctx_set_timing(self.ctx, False)
+            rec = U.upir_ctx_timings(self.ctx)
+            per_rep.append(sum(ms for _, ms in rec))
+            launches.extend(rec)
+        return statistics.median(per_rep), per_rep, launches
+
+
+def jacobi_region_loops(U, ha, hb, hr):
+    loops = []
+    for k in range(SWEEPS):
+        src, dst = (ha, hb) if k % 2 == 0 else (hb, ha)
+        loops.append(dict(lb=1, ub=N_GRID - 1, step=1, collapse=2, body=U.UPIR_BODY_JACOBI5,
+                          bufs=[src, dst], scalars=[N_GRID, N_GRID],
+                          reductions=[(U.UPIR_RED_MAX, U.UPIR_F32, U.UPIR_TERM_RESID, hr, k)]))
+    return loops
+
+
+def headline(rt: Runtime, steps: int, warmup: int, pk: dict, device: int):
+    U, torch = rt.U, rt.torch
+    u0 = I.jacobi_grid(N_GRID, seed=1)
+    a, b = u0.copy(), u0.copy()
+    res = np.full(SWEEPS, -np.inf, np.float32)
+    ha, hb = rt.map(a, U.UPIR_MAP_TOFROM), rt.map(b, U.UPIR_MAP_TOFROM)
+    hr = rt.map(res, U.UPIR_MAP_TOFROM)
+    r = rt.region(jacobi_region_loops(U, ha, hb, hr))
+    for _ in range(warmup):
+        U.upir_region_submit(r, 0)
+    U.upir_ctx_wait(rt.ctx)
+    U.upir_ctx_timings(rt.ctx)
+
+    import torch.distributed as dist
+    if dist.is_initialized():
+        dist.barrier()
+    torch.cuda.synchronize()
+    step_ms, kernel_ms = [], []
+    with ClockSampler(device) as clk:
+        for _ in range(steps):
+            rt.flush_l2()
+            U.upir_ctx_set_timing(rt.ctx, True)
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            ev0.record()
+            U.upir_region_submit(r, 0)
+            ev1.record()
+            U.upir_ctx_set_timing(rt.ctx, False)
+            rec = U.upir_ctx_timings(rt.ctx)  # waits for the stream
+            kernel_ms.extend(ms for _, ms in rec)
+            step_ms.append(ev0.elapsed_time(ev1))
+        torch.cuda.synchronize()
+    if dist.is_initialized():
+        dist.barrier()
+    total_s = sum(step_ms) / 1e3
+    units, secs = aggregate_throughput(steps * SWEEPS * JACOBI_BYTES_PER_SWEEP, total_s)
+    value = units / secs / 1e9
+    avg_kernel_s = statistics.mean(kernel_ms) / 1e3
+    achieved = JACOBI_BYTES_PER_SWEEP / avg_kernel_s / 1e9
+
+    # graph submission of the same region (CUDA graph of the 100 launches)
+    gms, _, _ = rt.timed_submits(lambda: U.upir_region_submit(r, U.UPIR_SUBMIT_GRAPH), steps, warmup)
+    U.upir_region_destroy(r)
+    for h in (ha, hb, hr):
+        U.upir_data_unmap(rt.ctx, h)
+
+    # end to end through the public API with host buffers (pinned)
+    e2e = jacobi_e2e(rt, u0, max(3, min(steps, 5)))
+    return {
+        "value": value, "ms_per_step": statistics.mean(step_ms), "clocks": clk.summary(),
+        "gpu_launches": steps * SWEEPS,
+        "roofline": {"bound": "hbm", "kernel": "jacobi_tma_kernel", "achieved": achieved,
+                     "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": achieved / pk["hbm_gbs"],
+                     "peak_source": pk["source"] + " (burst copy)",
+                     "algorithmic_bytes_per_launch": JACOBI_BYTES_PER_SWEEP,
+                     "avg_launch_us": avg_kernel_s * 1e6, "traffic": None},
+        "graph_ms_per_step": gms, "graph_value": SWEEPS * JACOBI_BYTES_PER_SWEEP / (gms / 1e3) / 1e9,
+        "e2e": e2e, "residual_last": float(res[-1]),
+    }
+
+
+def jacobi_e2e(rt: Runtime, u0: np.ndarray, steps: int) -> dict:
+    U, torch = rt.U, rt.torch
+    pa = torch.empty(u0.shape, dtype=torch.float32, pin_memory=True).numpy()
+    pb = torch.empty(u0.shape, dtype=torch.float32, pin_memory=True).numpy()
+    pr = torch.empty(SWEEPS, dtype=torch.float32, pin_memory=True).numpy()
+    times = []
+    for i in range(steps + 1):
+        pa[...] = u0
+        pb[...] = u0
+        pr[...] = -np.inf
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ha = U.upir_data_map(rt.ctx, pa.ctypes.data, pa.nbytes, U.UPIR_MAP_TOFROM)
+        hb = U.upir_data_map(rt.ctx, pb.ctypes.data, pb.nbytes, U.UPIR_MAP_TO)
+        # the residual variables start at -inf, so they are mapped tofrom
+        hr = U.upir_data_map(rt.ctx, pr.ctypes.data, pr.nbytes, U.UPIR_MAP_TOFROM)
+        r = rt.region(jacobi_region_loops(U, ha, hb, hr))
+        U.upir_region_submit(r, 0)
+        U.upir_region_destroy(r)
+        U.upir_data_unmap(rt.ctx, hb)
+        U.upir_data_unmap(rt.ctx, hr)
+        U.upir_data_unmap(rt.ctx, ha)
+        t1 = time.perf_counter()
+        if i:
+            times.append(t1 - t0)
+    t = statistics.median(times)
+    return {"value": SWEEPS * JACOBI_BYTES_PER_SWEEP / t / 1e9, "unit": "GB/s",
+            "h2d_bytes_per_step": 2 * u0.nbytes + SWEEPS * 4, "d2h_bytes_per_step": u0.nbytes + SWEEPS * 4,
+            "ms_per_step": t * 1e3}
+
+
+def extra_axpy(rt: Runtime, n: int, pk: dict) -> dict:
+    U = rt.U
+    x, y = I.axpy_inputs(n, seed=0)
+    fs = np.zeros(1, np.float32)
+    si = np.zeros(1, np.int64)
+    hx, hy = rt.map(x, U.UPIR_MAP_TO), rt.map(y, U.UPIR_MAP_TOFROM)
+    hf, hi = rt.map(fs, U.UPIR_MAP_TOFROM), rt.map(si, U.UPIR_MAP_TOFROM)
+    r = rt.region([dict(lb=0, ub=n, body=U.UPIR_BODY_AXPY, bufs=[hx, hy], scalars=[2.5, 3, 1000],
+                        reductions=[(U.UPIR_RED_ADD, U.UPIR_F32, U.UPIR_TERM_Y, hf, 0),
+                                    (U.UPIR_RED_ADD, U.UPIR_I64, U.UPIR_TERM_IMOD, hi, 0)])])
+    ms, _, _ = rt.timed_submits(lambda: U.upir_region_submit(r, 0), 20)
+    gms, _, _ = rt.timed_submits(lambda: U.upir_region_submit(r, U.UPIR_SUBMIT_GRAPH), 20)
+    U.upir_region_destroy(r)
+    for h in (hx, hy, hf, hi):
+        U.upir_data_unmap(rt.ctx, h)
+    gbs = 12 * n / (ms / 1e3) / 1e9
+    return {"n": n, "us": ms * 1e3, "GB/s": gbs, "frac_hbm": gbs / pk["hbm_gbs"],
+            "graph_us": gms * 1e3, "bytes": 12 * n}
+
+
+def extra_matvec(rt: Runtime, pk: dict) -> dict:
+    U = rt.U
+    n = 16384
+    a, x = I.matvec_inputs(n, n)
+    y = np.zeros(n, np.float32)
+    ha, hx, hy = rt.map(a, U.UPIR_MAP_TO), rt.map(x, U.UPIR_MAP_TO), rt.map(y, U.UPIR_MAP_TOFROM)
+    r = rt.region([dict(lb=0, ub=n, body=U.UPIR_BODY_MATVEC, bufs=[ha, hx, hy], scalars=[n, n])])
+    ms, _, _ = rt.timed_submits(lambda: U.upir_region_submit(r, 0), 10)
+    U.upir_region_destroy(r)
+    for h in (ha, hx, hy):
+        U.upir_data_unmap(rt.ctx, h)
+    rt.host.clear()
+    byts = 4 * n * n + 8 * n
+    gbs = byts / (ms / 1e3) / 1e9
+    return {"rows": n, "cols": n, "us": ms * 1e3, "GB/s": gbs, "frac_hbm": gbs / pk["hbm_gbs"]}
+
+
+def extra_gemm_f32(rt: Runtime) -> dict:
+    import torch
+    U = rt.U
+    m = n = k = 4096
+    a, b = I.gemm_inputs(m, n, k)
+    c = np.zeros((m, n), np.float32)
+    ha, hb, hc = rt.map(a, U.UPIR_MAP_TO), rt.map(b, U.UPIR_MAP_TO), rt.map(c, U.UPIR_MAP_TOFROM)
+    r = rt.region([dict(lb=0, ub=m, collapse=2, body=U.UPIR_BODY_GEMM_F32, bufs=[ha, hb, hc],
+                        scalars=[m, n, k])])
+    ms, _, _ = rt.timed_submits(lambda: U.upir_region_submit(r, 0), 5)
+    U.upir_region_destroy(r)
+    for h in (ha, hb, hc):
+        U.upir_data_unmap(rt.ctx, h)
+    rt.host.clear()
+    props = torch.cuda.get_device_properties(0)
+    fp32_peak = props.multi_processor_count * 128 * 2 * 2.032e9 / 1e12
+    tf = 2 * m * n * k / (ms / 1e3) / 1e12
+    return {"shape": [m, n, k], "ms": ms, "TFLOP/s": tf, "fp32_simt_peak_tflops": fp32_peak,
+            "frac_fp32_peak": tf / fp32_peak}
+
+
+def cpu_baseline_jacobi(budget_s: float = 12.0) -> dict:
+    """The oracle (FP64 numpy, single thread) on a bounded sample of the
+    headline workload: the full 4096^2 grid for as many sweeps as fit the budget."""
+    from oracle import upir_oracle as O
+    u0 = I.jacobi_grid(N_GRID, seed=1)
+    t0 = time.perf_counter()
+    O.jacobi_run(u0, 1)
+    one = time.perf_counter() - t0
+    sweeps = max(1, min(SWEEPS, int(budget_s / max(one, 1e-3))))
+    t0 = time.perf_counter()
+    O.jacobi_run(u0, sweeps)
+    dt = time.perf_counter() - t0
+    return {"value": sweeps * JACOBI_BYTES_PER_SWEEP / dt / 1e9, "unit": "GB/s", "cores": 1,
+            "kind": "oracle", "sample": f"{sweeps} of {SWEEPS} sweeps on the {N_GRID}x{N_GRID} grid, FP64 numpy",
+            "seconds": dt, "host_cores_available": os.cpu_count()}
+
+
+def run_ours(args) -> None:
+    rank, local_rank, world = dist_env()
+    import torch
+    import torch.distributed as dist
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    pk = peaks()
+    rt = Runtime(local_rank)
+    h = headline(rt, args.steps, args.warmup, pk, local_rank)
+    extra = {}
+    if rank == 0 and not args.no_extra:
+        for name, fn in (("axpy_2^20", lambda: extra_axpy(rt, 1 << 20, pk)),
+                         ("axpy_2^28", lambda: extra_axpy(rt, 1 << 28, pk)),
+                         ("matvec_16384", lambda: extra_matvec(rt, pk)),
+                         ("gemm_f32_4096", lambda: extra_gemm_f32(rt))):
+            try:
+                extra[name] = fn()
+            except Exception as e:  # report, keep the headline
+                extra[name] = {"error": repr(e)}
+            rt.host.clear()
+    cpu = cpu_baseline_jacobi() if (rank == 0 and world == 1 and not args.no_cpu) else None
+    if rank == 0:
+        line = {
+            "metric": "Parallel-loop HBM GB/s vs peak; batched regions/s fused vs per-region launch",
+            "value": round(h["value"], 2), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(h["ms_per_step"], 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "jacobi5_4096x4096_100sweeps_maxresidual",
+                       "grid": [N_GRID, N_GRID], "sweeps": SWEEPS, "schedule": "static",
+                       "parallelism": f"independent problem per rank x{world}",
+                       "l2": "flushed before each step (256 MiB write); working set 134 MB > 126 MB L2",
+                       "submission": "one launch per sweep on one stream"},
+            "roofline": h["roofline"], "clocks": h["clocks"], "gpu_launches": h["gpu_launches"],
+            "e2e": h["e2e"], "cpu_baseline": cpu,
+            "graph": {"ms_per_step": h["graph_ms_per_step"], "value": h["graph_value"]},
+            "extra": extra,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------- reference --
+
+def run_reference(args) -> None:
+    """The oracle, as it stands, on the host cores: each step one bounded sample
+    (2 FP64 sweeps of the 4096^2 grid) of the headline workload."""
+    rank, _, world = dist_env()
+    if rank != 0:
+        return
+    from oracle import upir_oracle as O
+    u0 = I.jacobi_grid(N_GRID, seed=1)
+    per = 2
+    for _ in range(args.warmup):
+        O.jacobi_run(u0, 1)
+    ts = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        O.jacobi_run(u0, per)
+        ts.append(time.perf_counter() - t0)
+    dt = sum(ts)
+    value = args.steps * per * JACOBI_BYTES_PER_SWEEP / dt / 1e9
+    line = {"impl": "reference", "metric": "Parallel-loop HBM GB/s vs peak; batched regions/s fused vs per-region launch",
+            "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "jacobi5_4096x4096_100sweeps_maxresidual", "grid": [N_GRID, N_GRID],
+                       "sweeps_per_step": per, "parallelism": "host oracle, rank 0 only"},
+            "cpu_baseline": {"value": value, "unit": "GB/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{per} FP64 sweeps of the {N_GRID}x{N_GRID} grid per step"},
+            "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main() -> None:
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-extra", action="store_true", help="skip the extra workloads")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

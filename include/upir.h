@@ -1,0 +1,342 @@
+/*
+ * upir.h — C ABI of the B300 runtime for offloaded UPIR regions.
+ *
+ * The calls follow the parallel constructs of UPIR (Unified Parallel
+ * Intermediate Representation, arXiv 2209.10643):
+ *   - data mapping to / from / tofrom / allocate ........ §4.1, Fig. "data attributes"
+ *   - SPMD region with num_teams x num_units ............. §3.1, Fig. "SPMD parallelism"
+ *   - canonical loop (lowerBound, upperBound, step,
+ *     collapse) with worksharing schedule(static|dynamic,
+ *     chunk) distributed over teams and units ........... §3.2, Fig. "data parallelism"
+ *   - sync: reduction (operation + data), barrier,
+ *     taskwait ........................................... §5, Fig. "synchronization"
+ *
+ * Every function returns a upir_status (0 = UPIR_OK, negative = error).  No
+ * function throws, aborts or exits the process.  After an error the per-context
+ * text of upir_last_error() says what was wrong.  Handles are not thread-safe:
+ * use one context per host thread.
+ *
+ * Memory ownership.  The caller owns every host buffer it maps; a host buffer
+ * must stay valid until the matching upir_data_unmap() returns.  Device memory
+ * of mapped buffers and of the runtime's workspace belongs to the library and is
+ * obtained through the allocator given to upir_init() (cudaMallocAsync /
+ * cudaFreeAsync on the context stream when none is given).  Device memory handed
+ * in with upir_data_map_device() stays owned by the caller.
+ *
+ * Work is enqueued on the context's CUDA stream and runs in submission order.
+ * Host/device copies of a mapping happen on that stream; upir_data_unmap() and
+ * UPIR_SYNC_TASKWAIT block the host until the stream has drained.
+ */
+#ifndef UPIR_H
+#define UPIR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status -- */
+
+typedef int32_t upir_status;
+
+#define UPIR_OK            0
+#define UPIR_EINVAL       (-1) /* bad argument: step 0, trip overflow, bad enum, sizes      */
+#define UPIR_ENOTMAPPED   (-2) /* a buffer handle that is not (or no longer) mapped           */
+#define UPIR_EBUSY        (-3) /* object still in use (e.g. unmap of a buffer a live region uses) */
+#define UPIR_ENOMEM       (-4) /* the allocator returned NULL                                  */
+#define UPIR_ECUDA        (-5) /* a CUDA runtime call failed                                   */
+#define UPIR_ETIMEDOUT    (-6) /* a bounded device-side wait ran out (device error word set)  */
+#define UPIR_EUNSUPPORTED (-7) /* valid request this build does not execute (e.g. K % 8 != 0 on tensor cores) */
+
+/* Static text for a status code; never NULL. */
+const char* upir_status_string(upir_status s);
+
+/* ----------------------------------------------------------------- handles -- */
+
+typedef struct upir_ctx_s*    upir_ctx;
+typedef struct upir_buf_s*    upir_buf;
+typedef struct upir_region_s* upir_region;
+typedef struct upir_batch_s*  upir_batch;
+
+/* Device allocator callback.  alloc returns device memory of at least `bytes`
+ * bytes, 256-byte aligned, usable in stream order on `stream`, or NULL.
+ * free releases it in stream order. */
+typedef struct {
+    void* (*alloc)(size_t bytes, void* stream, void* user);
+    void  (*free)(void* ptr, size_t bytes, void* stream, void* user);
+    void* user;
+} upir_allocator;
+
+/* Create a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t to
+ * enqueue on (NULL: the context creates and owns its own non-blocking stream).
+ * `allocator` may be NULL (cudaMallocAsync/cudaFreeAsync).  The context owns a
+ * small device workspace (reduction partials, counters, the device error word).
+ * Errors: EINVAL (out == NULL, bad device), ECUDA, ENOMEM. */
+upir_status upir_init(upir_ctx* out, int32_t device, void* cuda_stream,
+                      const upir_allocator* allocator);
+
+/* Wait for the stream, free every buffer still mapped (no copy back), every
+ * region and batch, and the context.  A NULL context is a no-op. */
+upir_status upir_finalize(upir_ctx ctx);
+
+/* Text describing the last error on `ctx` (valid until the next call on it). */
+const char* upir_last_error(upir_ctx ctx);
+
+/* ------------------------------------------------------------ data mapping -- */
+/* §4.1: the data-mapping property of a data item is to, from, tofrom or
+ * allocate. */
+
+typedef enum {
+    UPIR_MAP_TO     = 0, /* allocate + host->device copy at map; no copy back at unmap     */
+    UPIR_MAP_FROM   = 1, /* allocate (contents undefined) at map; device->host at unmap    */
+    UPIR_MAP_TOFROM = 2, /* host->device at map; device->host at unmap                     */
+    UPIR_MAP_ALLOC  = 3  /* allocate only (contents undefined); no copies                  */
+} upir_map_kind;
+
+/* Map `bytes` bytes at host address `host` with mapping `kind`.  The copy for
+ * TO/TOFROM is enqueued on the context stream (asynchronous with respect to the
+ * host when `host` is page-locked).  bytes == 0 gives a valid empty mapping.
+ * Errors: EINVAL (NULL out, NULL host with bytes > 0 for TO/FROM/TOFROM, bad
+ * kind), ENOMEM, ECUDA. */
+upir_status upir_data_map(upir_ctx ctx, void* host, size_t bytes, int32_t kind,
+                          upir_buf* out);
+
+/* Wrap caller-owned device memory (e.g. a resident torch tensor) as a mapped
+ * buffer: no allocation, no copy, and unmap neither copies nor frees it. */
+upir_status upir_data_map_device(upir_ctx ctx, void* device_ptr, size_t bytes,
+                                 upir_buf* out);
+
+/* Explicit data movement of a mapped buffer (§4.2, data_update):
+ * direction UPIR_MAP_TO copies host->device, UPIR_MAP_FROM device->host and
+ * waits for it.  EINVAL for a device-wrapped buffer or another direction. */
+upir_status upir_data_update(upir_ctx ctx, upir_buf buf, int32_t direction);
+
+/* End a mapping: for FROM/TOFROM enqueue the device->host copy, wait for the
+ * stream, then release the device memory.  EBUSY if a live region or batch
+ * still refers to the buffer (destroy those first); ENOTMAPPED for a stale
+ * handle. */
+upir_status upir_data_unmap(upir_ctx ctx, upir_buf buf);
+
+/* Device address and size of a mapped buffer. */
+upir_status upir_buf_device_ptr(upir_buf buf, void** device_ptr, size_t* bytes);
+
+/* ------------------------------------------------------------- SPMD region -- */
+/* §3.1: an SPMD region runs num_teams teams of num_units units each.  Here a
+ * team is a CUDA thread block and a unit a thread, so the launch geometry is
+ * exactly <<<num_teams, num_units>>> (1 <= num_units <= 1024).  0 for either
+ * lets the planner choose it per loop.  The returned region is empty; loops and
+ * syncs are recorded into it and run by upir_region_submit().  A region can be
+ * submitted any number of times. */
+upir_status upir_spmd_region(upir_ctx ctx, int32_t num_teams, int32_t num_units,
+                             upir_region* out);
+
+/* --------------------------------------------------------- worksharing loop -- */
+
+typedef enum { UPIR_SCHED_STATIC = 0, UPIR_SCHED_DYNAMIC = 1 } upir_sched; /* §3.2 subset */
+
+typedef enum {
+    UPIR_RED_NONE = 0, UPIR_RED_ADD = 1, UPIR_RED_MUL = 2, UPIR_RED_MAX = 3, UPIR_RED_MIN = 4
+} upir_red_op;
+
+typedef enum { UPIR_F32 = 0, UPIR_I64 = 1 } upir_dtype;
+
+/* Loop bodies (hand-written sm_103a kernels).  Buffers (bufs[]) and scalars
+ * (scalars[]) per body; all arrays are dense, row-major, FP32 unless stated.
+ *
+ *  AXPY      bufs x[n], y[n]; scalars a [, imod_mul, imod_mod].
+ *            y[iv] = fma(a, x[iv], y[iv]) for every induction value iv  (§6 AXPY)
+ *  IMOD      no bufs; scalars imod_mul, imod_mod.  Empty body: only reduction
+ *            terms over iv.
+ *  COVERAGE  bufs owner[trip] (int64), count[trip] (int64) [; scalars imod_mul,
+ *            imod_mod].  owner[k] = flattened worker id (team*units + unit) that
+ *            ran logical iteration k, count[k] += 1: schedule instrumentation.
+ *  JACOBI5   bufs u_in[rows*cols], u_out[rows*cols]; scalars rows, cols.
+ *            collapse(2) over interior rows [lb, ub) (1 <= lb, ub <= rows-1, step 1)
+ *            and all interior columns: u_out = 0.25*((N+S)+(W+E)), rounded per
+ *            operation, no contraction.  Other points of u_out are not written.
+ *  MATVEC    bufs A[rows*cols], x[cols], y[rows]; scalars rows, cols.
+ *            y[r] = sum_j A[r][j] x[j] for rows r of the loop (§6 matvec).
+ *  GEMM_F32  bufs A[M*K], B[K*N], C[M*N]; scalars M, N, K.  C = A B, FP32 SIMT.
+ *  GEMM_BF16 bufs A[M*K] bf16, Bt[N*K] bf16 (B transposed, K contiguous),
+ *            C[M*N] FP32; scalars M, N, K.  Tensor cores (tcgen05), FP32 accumulate.
+ *  GEMM_BF16X3 bufs A_hi, A_lo [M*K] bf16, Bt_hi, Bt_lo [N*K] bf16, C[M*N];
+ *            scalars M, N, K.  C = A_hi B_hi + A_hi B_lo + A_lo B_hi on tensor cores.
+ *  SPLIT_BF16 bufs src[rows*cols] FP32, hi, lo (bf16) ; scalars rows, cols,
+ *            transpose (0/1).  hi = bf16(src), lo = bf16(src - hi) (round to
+ *            nearest even); with transpose the outputs are [cols*rows].
+ *
+ *  GEMM bodies: the loop runs over rows [lb, ub) of C with collapse 2 (all N
+ *  columns); tensor-core bodies need K % 8 == 0 (EUNSUPPORTED otherwise).
+ */
+typedef enum {
+    UPIR_BODY_AXPY = 0, UPIR_BODY_IMOD = 1, UPIR_BODY_JACOBI5 = 2, UPIR_BODY_MATVEC = 3,
+    UPIR_BODY_GEMM_F32 = 4, UPIR_BODY_GEMM_BF16 = 5, UPIR_BODY_GEMM_BF16X3 = 6,
+    UPIR_BODY_COVERAGE = 7, UPIR_BODY_SPLIT_BF16 = 8
+} upir_body;
+
+/* Value each iteration contributes to a reduction.
+ *   TERM_Y     AXPY: the updated y[iv];  MATVEC: y[r]
+ *   TERM_XY    AXPY: x[iv] * y[iv] (after the update; "AXPY + dot")
+ *   TERM_IMOD  (imod_mul * iv) mod imod_mod, 64-bit wrap, remainder in [0, mod)
+ *   TERM_IV    the induction value iv itself
+ *   TERM_RESID JACOBI5: |u_out - u_in| at the point                          */
+typedef enum {
+    UPIR_TERM_Y = 0, UPIR_TERM_XY = 1, UPIR_TERM_IMOD = 2, UPIR_TERM_IV = 3, UPIR_TERM_RESID = 4
+} upir_term;
+
+/* A reduction clause (§5: sync "reduction" with an operation and its data).
+ * The variable is element `index` of mapped buffer `var` (FP32 or int64).  Its
+ * value before the loop is combined exactly once with the iterations' terms.
+ * FP32 "+" is compensated (TwoSum) and, like FP32 "*", combined in a fixed tree
+ * order over per-team (static) or per-chunk (dynamic) partials, so results are
+ * bit-identical from run to run.  max/min (FP32: NaN operands ignored) and
+ * int64 +, *, max, min (two's-complement wrap) are exact in any order. */
+typedef struct {
+    int32_t  op;     /* upir_red_op */
+    int32_t  dtype;  /* upir_dtype  */
+    int32_t  term;   /* upir_term   */
+    int32_t  reserved;
+    upir_buf var;
+    int64_t  index;
+} upir_reduction;
+
+/* Tuning hints (§2.4 "UPIR extension": key-value pairs).  Unknown keys: EINVAL. */
+typedef enum {
+    UPIR_HINT_VARIANT   = 1, /* kernel variant of the body (body-specific, 0 = default)       */
+    UPIR_HINT_TILE_M    = 2, /* tile rows (JACOBI5 tiled variant, GEMM)                       */
+    UPIR_HINT_TILE_N    = 3, /* tile cols                                                     */
+    UPIR_HINT_VEC       = 4  /* iterations per vector access for AXPY (1 or 4)                */
+} upir_hint_key;
+
+/* The canonical loop with its worksharing parallelization (§3.2).
+ * Iterations: iv = lb, lb+step, ... while iv < ub (step > 0) or iv > ub
+ * (step < 0); trip = ceil((ub-lb)/step) or 0; step 0 is EINVAL.
+ * sched/chunk: static chunk c > 0 gives logical chunk j (iterations
+ * [j c, min((j+1) c, trip))) to worker j mod W; static chunk 0 splits the
+ * iterations into W contiguous blocks, the first (trip mod W) one longer;
+ * dynamic chunk c (0 means 1) hands out chunks in increasing order to whichever
+ * worker asks next.  W = teams * units for element bodies; the MATVEC worker is
+ * a warp and the tiled JACOBI5 / GEMM worker is a team (the loop is tiled and
+ * the tile loop workshared).  nowait drops the implicit barrier at the loop's
+ * end (§5); on one stream the next loop still starts after this one.
+ * Validation is eager: upir_loop() checks every field, buffer size and index
+ * range against the mapped buffers and returns EINVAL/ENOTMAPPED/EUNSUPPORTED
+ * without recording anything on error. */
+typedef struct {
+    int64_t lb, ub, step;
+    int32_t collapse;      /* 1, or 2 for JACOBI5 / GEMM_* */
+    int32_t sched;         /* upir_sched */
+    int64_t chunk;         /* >= 0 */
+    int32_t body;          /* upir_body */
+    int32_t nbufs;
+    const upir_buf* bufs;
+    int32_t nscalars;
+    int32_t nreductions;   /* 0..2 */
+    const double* scalars;
+    const upir_reduction* reductions;
+    int32_t nowait;
+    int32_t nhints;        /* number of (key, value) pairs */
+    const int64_t* hints;  /* key0, value0, key1, value1, ... */
+} upir_loop_desc;
+
+upir_status upir_loop(upir_region region, const upir_loop_desc* loop);
+
+/* -------------------------------------------------------------------- sync -- */
+
+typedef enum { UPIR_SYNC_BARRIER = 0, UPIR_SYNC_TASKWAIT = 1 } upir_sync_kind; /* §5 subset */
+
+/* BARRIER records an explicit barrier after the last recorded loop (redundant
+ * with an implicit one, which the runtime then elides).  TASKWAIT blocks the
+ * host until everything submitted on the context has finished and reports a
+ * device-side error (ETIMEDOUT) if one was raised. */
+upir_status upir_sync(upir_region region, int32_t kind);
+
+/* ----------------------------------------------------------------- execute -- */
+
+#define UPIR_SUBMIT_GRAPH 1  /* capture the region's launches in a CUDA graph once, replay it */
+
+/* Enqueue every recorded loop of the region on the context stream, in order.
+ * Asynchronous: returns once enqueued.  Buffers are resolved at submit time
+ * (ENOTMAPPED if one was unmapped since). */
+upir_status upir_region_submit(upir_region region, int32_t flags);
+
+/* Free a region (waits for nothing: its launches already hold what they need). */
+upir_status upir_region_destroy(upir_region region);
+
+/* Many independent regions at once.
+ *   LAUNCHES   : one launch per loop, regions one after another on the stream
+ *   GRAPH      : the same launches captured once in a CUDA graph and replayed
+ *   PERSISTENT : one persistent kernel over a work list of (region, tile)
+ *                items, longest first, claimed with an atomic counter; each
+ *                region's reduction is finalized by its last tile (fixed
+ *                order), and the launch is captured in a CUDA graph.
+ * PERSISTENT accepts regions of single AXPY (reductions over TERM_Y / TERM_XY),
+ * JACOBI5 (max residual) and MATVEC loops; others give EUNSUPPORTED. */
+typedef enum { UPIR_BATCH_LAUNCHES = 0, UPIR_BATCH_GRAPH = 1, UPIR_BATCH_PERSISTENT = 2 } upir_batch_mode;
+
+upir_status upir_batch_create(upir_ctx ctx, const upir_region* regions, int32_t n,
+                              int32_t mode, upir_batch* out);
+upir_status upir_batch_submit(upir_batch batch);
+upir_status upir_batch_destroy(upir_batch batch);
+
+/* Taskwait at context level: wait for the stream, then read and clear the
+ * device error word (ETIMEDOUT if a bounded wait ran out). */
+upir_status upir_ctx_wait(upir_ctx ctx);
+
+/* ------------------------------------------------------------ diagnostics -- */
+
+/* Launch records: when enabled, every kernel launch of a submitted loop is
+ * bracketed by CUDA events on the context stream.  upir_ctx_timings() waits
+ * for the stream and returns up to `cap` per-launch durations (ms) recorded
+ * since the last call, with the body of each; *count gets the number written. */
+upir_status upir_ctx_set_timing(upir_ctx ctx, int32_t enable);
+upir_status upir_ctx_timings(upir_ctx ctx, float* ms, int32_t* body, int32_t cap,
+                             int32_t* count);
+
+/* Launch geometry the planner chose for loop `loop_index` of a region (after
+ * upir_loop): teams (grid) and units (block) of its main kernel. */
+upir_status upir_region_loop_geometry(upir_region region, int32_t loop_index,
+                                      int32_t* teams, int32_t* units);
+
+/* Bounded-wait self test: launches one block that waits on an mbarrier phase
+ * nothing will complete, with the same bounded-spin helper the tensor-core
+ * GEMM uses, giving up after `spin_limit` polls.  The wait ends, the device
+ * error word is set and the next upir_ctx_wait() returns UPIR_ETIMEDOUT; the
+ * context stays usable. */
+upir_status upir_selftest_bounded_wait(upir_ctx ctx, int64_t spin_limit);
+
+/* Spin budget (polls) of every bounded device-side wait; default 2^26, also
+ * settable with the environment variable UPIR_SPIN_LIMIT. */
+upir_status upir_ctx_set_spin_limit(upir_ctx ctx, int64_t spin_limit);
+
+/* ------------------------------------------------------ learned cost model -- */
+/* A 12 -> 64 -> 64 -> 1 ReLU MLP predicting log2 of a loop's time from its
+ * features; weights used in bfloat16, FP32 accumulation and FP32 master
+ * weights.  Parameter block layout (FP32, contiguous, 5,121 floats):
+ *   W1[64][12], b1[64], W2[64][64], b2[64], W3[1][64], b3[1].
+ * All pointers are device pointers; calls are enqueued on the context stream. */
+
+#define UPIR_MLP_IN     12
+#define UPIR_MLP_HIDDEN 64
+#define UPIR_MLP_NPARAM (64 * 12 + 64 + 64 * 64 + 64 + 64 + 1)
+
+/* pred[b] for b < batch; x is [batch][12]. */
+upir_status upir_mlp_forward(upir_ctx ctx, const float* params, const float* x,
+                             int32_t batch, float* pred);
+
+/* Mean-squared-error loss against target[batch] and its gradient with respect
+ * to every parameter (same layout as params).  loss may be NULL. */
+upir_status upir_mlp_backward(upir_ctx ctx, const float* params, const float* x,
+                              const float* target, int32_t batch, float* grad,
+                              float* loss);
+
+/* params -= lr * grad, elementwise. */
+upir_status upir_mlp_sgd(upir_ctx ctx, float* params, const float* grad, float lr);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* UPIR_H */

@@ -1,0 +1,338 @@
+// Device-side building blocks shared by the loop kernels: compensated FP32
+// accumulation, reduction combine rules, warp/block trees in a fixed order,
+// worksharing schedule iteration, bounded mbarrier waits and TMA copies.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+#include "upir_internal.h"
+
+namespace upir {
+
+// ----------------------------------------------------------------------------
+// Reductions (§5: a reduction sync combines the units' partial values with the
+// clause's operation).  FP32 "+" keeps a (sum, compensation) pair built with
+// Knuth's TwoSum, so the result is close to the correctly rounded sum
+// whatever the order; the combine order itself is fixed, so results repeat
+// bit for bit.
+// ----------------------------------------------------------------------------
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float bp = __fsub_rn(s, a);
+    const float ap = __fsub_rn(s, bp);
+    e = __fadd_rn(__fsub_rn(a, ap), __fsub_rn(b, bp));
+}
+
+struct FAcc {
+    float s, c;
+};
+
+__device__ __forceinline__ FAcc facc_identity(int op) {
+    switch (op) {
+        case UPIR_RED_MUL: return {1.0f, 0.0f};
+        case UPIR_RED_MAX: return {-__int_as_float(0x7f800000), 0.0f};
+        case UPIR_RED_MIN: return {__int_as_float(0x7f800000), 0.0f};
+        default: return {0.0f, 0.0f};
+    }
+}
+
+// Add one term.  ``err`` is an exact low-order part of the term (the error of
+// a rounded product), folded into the compensation for "+".
+__device__ __forceinline__ void facc_add(FAcc& a, float v, int op, float err = 0.0f) {
+    switch (op) {
+        case UPIR_RED_ADD: {
+            float s, e;
+            two_sum(a.s, v, s, e);
+            a.s = s;
+            a.c = __fadd_rn(a.c, __fadd_rn(e, err));
+            break;
+        }
+        case UPIR_RED_MUL: a.s = __fmul_rn(a.s, v); break;
+        case UPIR_RED_MAX: a.s = fmaxf(a.s, v); break;
+        case UPIR_RED_MIN: a.s = fminf(a.s, v); break;
+        default: break;
+    }
+}
+
+// Commutative combine of two partials (identical bits for (a, b) and (b, a)).
+__device__ __forceinline__ FAcc facc_combine(FAcc a, FAcc b, int op) {
+    switch (op) {
+        case UPIR_RED_ADD: {
+            float s, e;
+            two_sum(a.s, b.s, s, e);
+            return {s, __fadd_rn(__fadd_rn(a.c, b.c), e)};
+        }
+        case UPIR_RED_MUL: return {__fmul_rn(a.s, b.s), 0.0f};
+        case UPIR_RED_MAX: return {fmaxf(a.s, b.s), 0.0f};
+        case UPIR_RED_MIN: return {fminf(a.s, b.s), 0.0f};
+        default: return a;
+    }
+}
+
+__device__ __forceinline__ long long iacc_identity(int op) {
+    switch (op) {
+        case UPIR_RED_MUL: return 1;
+        case UPIR_RED_MAX: return (long long)0x8000000000000000ull;
+        case UPIR_RED_MIN: return 0x7fffffffffffffffll;
+        default: return 0;
+    }
+}
+
+__device__ __forceinline__ long long iacc_combine(long long a, long long b, int op) {
+    switch (op) {
+        case UPIR_RED_ADD: return (long long)((unsigned long long)a + (unsigned long long)b);
+        case UPIR_RED_MUL: return (long long)((unsigned long long)a * (unsigned long long)b);
+        case UPIR_RED_MAX: return a > b ? a : b;
+        case UPIR_RED_MIN: return a < b ? a : b;
+        default: return a;
+    }
+}
+
+__device__ __forceinline__ Partial make_partial(FAcc f, long long i) {
+    Partial p;
+    p.s = f.s;
+    p.c = f.c;
+    p.i = i;
+    return p;
+}
+
+__device__ __forceinline__ Partial combine_partial(const Partial& a, const Partial& b,
+                                                   int fop, int iop) {
+    FAcc f = facc_combine(FAcc{a.s, a.c}, FAcc{b.s, b.c}, fop);
+    return make_partial(f, iacc_combine(a.i, b.i, iop));
+}
+
+__device__ __forceinline__ Partial identity_partial(int fop, int iop) {
+    return make_partial(facc_identity(fop), iacc_identity(iop));
+}
+
+__device__ __forceinline__ Partial shfl_xor_partial(const Partial& p, int m) {
+    Partial q;
+    q.s = __shfl_xor_sync(0xffffffffu, p.s, m);
+    q.c = __shfl_xor_sync(0xffffffffu, p.c, m);
+    q.i = __shfl_xor_sync(0xffffffffu, p.i, m);
+    return q;
+}
+
+// Butterfly over the 32 lanes: every lane ends with the same combined value.
+__device__ __forceinline__ Partial warp_reduce_partial(Partial p, int fop, int iop) {
+#pragma unroll
+    for (int m = 16; m >= 1; m >>= 1) p = combine_partial(p, shfl_xor_partial(p, m), fop, iop);
+    return p;
+}
+
+// Fixed-shape block tree; the result is valid in every thread.  All threads of
+// the block must call it.
+__device__ __forceinline__ Partial block_reduce_partial(Partial p, int fop, int iop) {
+    __shared__ Partial warp_part[32];
+    __shared__ Partial result;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwarps = (blockDim.x + 31) >> 5;
+    p = warp_reduce_partial(p, fop, iop);
+    __syncthreads();  // warp_part may still be read by a previous call
+    if (lane == 0) warp_part[warp] = p;
+    __syncthreads();
+    if (warp == 0) {
+        Partial q = lane < nwarps ? warp_part[lane] : identity_partial(fop, iop);
+        q = warp_reduce_partial(q, fop, iop);
+        if (lane == 0) result = q;
+    }
+    __syncthreads();
+    return result;
+}
+
+// Partials written by other blocks are read through L2 (L1 is not coherent).
+__device__ __forceinline__ Partial load_partial_cg(const Partial* src) {
+    const float4 v = __ldcg(reinterpret_cast<const float4*>(src));
+    Partial p;
+    p.s = v.x;
+    p.c = v.y;
+    p.i = (long long)(((unsigned long long)__float_as_uint(v.w) << 32) | __float_as_uint(v.z));
+    return p;
+}
+
+// Reduce slots [0, n) in a fixed order: thread t folds t, t + B, t + 2B, ...
+// sequentially, then the block tree.  Every thread of the block must call it.
+__device__ __forceinline__ Partial block_reduce_slots(const Partial* slots, int64_t n,
+                                                      int fop, int iop) {
+    Partial acc = identity_partial(fop, iop);
+    for (int64_t k = threadIdx.x; k < n; k += blockDim.x)
+        acc = combine_partial(acc, load_partial_cg(slots + k), fop, iop);
+    return block_reduce_partial(acc, fop, iop);
+}
+
+// Combine the reduction variables' values before the loop with the final
+// partial and store them (one thread).
+__device__ __forceinline__ void write_reduction_vars(const RedVars& rv, const Partial& fin) {
+    if (rv.fvar) {
+        const float init = *rv.fvar;
+        FAcc r = facc_combine(FAcc{init, 0.0f}, FAcc{fin.s, fin.c}, rv.fop);
+        *rv.fvar = rv.fop == UPIR_RED_ADD ? __fadd_rn(r.s, r.c) : r.s;
+    }
+    if (rv.ivar) *rv.ivar = iacc_combine(*rv.ivar, fin.i, rv.iop);
+}
+
+// Static schedules: block partial -> slot blockIdx.x; the last block of each
+// group of kGroup blocks folds its group, the last group folds the groups.
+// The counters are returned to zero by the blocks that finish with them.
+__device__ __forceinline__ void finish_static(const RedVars& rv, const Scratch& sc,
+                                              const Partial& block_p) {
+    __shared__ int last_in_group, last_overall;
+    const int64_t nblocks = gridDim.x;
+    const int64_t b = blockIdx.x;
+    const int64_t g = b / kGroup;
+    const int64_t ngroups = (nblocks + kGroup - 1) / kGroup;
+    if (threadIdx.x == 0) {
+        sc.partials[b] = block_p;
+        __threadfence();
+        const unsigned gsize = (unsigned)(kGroup < nblocks - g * kGroup ? (int64_t)kGroup : nblocks - g * kGroup);
+        const unsigned t = atomicAdd(sc.group_tickets + g, 1u);
+        last_in_group = (t == gsize - 1);
+    }
+    __syncthreads();
+    if (!last_in_group) return;
+    __threadfence();
+    const int64_t gsize = (kGroup < nblocks - g * kGroup ? (int64_t)kGroup : nblocks - g * kGroup);
+    const Partial gp = block_reduce_slots(sc.partials + g * kGroup, gsize, rv.fop, rv.iop);
+    if (threadIdx.x == 0) {
+        sc.group_tickets[g] = 0;
+        sc.group_partials[g] = gp;
+        __threadfence();
+        const unsigned t = atomicAdd(sc.ticket, 1u);
+        last_overall = (t == (unsigned)ngroups - 1);
+    }
+    __syncthreads();
+    if (!last_overall) return;
+    __threadfence();
+    const Partial fin = block_reduce_slots(sc.group_partials, ngroups, rv.fop, rv.iop);
+    if (threadIdx.x == 0) {
+        *sc.ticket = 0;
+        write_reduction_vars(rv, fin);
+    }
+}
+
+// Dynamic schedules: partials are per chunk (written by the thread that ran
+// the chunk); the last block to finish folds all chunk slots in index order
+// and resets the chunk counter.
+__device__ __forceinline__ void finish_dynamic(const RedVars& rv, const Scratch& sc,
+                                               int64_t nchunks, bool has_red) {
+    __shared__ int last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned t = atomicAdd(sc.ticket, 1u);
+        last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    if (has_red) {
+        const Partial fin = block_reduce_slots(sc.partials, nchunks, rv.fop, rv.iop);
+        if (threadIdx.x == 0) write_reduction_vars(rv, fin);
+    }
+    if (threadIdx.x == 0) {
+        *sc.ticket = 0;
+        *sc.chunk_counter = 0;
+    }
+}
+
+// Warp-aggregated claim of the next dynamic chunk: the active lanes take
+// consecutive tickets with one atomic.
+__device__ __forceinline__ unsigned long long claim_chunk(unsigned long long* counter) {
+    const unsigned mask = __activemask();
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(mask) - 1;
+    unsigned long long base = 0;
+    if (lane == leader) base = atomicAdd(counter, (unsigned long long)__popc(mask));
+    base = __shfl_sync(mask, base, leader);
+    return base + __popc(mask & ((1u << lane) - 1u));
+}
+
+// ----------------------------------------------------------------------------
+// Worksharing (§3.2, schedule(static[, chunk])): call f(k0, k1) for each
+// contiguous range of logical iterations worker w owns.
+//   chunk > 0 : chunks j = w, w + W, ... ([j c, min((j+1) c, trip)))
+//   chunk = 0 : one block of ceil/floor(trip / W), the longer ones first.
+// ----------------------------------------------------------------------------
+
+template <class F>
+__device__ __forceinline__ void static_ranges(int64_t trip, int64_t chunk, int64_t W,
+                                              int64_t w, F&& f) {
+    if (chunk > 0) {
+        for (int64_t j = w; j < (trip + chunk - 1) / chunk; j += W) {
+            const int64_t k0 = j * chunk;
+            f(k0, min(k0 + chunk, trip));
+        }
+    } else {
+        const int64_t base = trip / W, extra = trip % W;
+        const int64_t start = w * base + min(w, extra);
+        const int64_t len = base + (w < extra ? 1 : 0);
+        if (len > 0) f(start, start + len);
+    }
+}
+
+// ----------------------------------------------------------------------------
+// mbarrier and TMA (PTX ISA: mbarrier.*, cp.async.bulk.tensor).  Every wait is
+// bounded: after ``limit`` polls it records UPIR_ERR_WAIT_TIMEOUT in the
+// device error word and returns false; callers then skip the dependent work.
+// ----------------------------------------------------------------------------
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                 ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity) : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for phase ``parity`` of ``bar``.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity,
+                                                  long long limit, int* err_word) {
+    for (long long n = 0; n < limit; ++n)
+        if (mbar_try_wait(bar, parity)) return true;
+    if (err_word) atomicCAS(err_word, 0, UPIR_ERR_WAIT_TIMEOUT);
+    return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* smem_dst, const void* tmap, uint64_t* bar,
+                                            int32_t x, int32_t y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];"
+        ::"r"(smem_u32(smem_dst)), "l"(tmap), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void prefetch_tmap(const void* tmap) {
+    asm volatile("prefetch.tensormap [%0];" ::"l"(tmap) : "memory");
+}
+
+}  // namespace upir

@@ -1,0 +1,515 @@
+// Loop validation and launch planning (§3.2: canonical loop + worksharing;
+// §5: reduction clauses).  A loop is checked completely when it is recorded;
+// the planner then fixes the kernel variant, the launch geometry, the device
+// scratch and the kernel parameters, so submission only launches.
+#include <cstring>
+
+#include "runtime_internal.h"
+
+using namespace upir;
+
+namespace {
+
+constexpr int64_t kMaxTrip = 1ll << 62;
+constexpr int kResidentThreadsPerSM = 2048;
+
+int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// ceil((ub - lb) / step) in 128-bit arithmetic (no overflow for any int64 bounds).
+bool compute_trip(int64_t lb, int64_t ub, int64_t step, int64_t* trip) {
+    __int128 n = 0;
+    if (step > 0 && ub > lb) n = ((__int128)ub - lb + step - 1) / step;
+    if (step < 0 && lb > ub) n = ((__int128)lb - ub + (-(__int128)step) - 1) / (-(__int128)step);
+    if (n > kMaxTrip) return false;
+    *trip = (int64_t)n;
+    return true;
+}
+
+bool is_int(double v) { return v == (double)(int64_t)v; }
+
+struct Check {
+    upir_ctx ctx;
+    upir_status st = UPIR_OK;
+    bool operator()(bool cond, upir_status code, const char* msg) {
+        if (!cond && st == UPIR_OK) st = fail(ctx, code, "upir_loop: %s", msg);
+        return cond;
+    }
+};
+
+// Device scratch: [chunk counter u64][ticket u32][pad][group tickets u32 x G]
+// [group partials x G][partials x S], zeroed once.
+upir_status alloc_scratch(upir_ctx ctx, LoopRec& lp, int64_t ngroups, int64_t nslots, Scratch* sc) {
+    const size_t head = 16;
+    const size_t gt = ((size_t)ngroups * 4 + 15) / 16 * 16;
+    const size_t bytes = head + gt + (size_t)ngroups * sizeof(Partial) + (size_t)nslots * sizeof(Partial);
+    char* p = static_cast<char*>(dev_alloc(ctx, bytes));
+    if (!p) return fail(ctx, UPIR_ENOMEM, "upir_loop: scratch allocation of %zu bytes failed", bytes);
+    cudaError_t e = cudaMemsetAsync(p, 0, bytes, ctx->stream);
+    if (e != cudaSuccess) {
+        dev_free(ctx, p, bytes);
+        return cuda_fail(ctx, e, "upir_loop: scratch memset");
+    }
+    lp.scratch = p;
+    lp.scratch_bytes = bytes;
+    sc->chunk_counter = reinterpret_cast<unsigned long long*>(p);
+    sc->ticket = reinterpret_cast<unsigned*>(p + 8);
+    sc->group_tickets = reinterpret_cast<unsigned*>(p + head);
+    sc->group_partials = reinterpret_cast<Partial*>(p + head + gt);
+    sc->partials = sc->group_partials + ngroups;
+    return UPIR_OK;
+}
+
+int default_teams_for_chunks(int64_t nchunks, int units) {
+    const int64_t resident = (int64_t)kNumSMs * (kResidentThreadsPerSM / units);
+    return (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(nchunks, units), resident));
+}
+
+}  // namespace
+
+namespace upir {
+
+using PFN_encodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                     const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                     const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                     CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+upir_status encode_tmap_2d(upir_ctx ctx, CUtensorMap* m, const void* base, int dtype_code,
+                           int elem_bytes, uint64_t cols, uint64_t rows, uint32_t box_cols,
+                           uint32_t box_rows, int swizzle_128b) {
+    static PFN_encodeTiled fn = nullptr;
+    if (!fn) {
+        cudaDriverEntryPointQueryResult q;
+        void* f = nullptr;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000,
+                                                         cudaEnableDefault, &q);
+        if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !f)
+            return fail(ctx, UPIR_ECUDA, "cuTensorMapEncodeTiled entry point unavailable");
+        fn = reinterpret_cast<PFN_encodeTiled>(f);
+    }
+    const cuuint64_t dims[2] = {cols, rows};
+    const cuuint64_t strides[1] = {cols * (uint64_t)elem_bytes};
+    const cuuint32_t box[2] = {box_cols, box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(m, (CUtensorMapDataType)dtype_code, 2, const_cast<void*>(base), dims, strides,
+                    box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    swizzle_128b ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(ctx, UPIR_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return UPIR_OK;
+}
+
+void release_loop(upir_ctx ctx, LoopRec& lp) {
+    if (lp.scratch) {
+        cudaStreamSynchronize(ctx->stream);
+        dev_free(ctx, lp.scratch, lp.scratch_bytes);
+        lp.scratch = nullptr;
+    }
+    if (lp.holds_refs) {
+        for (upir_buf b : lp.bufs) b->refs--;
+        for (auto& red : lp.reds) red.var->refs--;
+        lp.holds_refs = false;
+    }
+}
+
+upir_status plan_loop(upir_region r, const upir_loop_desc* d, LoopRec& lp) {
+    upir_ctx ctx = r->ctx;
+    Check ok{ctx};
+    if (!ok(d != nullptr, UPIR_EINVAL, "descriptor is NULL")) return ok.st;
+    ok(d->step != 0, UPIR_EINVAL, "step must be non-zero");
+    ok(d->chunk >= 0, UPIR_EINVAL, "chunk must be >= 0");
+    ok(d->sched == UPIR_SCHED_STATIC || d->sched == UPIR_SCHED_DYNAMIC, UPIR_EINVAL, "unknown schedule");
+    ok(d->body >= UPIR_BODY_AXPY && d->body <= UPIR_BODY_SPLIT_BF16, UPIR_EINVAL, "unknown body");
+    ok(d->nbufs >= 0 && (d->nbufs == 0 || d->bufs), UPIR_EINVAL, "bad buffer list");
+    ok(d->nscalars >= 0 && (d->nscalars == 0 || d->scalars), UPIR_EINVAL, "bad scalar list");
+    ok(d->nreductions >= 0 && d->nreductions <= 2 && (d->nreductions == 0 || d->reductions),
+       UPIR_EINVAL, "0..2 reductions per loop");
+    ok(d->nhints >= 0 && (d->nhints == 0 || d->hints), UPIR_EINVAL, "bad hint list");
+    ok(d->collapse == 1 || d->collapse == 2, UPIR_EINVAL, "collapse must be 1 or 2");
+    if (ok.st) return ok.st;
+    if (!ok(compute_trip(d->lb, d->ub, d->step, &lp.trip), UPIR_EINVAL, "trip count overflows"))
+        return ok.st;
+
+    lp.lb = d->lb;
+    lp.ub = d->ub;
+    lp.step = d->step;
+    lp.chunk = d->chunk;
+    lp.collapse = d->collapse;
+    lp.sched = d->sched;
+    lp.body = d->body;
+    lp.nowait = d->nowait;
+    for (int i = 0; i < d->nbufs; ++i) {
+        if (!d->bufs[i] || !ctx->all_bufs.count(d->bufs[i]) || !d->bufs[i]->live)
+            return fail(ctx, UPIR_ENOTMAPPED, "upir_loop: buffer %d is not mapped", i);
+        lp.bufs.push_back(d->bufs[i]);
+    }
+    lp.scalars.assign(d->scalars, d->scalars + d->nscalars);
+    for (int i = 0; i < d->nhints; ++i) {
+        const int64_t k = d->hints[2 * i], v = d->hints[2 * i + 1];
+        if (k == UPIR_HINT_VARIANT) ok(v >= 0 && v <= 3, UPIR_EINVAL, "variant hint out of range"), lp.variant = (int)v;
+        else if (k == UPIR_HINT_TILE_M) ok(v >= 1 && v <= 254, UPIR_EINVAL, "tile_m hint out of range"), lp.tile_m = (int)v;
+        else if (k == UPIR_HINT_TILE_N) ok(v >= 4 && v <= 248 && v % 4 == 0, UPIR_EINVAL, "tile_n hint must be a multiple of 4 in [4, 248]"), lp.tile_n = (int)v;
+        else if (k == UPIR_HINT_VEC) ok(v == 1 || v == 4, UPIR_EINVAL, "vec hint must be 1 or 4"), lp.vec = (int)v;
+        else ok(false, UPIR_EINVAL, "unknown hint key");
+    }
+    if (ok.st) return ok.st;
+
+    // Reductions: at most one FP32 and one int64 clause.
+    RedVars rv{nullptr, nullptr, UPIR_RED_NONE, UPIR_RED_NONE, 0, 0};
+    for (int i = 0; i < d->nreductions; ++i) {
+        const upir_reduction& red = d->reductions[i];
+        ok(red.op >= UPIR_RED_ADD && red.op <= UPIR_RED_MIN, UPIR_EINVAL, "unknown reduction op");
+        ok(red.dtype == UPIR_F32 || red.dtype == UPIR_I64, UPIR_EINVAL, "unknown reduction dtype");
+        ok(red.term >= UPIR_TERM_Y && red.term <= UPIR_TERM_RESID, UPIR_EINVAL, "unknown reduction term");
+        if (ok.st) return ok.st;
+        if (!red.var || !ctx->all_bufs.count(red.var) || !red.var->live)
+            return fail(ctx, UPIR_ENOTMAPPED, "upir_loop: reduction variable %d is not mapped", i);
+        const size_t esz = red.dtype == UPIR_F32 ? 4 : 8;
+        if (!ok(red.index >= 0 && (size_t)(red.index + 1) * esz <= red.var->bytes, UPIR_EINVAL,
+                "reduction index outside its buffer"))
+            return ok.st;
+        if (red.dtype == UPIR_F32) {
+            if (!ok(rv.fvar == nullptr, UPIR_EINVAL, "at most one FP32 reduction per loop")) return ok.st;
+            rv.fvar = static_cast<float*>(red.var->dev) + red.index;
+            rv.fop = red.op;
+            rv.fterm = red.term;
+        } else {
+            if (!ok(rv.ivar == nullptr, UPIR_EINVAL, "at most one int64 reduction per loop")) return ok.st;
+            rv.ivar = static_cast<long long*>(red.var->dev) + red.index;
+            rv.iop = red.op;
+            rv.iterm = red.term;
+        }
+        lp.reds.push_back(red);
+    }
+    const bool has_f = rv.fvar != nullptr, has_i = rv.ivar != nullptr;
+    const bool has_red = has_f || has_i;
+    const int64_t first_iv = lp.lb;
+    const int64_t last_iv = lp.trip ? lp.lb + (lp.trip - 1) * lp.step : lp.lb;
+    const int64_t min_iv = std::min(first_iv, last_iv), max_iv = std::max(first_iv, last_iv);
+    auto buf_floats = [&](int i) { return (int64_t)(lp.bufs[i]->bytes / 4); };
+
+    // int64 terms over the induction value
+    long long imod_mul = 0, imod_mod = 1, imod_inc = 0;
+    auto check_int_terms = [&](int scalar_base) {
+        if (!has_i) return;
+        ok(rv.iterm == UPIR_TERM_IMOD || rv.iterm == UPIR_TERM_IV, UPIR_EINVAL,
+           "int64 reductions take TERM_IMOD or TERM_IV");
+        if (rv.iterm != UPIR_TERM_IMOD) return;
+        if (!ok((int)lp.scalars.size() >= scalar_base + 2, UPIR_EINVAL, "TERM_IMOD needs scalars mul, mod"))
+            return;
+        const double mu = lp.scalars[scalar_base], mo = lp.scalars[scalar_base + 1];
+        ok(is_int(mu) && is_int(mo) && mo >= 1 && mo < 4.6e18 && std::abs(mu) < 9.2e18, UPIR_EINVAL,
+           "TERM_IMOD needs integer mul and a modulus in [1, 2^62)");
+        if (ok.st) return;
+        imod_mul = (long long)mu;
+        imod_mod = (long long)mo;
+        const __int128 big = (__int128)1 << 62;
+        const __int128 pm = (__int128)imod_mul * std::max<__int128>(-(__int128)min_iv, (__int128)max_iv);
+        ok(pm < big && pm > -big, UPIR_EINVAL, "(mul * iv) overflows int64 for this loop");
+        const __int128 inc = ((__int128)imod_mul * lp.step) % imod_mod;
+        imod_inc = (long long)(inc < 0 ? inc + imod_mod : inc);
+    };
+
+    const int U0 = r->units, T0 = r->teams;
+    lp.units = U0 ? U0 : 256;
+    lp.kind = LK_ELEM;
+    ElemParams& ep = lp.ep;
+    memset(&ep, 0, sizeof(ep));
+    ep.lb = lp.lb;
+    ep.step = lp.step;
+    ep.trip = lp.trip;
+    ep.chunk = lp.chunk;
+    ep.rv = rv;
+    ep.imod_mod = 1;
+
+    switch (lp.body) {
+        case UPIR_BODY_AXPY: {
+            ok(lp.bufs.size() == 2, UPIR_EINVAL, "AXPY takes bufs x, y");
+            ok(lp.scalars.size() >= 1, UPIR_EINVAL, "AXPY takes scalar a");
+            ok(lp.collapse == 1, UPIR_EINVAL, "AXPY is a collapse(1) loop");
+            if (ok.st) return ok.st;
+            if (lp.trip)
+                ok(min_iv >= 0 && max_iv < buf_floats(0) && max_iv < buf_floats(1), UPIR_EINVAL,
+                   "AXPY iterations index outside x or y");
+            if (has_f) ok(rv.fterm == UPIR_TERM_Y || rv.fterm == UPIR_TERM_XY, UPIR_EINVAL,
+                          "AXPY FP32 reductions take TERM_Y or TERM_XY");
+            check_int_terms(1);
+            ep.x = static_cast<const float*>(lp.bufs[0]->dev);
+            ep.y = static_cast<float*>(lp.bufs[1]->dev);
+            ep.a = (float)lp.scalars[0];
+            break;
+        }
+        case UPIR_BODY_IMOD: {
+            ok(lp.bufs.empty(), UPIR_EINVAL, "IMOD takes no buffers");
+            ok(!has_f, UPIR_EINVAL, "IMOD has no FP32 terms");
+            check_int_terms(0);
+            break;
+        }
+        case UPIR_BODY_COVERAGE: {
+            ok(lp.bufs.size() == 2, UPIR_EINVAL, "COVERAGE takes bufs owner, count");
+            ok(!has_f, UPIR_EINVAL, "COVERAGE has no FP32 terms");
+            if (ok.st) return ok.st;
+            ok((int64_t)(lp.bufs[0]->bytes / 8) >= lp.trip && (int64_t)(lp.bufs[1]->bytes / 8) >= lp.trip,
+               UPIR_EINVAL, "COVERAGE buffers need trip int64 elements");
+            check_int_terms(0);
+            ep.owner = static_cast<long long*>(lp.bufs[0]->dev);
+            ep.count = static_cast<unsigned long long*>(lp.bufs[1]->dev);
+            lp.vec = 1;
+            break;
+        }
+        case UPIR_BODY_JACOBI5: {
+            ok(lp.bufs.size() == 2, UPIR_EINVAL, "JACOBI5 takes bufs u_in, u_out");
+            ok(lp.scalars.size() >= 2, UPIR_EINVAL, "JACOBI5 takes scalars rows, cols");
+            ok(lp.collapse == 2, UPIR_EINVAL, "JACOBI5 is a collapse(2) loop");
+            if (ok.st) return ok.st;
+            const double rows = lp.scalars[0], cols = lp.scalars[1];
+            ok(is_int(rows) && is_int(cols) && rows >= 3 && cols >= 3 && rows < 2e9 && cols < 2e9,
+               UPIR_EINVAL, "JACOBI5 grid must be at least 3 x 3");
+            if (ok.st) return ok.st;
+            const int64_t R = (int64_t)rows, C = (int64_t)cols;
+            ok(lp.bufs[0] != lp.bufs[1], UPIR_EINVAL, "JACOBI5 needs distinct u_in and u_out");
+            ok(buf_floats(0) >= R * C && buf_floats(1) >= R * C, UPIR_EINVAL, "JACOBI5 buffers smaller than the grid");
+            ok(lp.step == 1 && (lp.trip == 0 || (lp.lb >= 1 && lp.ub <= R - 1)), UPIR_EINVAL,
+               "JACOBI5 rows must be a unit-step range inside [1, rows-1)");
+            ok(!has_i, UPIR_EINVAL, "JACOBI5 has no int64 terms");
+            if (has_f) ok(rv.fterm == UPIR_TERM_RESID, UPIR_EINVAL, "JACOBI5 reductions take TERM_RESID");
+            if (ok.st) return ok.st;
+            const float* uin = static_cast<const float*>(lp.bufs[0]->dev);
+            float* uout = static_cast<float*>(lp.bufs[1]->dev);
+            const bool tma_ok = C % 4 == 0 && (reinterpret_cast<uintptr_t>(uin) & 15) == 0 &&
+                                (reinterpret_cast<uintptr_t>(uout) & 15) == 0 &&
+                                (!has_f || rv.fop == UPIR_RED_MAX || rv.fop == UPIR_RED_MIN);
+            if (lp.variant == 0 && tma_ok) {
+                lp.kind = LK_JACOBI_TMA;
+                JacobiParams& jp = lp.jp;
+                memset(&jp, 0, sizeof(jp));
+                lp.tile_m = lp.tile_m ? lp.tile_m : 32;
+                lp.tile_n = lp.tile_n ? lp.tile_n : 128;
+                lp.tile_n = (int)std::min<int64_t>(lp.tile_n, 4 * (int64_t)lp.units);
+                jp.uin = uin;
+                jp.uout = uout;
+                jp.rows = R;
+                jp.cols = C;
+                jp.r_lb = lp.lb;
+                jp.r_ub = lp.lb + lp.trip;
+                jp.tile_m = lp.tile_m;
+                jp.tile_n = lp.tile_n;
+                jp.tiles_r = ceil_div(lp.trip, lp.tile_m);
+                jp.tiles_c = ceil_div(C, lp.tile_n);
+                jp.ntiles = jp.tiles_r * jp.tiles_c;
+                jp.chunk = lp.chunk;
+                jp.sched = lp.sched;
+                jp.rvar = rv.fvar;
+                jp.rop = rv.fop == UPIR_RED_MIN ? UPIR_RED_MIN : UPIR_RED_MAX;
+                jp.spin_limit = ctx->spin_limit;
+                jp.err_word = ctx->err_word;
+                lp.smem = jacobi_tma_smem_bytes(lp.tile_m, lp.tile_n);
+                if (!ok(lp.smem <= 200 * 1024, UPIR_EINVAL, "Jacobi tile too large for shared memory"))
+                    return ok.st;
+                if (lp.trip) {
+                    upir_status st = encode_tmap_2d(ctx, &lp.tmap[0], uin, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4,
+                                                    (uint64_t)C, (uint64_t)R, (uint32_t)(lp.tile_n + 8),
+                                                    (uint32_t)(lp.tile_m + 2), 0);
+                    if (st != UPIR_OK) return st;
+                }
+                const int64_t c = lp.chunk > 0 ? lp.chunk : 1;
+                if (T0) lp.teams = T0;
+                else if (lp.sched == UPIR_SCHED_STATIC && lp.chunk == 0)
+                    lp.teams = (int)std::min<int64_t>(std::max<int64_t>(jp.ntiles, 1), 0x7fffffff);
+                else
+                    lp.teams = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(jp.ntiles, c), kNumSMs * 8));
+                if (lp.sched == UPIR_SCHED_DYNAMIC) {
+                    upir_status st = alloc_scratch(ctx, lp, 0, 0, &jp.sc);
+                    if (st != UPIR_OK) return st;
+                }
+                lp.skip = lp.trip == 0;
+                return UPIR_OK;
+            }
+            // per-point variant (worker = unit, iteration = point)
+            ep.uin = uin;
+            ep.uout = uout;
+            ep.rows = R;
+            ep.cols = C;
+            ep.trip = lp.trip * (C - 2);
+            ep.step = 1;
+            lp.vec = 1;
+            lp.trip = ep.trip;
+            break;
+        }
+        case UPIR_BODY_MATVEC: {
+            ok(lp.bufs.size() == 3, UPIR_EINVAL, "MATVEC takes bufs A, x, y");
+            ok(lp.scalars.size() >= 2, UPIR_EINVAL, "MATVEC takes scalars rows, cols");
+            ok(!has_red, UPIR_EINVAL, "MATVEC takes no reduction clause");
+            ok(lp.collapse == 1, UPIR_EINVAL, "MATVEC is a collapse(1) loop over rows");
+            if (ok.st) return ok.st;
+            const double rows = lp.scalars[0], cols = lp.scalars[1];
+            ok(is_int(rows) && is_int(cols) && rows >= 0 && cols >= 0, UPIR_EINVAL, "bad matvec shape");
+            if (ok.st) return ok.st;
+            const int64_t R = (int64_t)rows, C = (int64_t)cols;
+            ok(buf_floats(0) >= R * C && buf_floats(1) >= C && buf_floats(2) >= R, UPIR_EINVAL,
+               "MATVEC buffers smaller than the shape");
+            if (lp.trip) ok(min_iv >= 0 && max_iv < R, UPIR_EINVAL, "MATVEC rows outside [0, rows)");
+            ok(lp.units % 32 == 0, UPIR_EINVAL, "MATVEC needs num_units a multiple of 32 (worker = warp)");
+            if (ok.st) return ok.st;
+            lp.kind = LK_MATVEC;
+            MatvecParams& mp = lp.mp;
+            memset(&mp, 0, sizeof(mp));
+            mp.A = static_cast<const float*>(lp.bufs[0]->dev);
+            mp.x = static_cast<const float*>(lp.bufs[1]->dev);
+            mp.y = static_cast<float*>(lp.bufs[2]->dev);
+            mp.rows = R;
+            mp.cols = C;
+            mp.lb = lp.lb;
+            mp.step = lp.step;
+            mp.trip = lp.trip;
+            mp.chunk = lp.chunk;
+            mp.sched = lp.sched;
+            const int64_t wpb = lp.units / 32;
+            const int64_t resident_warps = (int64_t)kNumSMs * (kResidentThreadsPerSM / 32);
+            if (T0) lp.teams = T0;
+            else if (lp.sched == UPIR_SCHED_STATIC && lp.chunk == 0) {
+                const int64_t per = std::max<int64_t>(1, ceil_div(lp.trip, resident_warps));
+                lp.teams = (int)std::max<int64_t>(1, ceil_div(ceil_div(lp.trip, per), wpb));
+            } else {
+                const int64_t c = lp.chunk > 0 ? lp.chunk : 1;
+                lp.teams = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(ceil_div(lp.trip, c), wpb),
+                                                                       resident_warps / wpb));
+            }
+            if (lp.sched == UPIR_SCHED_DYNAMIC) {
+                upir_status st = alloc_scratch(ctx, lp, 0, 0, &mp.sc);
+                if (st != UPIR_OK) return st;
+            }
+            lp.skip = lp.trip == 0;
+            return UPIR_OK;
+        }
+        case UPIR_BODY_GEMM_F32:
+        case UPIR_BODY_GEMM_BF16:
+        case UPIR_BODY_GEMM_BF16X3: {
+            const bool tc = lp.body != UPIR_BODY_GEMM_F32;
+            const size_t nb = lp.body == UPIR_BODY_GEMM_BF16X3 ? 5 : 3;
+            ok(lp.bufs.size() == nb, UPIR_EINVAL, "GEMM buffer count (F32: A B C; BF16: A Bt C; BF16X3: Ah Al Bth Btl C)");
+            ok(lp.scalars.size() >= 3, UPIR_EINVAL, "GEMM takes scalars M, N, K");
+            ok(!has_red, UPIR_EINVAL, "GEMM takes no reduction clause");
+            ok(lp.collapse == 2, UPIR_EINVAL, "GEMM is a collapse(2) loop");
+            if (ok.st) return ok.st;
+            const double Md = lp.scalars[0], Nd = lp.scalars[1], Kd = lp.scalars[2];
+            ok(is_int(Md) && is_int(Nd) && is_int(Kd) && Md >= 0 && Nd >= 0 && Kd >= 0 && Md < 2e9 && Nd < 2e9 && Kd < 2e9,
+               UPIR_EINVAL, "bad GEMM shape");
+            if (ok.st) return ok.st;
+            const int64_t M = (int64_t)Md, N = (int64_t)Nd, K = (int64_t)Kd;
+            ok(lp.step == 1 && (lp.trip == 0 || (lp.lb >= 0 && lp.ub <= M)), UPIR_EINVAL,
+               "GEMM rows must be a unit-step range inside [0, M)");
+            if (ok.st) return ok.st;
+            if (!tc) {
+                ok((int64_t)(lp.bufs[0]->bytes / 4) >= M * K && (int64_t)(lp.bufs[1]->bytes / 4) >= K * N &&
+                   (int64_t)(lp.bufs[2]->bytes / 4) >= M * N, UPIR_EINVAL, "GEMM buffers smaller than the shape");
+                ok(lp.units == 256, UPIR_EUNSUPPORTED, "GEMM_F32 runs with num_units 256");
+                if (ok.st) return ok.st;
+                lp.kind = LK_GEMM_F32;
+                GemmParams& gp = lp.gp;
+                memset(&gp, 0, sizeof(gp));
+                gp.A = static_cast<const float*>(lp.bufs[0]->dev);
+                gp.B = static_cast<const float*>(lp.bufs[1]->dev);
+                gp.C = static_cast<float*>(lp.bufs[2]->dev);
+                gp.M = M;
+                gp.N = N;
+                gp.K = K;
+                gp.row_lb = lp.lb;
+                gp.row_ub = lp.lb + lp.trip;
+                gp.chunk = lp.chunk;
+                gp.sched = lp.sched;
+                const int64_t ntiles = ceil_div(lp.trip, 128) * ceil_div(N, 128);
+                const int64_t c = lp.chunk > 0 ? lp.chunk : 1;
+                if (T0) lp.teams = T0;
+                else if (lp.sched == UPIR_SCHED_STATIC && lp.chunk == 0)
+                    lp.teams = (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, 0x7fffffff));
+                else
+                    lp.teams = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(ntiles, c), kNumSMs * 2));
+                if (lp.sched == UPIR_SCHED_DYNAMIC) {
+                    upir_status st = alloc_scratch(ctx, lp, 0, 0, &gp.sc);
+                    if (st != UPIR_OK) return st;
+                }
+                lp.skip = lp.trip == 0 || N == 0;
+                return UPIR_OK;
+            }
+            return plan_gemm_tc(r, lp, M, N, K, ok.st);
+        }
+        case UPIR_BODY_SPLIT_BF16: {
+            ok(lp.bufs.size() == 3, UPIR_EINVAL, "SPLIT_BF16 takes bufs src, hi, lo");
+            ok(lp.scalars.size() >= 3, UPIR_EINVAL, "SPLIT_BF16 takes scalars rows, cols, transpose");
+            ok(!has_red, UPIR_EINVAL, "SPLIT_BF16 takes no reduction clause");
+            if (ok.st) return ok.st;
+            const double rows = lp.scalars[0], cols = lp.scalars[1];
+            ok(is_int(rows) && is_int(cols) && rows >= 0 && cols >= 0, UPIR_EINVAL, "bad split shape");
+            if (ok.st) return ok.st;
+            const int64_t R = (int64_t)rows, C = (int64_t)cols;
+            ok(buf_floats(0) >= R * C && (int64_t)(lp.bufs[1]->bytes / 2) >= R * C &&
+               (int64_t)(lp.bufs[2]->bytes / 2) >= R * C, UPIR_EINVAL, "SPLIT_BF16 buffers smaller than the shape");
+            ok(lp.step == 1 && (lp.trip == 0 || (lp.lb >= 0 && lp.ub <= R)), UPIR_EINVAL,
+               "SPLIT_BF16 rows must be a unit-step range inside [0, rows)");
+            ok(lp.units == 256, UPIR_EUNSUPPORTED, "SPLIT_BF16 runs with num_units 256");
+            if (ok.st) return ok.st;
+            lp.kind = LK_SPLIT;
+            SplitParams& sp = lp.sp;
+            sp.src = static_cast<const float*>(lp.bufs[0]->dev);
+            sp.hi = static_cast<uint16_t*>(lp.bufs[1]->dev);
+            sp.lo = static_cast<uint16_t*>(lp.bufs[2]->dev);
+            sp.rows = R;
+            sp.cols = C;
+            sp.lb = lp.lb;
+            sp.ub = lp.lb + lp.trip;
+            sp.transpose = lp.scalars[2] != 0.0;
+            const int64_t ntiles = ceil_div(lp.trip, 32) * ceil_div(C, 32);
+            lp.teams = T0 ? T0 : (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, kNumSMs * 8));
+            lp.skip = lp.trip == 0 || C == 0;
+            return UPIR_OK;
+        }
+        default:
+            return fail(ctx, UPIR_EINVAL, "upir_loop: unknown body");
+    }
+    if (ok.st) return ok.st;
+
+    // element engine geometry and scratch
+    ep.imod_mul = imod_mul;
+    ep.imod_mod = imod_mod;
+    ep.imod_inc = imod_inc;
+    const int64_t trip = lp.trip;
+    const int U = lp.units;
+    const int64_t V = (lp.body == UPIR_BODY_AXPY && lp.step == 1) ? lp.vec : (lp.body == UPIR_BODY_IMOD ? 4 : 1);
+    if (lp.sched == UPIR_SCHED_STATIC) {
+        if (T0) lp.teams = T0;
+        else if (lp.chunk == 0) lp.teams = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(trip, U * V), 0x7fffffff));
+        else lp.teams = default_teams_for_chunks(ceil_div(trip, lp.chunk), U);
+        if (has_red) {
+            const int64_t ng = ceil_div(lp.teams, kGroup);
+            upir_status st = alloc_scratch(ctx, lp, ng, lp.teams, &ep.sc);
+            if (st != UPIR_OK) return st;
+        }
+    } else {
+        const int64_t c = lp.chunk > 0 ? lp.chunk : 1;
+        ep.nchunks = ceil_div(trip, c);
+        if (has_red && !ok(ep.nchunks <= (1ll << 27), UPIR_EUNSUPPORTED,
+                           "dynamic reductions need at most 2^27 chunks (raise the chunk)"))
+            return ok.st;
+        lp.teams = T0 ? T0 : default_teams_for_chunks(ep.nchunks, U);
+        upir_status st = alloc_scratch(ctx, lp, 0, has_red ? ep.nchunks : 0, &ep.sc);
+        if (st != UPIR_OK) return st;
+    }
+    lp.skip = trip == 0;
+    return UPIR_OK;
+}
+
+cudaError_t launch_loop(upir_ctx ctx, LoopRec& lp, cudaStream_t s) {
+    switch (lp.kind) {
+        case LK_ELEM:
+            return launch_elem(lp.body, lp.sched == UPIR_SCHED_DYNAMIC, lp.ep.rv.fvar != nullptr,
+                               lp.ep.rv.ivar != nullptr, lp.teams, lp.units, lp.ep, s);
+        case LK_JACOBI_TMA: return launch_jacobi_tma(lp.teams, lp.units, lp.jp, &lp.tmap[0], s);
+        case LK_MATVEC: return launch_matvec(lp.teams, lp.units, lp.mp, s);
+        case LK_GEMM_F32: return launch_gemm_f32(lp.teams, lp.units, lp.gp, s);
+        case LK_SPLIT: return launch_split_bf16(lp.teams, lp.units, lp.sp, s);
+        case LK_GEMM_TC: return launch_gemm_tc_loop(ctx, lp, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace upir

@@ -1,0 +1,107 @@
+// Host-side runtime objects behind the opaque C ABI handles.
+#pragma once
+
+#include <string>
+#include <unordered_set>
+#include <memory>
+#include <vector>
+
+#include "upir_internal.h"
+
+struct upir_buf_s {
+    upir_ctx ctx = nullptr;
+    void* host = nullptr;
+    void* dev = nullptr;
+    size_t bytes = 0;
+    int kind = UPIR_MAP_TO;
+    bool wrapped = false;  // caller-owned device memory
+    bool live = true;
+    int refs = 0;          // loops of live regions that use this buffer
+};
+
+namespace upir {
+
+enum LaunchKind {
+    LK_ELEM = 0, LK_JACOBI_TMA = 1, LK_MATVEC = 2, LK_GEMM_F32 = 3, LK_SPLIT = 4, LK_GEMM_TC = 5
+};
+
+// A recorded, validated and planned loop.
+struct LoopRec {
+    int64_t lb = 0, ub = 0, step = 1, chunk = 0, trip = 0;
+    int collapse = 1, sched = 0, body = 0, nowait = 0;
+    std::vector<upir_buf> bufs;
+    std::vector<double> scalars;
+    std::vector<upir_reduction> reds;
+    int variant = 0, tile_m = 0, tile_n = 0, vec = 4;
+    int teams = 0, units = 0;
+    int kind = LK_ELEM;
+    bool skip = false;       // zero-trip loop: nothing to launch
+    bool holds_refs = false;
+    void* scratch = nullptr;
+    size_t scratch_bytes = 0;
+    size_t smem = 0;
+    ElemParams ep{};
+    JacobiParams jp{};
+    MatvecParams mp{};
+    GemmParams gp{};
+    SplitParams sp{};
+    alignas(64) CUtensorMap tmap[4];
+    int tc_variant = 0;
+};
+
+struct TimingRec {
+    cudaEvent_t a, b;
+    int body;
+};
+
+}  // namespace upir
+
+struct upir_region_s {
+    upir_ctx ctx = nullptr;
+    int teams = 0, units = 0;
+    std::vector<std::unique_ptr<upir::LoopRec>> loops;
+    cudaGraphExec_t gexec = nullptr;
+    int batch_refs = 0;
+};
+
+struct upir_ctx_s {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    upir_allocator alloc{nullptr, nullptr, nullptr};
+    std::string err;
+    std::unordered_set<upir_buf> all_bufs;
+    std::unordered_set<upir_region> regions;
+    std::unordered_set<upir_batch> batches;
+    int* err_word = nullptr;
+    long long spin_limit = 1ll << 26;
+    bool timing = false;
+    std::vector<upir::TimingRec> timings;
+    std::vector<cudaEvent_t> event_pool;
+};
+
+namespace upir {
+
+upir_status fail(upir_ctx ctx, upir_status code, const char* fmt, ...);
+upir_status cuda_fail(upir_ctx ctx, cudaError_t e, const char* what);
+void* dev_alloc(upir_ctx ctx, size_t bytes);
+void dev_free(upir_ctx ctx, void* p, size_t bytes);
+
+upir_status plan_loop(upir_region r, const upir_loop_desc* d, LoopRec& lp);
+void release_loop(upir_ctx ctx, LoopRec& lp);
+cudaError_t launch_loop(upir_ctx ctx, LoopRec& lp, cudaStream_t s);
+upir_status launch_region_loops(upir_region r, bool timed);
+upir_status capture_graph(upir_ctx ctx, const std::vector<upir_region>& regions,
+                          cudaGraphExec_t* out);
+upir_status launch_graph_timed(upir_ctx ctx, cudaGraphExec_t g, int tag);
+void destroy_region(upir_region r);
+upir_status plan_gemm_tc(upir_region r, LoopRec& lp, int64_t M, int64_t N, int64_t K, upir_status st);
+cudaError_t launch_gemm_tc_loop(upir_ctx ctx, LoopRec& lp, cudaStream_t s);
+void destroy_batch(upir_batch b);
+
+// Encode a 2D tiled TMA descriptor (row-major [rows][cols] of `elem_bytes`).
+upir_status encode_tmap_2d(upir_ctx ctx, CUtensorMap* m, const void* base, int dtype_code,
+                           int elem_bytes, uint64_t cols, uint64_t rows, uint32_t box_cols,
+                           uint32_t box_rows, int swizzle_128b);
+
+}  // namespace upir

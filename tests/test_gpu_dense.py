@@ -1,0 +1,133 @@
+"""Parity of the dense loop nests (matvec, FP32 GEMM, bfloat16 split) against
+the FP64 oracle."""
+import numpy as np
+import pytest
+
+import upir_inputs as I
+from oracle import upir_oracle as O
+
+pytestmark = pytest.mark.gpu
+
+U = pytest.importorskip("paper_2209_10643_b300")
+from upir_helpers import Session  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def s():
+    sess = Session()
+    yield sess
+    sess.close()
+
+
+def run_matvec(s, a, x, teams=0, units=0, sched=0, chunk=0, lb=0, ub=None, step=1):
+    rows, cols = a.shape
+    y = np.full(rows, -7.0, np.float32)
+    ha, hx, hy = s.map(a, U.UPIR_MAP_TO), s.map(x, U.UPIR_MAP_TO), s.map(y, U.UPIR_MAP_TOFROM)
+    s.run([dict(lb=lb, ub=rows if ub is None else ub, step=step, body=U.UPIR_BODY_MATVEC,
+                bufs=[ha, hx, hy], scalars=[rows, cols], sched=sched, chunk=chunk)], teams, units)
+    for h in (ha, hx, hy):
+        s.unmap(h)
+    return y
+
+
+def check_matvec(a, x, y):
+    ref = O.matvec(a, x)
+    absax = np.abs(a.astype(np.float64)) @ np.abs(x.astype(np.float64))
+    assert np.linalg.norm(y - ref) <= 1e-5 * np.linalg.norm(ref)
+    assert np.all(np.abs(y - ref) <= 1e-5 * absax + 1e-30)
+
+
+@pytest.mark.parametrize("rows,cols", [(1, 1), (5, 3), (33, 517), (1000, 1003), (257, 4096), (64, 20000)])
+def test_matvec_shapes(s, rows, cols):
+    a, x = I.matvec_inputs(rows, cols)
+    check_matvec(a, x, run_matvec(s, a, x))
+
+
+@pytest.mark.parametrize("teams,units,sched,chunk", [(3, 64, 0, 0), (2, 32, 0, 5), (4, 128, 1, 2), (0, 0, 1, 0)])
+def test_matvec_schedules(s, teams, units, sched, chunk):
+    a, x = I.matvec_inputs(301, 700, seed_a=11)
+    check_matvec(a, x, run_matvec(s, a, x, teams, units, sched, chunk))
+
+
+def test_matvec_exact_structured(s):
+    n = 513
+    x = (np.arange(n) - 200).astype(np.float32)
+    perm = np.random.default_rng(3).permutation(n)
+    p = np.eye(n, dtype=np.float32)[perm]
+    assert np.array_equal(run_matvec(s, p, x), x[perm])
+    ones = np.ones((7, n), np.float32)
+    assert np.all(run_matvec(s, ones, x) == float(x.astype(np.float64).sum()))
+
+
+def test_matvec_strided_rows_only_touch_their_rows(s):
+    a, x = I.matvec_inputs(100, 64)
+    y = run_matvec(s, a, x, lb=97, ub=0, step=-4)
+    rows = np.arange(97, 0, -4)
+    ref = O.matvec(a, x)
+    assert np.allclose(y[rows], ref[rows], rtol=1e-5, atol=1e-6)
+    other = np.setdiff1d(np.arange(100), rows)
+    assert np.all(y[other] == -7.0)
+
+
+def test_matvec_full_workload_16384(s):
+    a, x = I.matvec_inputs(16384, 16384)
+    check_matvec(a, x, run_matvec(s, a, x))
+
+
+def run_gemm(s, a, b, teams=0, sched=0, chunk=0, lb=0, ub=None):
+    m, k = a.shape
+    n = b.shape[1]
+    c = np.full((m, n), -3.0, np.float32)
+    ha, hb, hc = s.map(a, U.UPIR_MAP_TO), s.map(b, U.UPIR_MAP_TO), s.map(c, U.UPIR_MAP_TOFROM)
+    s.run([dict(lb=lb, ub=m if ub is None else ub, step=1, collapse=2, body=U.UPIR_BODY_GEMM_F32,
+                bufs=[ha, hb, hc], scalars=[m, n, k], sched=sched, chunk=chunk)], teams, 0)
+    for h in (ha, hb, hc):
+        s.unmap(h)
+    return c
+
+
+@pytest.mark.parametrize("m,n,k", [(1, 1, 1), (300, 200, 130), (128, 256, 64), (129, 127, 17), (1024, 1024, 1024)])
+def test_gemm_f32_vs_fp64(s, m, n, k):
+    a, b = I.gemm_inputs(m, n, k)
+    c = run_gemm(s, a, b)
+    ref = O.gemm(a, b)
+    assert np.linalg.norm(c - ref) <= 1e-5 * np.linalg.norm(ref)
+
+
+def test_gemm_f32_exact_integers_and_schedules(s):
+    a = I.small_int_matrix(200, 77, -8, 8, seed=1)
+    b = I.small_int_matrix(77, 150, -8, 8, seed=2)
+    ref = O.gemm(a, b)
+    for teams, sched, chunk in [(0, 0, 0), (3, 0, 1), (2, 1, 1)]:
+        assert np.array_equal(run_gemm(s, a, b, teams, sched, chunk), ref)
+
+
+def test_gemm_f32_full_size_sampled_and_freivalds(s):
+    a, b = I.gemm_inputs(4096, 4096, 4096)
+    c = run_gemm(s, a, b)
+    g = np.random.default_rng(12)
+    rows, cols = g.integers(0, 4096, 4096), g.integers(0, 4096, 4096)
+    ref = np.einsum("ik,ki->i", a[rows].astype(np.float64), b[:, cols].astype(np.float64))
+    assert np.linalg.norm(c[rows, cols] - ref) <= 1e-5 * np.linalg.norm(ref)
+    r = g.choice([-1.0, 1.0], 4096)
+    lhs = c.astype(np.float64) @ r
+    rhs = a.astype(np.float64) @ (b.astype(np.float64) @ r)
+    assert np.linalg.norm(lhs - rhs) <= 1e-5 * np.linalg.norm(rhs)
+
+
+@pytest.mark.parametrize("rows,cols,transpose", [(64, 96, 0), (65, 97, 1), (1, 5, 1), (300, 40, 0)])
+def test_split_bf16_bit_exact(s, rows, cols, transpose):
+    a, _ = I.gemm_inputs(rows, 4, cols)
+    hi = np.zeros(rows * cols, np.uint16)
+    lo = np.zeros(rows * cols, np.uint16)
+    hs, hh, hl = s.map(a, U.UPIR_MAP_TO), s.map(hi, U.UPIR_MAP_TOFROM), s.map(lo, U.UPIR_MAP_TOFROM)
+    s.run([dict(lb=0, ub=rows, body=U.UPIR_BODY_SPLIT_BF16, bufs=[hs, hh, hl],
+                scalars=[rows, cols, transpose])])
+    for h in (hs, hh, hl):
+        s.unmap(h)
+    wh, wl = O.split_bf16(a)
+    wh = (wh.view(np.uint32) >> 16).astype(np.uint16)
+    wl = (wl.view(np.uint32) >> 16).astype(np.uint16)
+    if transpose:
+        wh, wl = wh.T.copy(), wl.T.copy()
+    assert np.array_equal(hi, wh.ravel()) and np.array_equal(lo, wl.ravel())

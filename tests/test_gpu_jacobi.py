@@ -1,0 +1,122 @@
+"""Parity of the 5-point Jacobi sweep loops against the oracle: the field and
+the per-sweep max residual are bit-exact against the FP32 mirror (the kernel
+applies the same IEEE operations in the same order) and within 1e-5 of the
+FP64 oracle."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import upir_inputs as I
+from oracle import upir_oracle as O
+
+pytestmark = pytest.mark.gpu
+
+U = pytest.importorskip("paper_2209_10643_b300")
+from upir_helpers import Session, jacobi_loop  # noqa: E402
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+ABS_F64 = 1e-5
+
+
+@pytest.fixture(scope="module")
+def s():
+    sess = Session()
+    yield sess
+    sess.close()
+
+
+def run_sweeps(s, u0, sweeps, teams=0, units=0, hints=(), sched=0, chunk=0, graph=False):
+    rows, cols = u0.shape
+    a = u0.copy()
+    b = u0.copy()
+    res = np.full(max(sweeps, 1), -np.inf, np.float32)
+    ha, hb = s.map(a, U.UPIR_MAP_TOFROM), s.map(b, U.UPIR_MAP_TOFROM)
+    hr = s.map(res, U.UPIR_MAP_TOFROM)
+    loops = []
+    for k in range(sweeps):
+        src, dst = (ha, hb) if k % 2 == 0 else (hb, ha)
+        loops.append(jacobi_loop(src, dst, rows, cols, hres=hr, res_index=k, hints=hints,
+                                 sched=sched, chunk=chunk))
+    s.run(loops, teams, units, flags=U.UPIR_SUBMIT_GRAPH if graph else 0)
+    for h in (ha, hb, hr):
+        s.unmap(h)
+    return (a if sweeps % 2 == 0 else b), res[:sweeps]
+
+
+def test_hand_worked_5x5():
+    with open(os.path.join(GOLD, "jacobi_5x5.json")) as f:
+        g = json.load(f)
+    sess = Session()
+    try:
+        u, res = run_sweeps(sess, np.array(g["initial"], np.float32), 2)
+    finally:
+        sess.close()
+    assert np.array_equal(u.astype(np.float64), np.array(g["after_sweep_2"]))
+    assert res.tolist() == [g["residual_1"], g["residual_2"]]
+
+
+@pytest.mark.parametrize("rows,cols,sweeps,hints", [
+    (64, 64, 7, ()),
+    (131, 260, 5, ()),                                  # several tiles, ragged in both directions
+    (37, 61, 4, ()),                                    # cols % 4 != 0: per-point variant
+    (200, 516, 3, ((U.UPIR_HINT_TILE_M, 7), (U.UPIR_HINT_TILE_N, 20))),
+    (300, 300, 3, ((U.UPIR_HINT_VARIANT, 1),)),         # per-point variant forced
+    (3, 3, 2, ()), (3, 8, 2, ()), (8, 3, 2, ()),        # degenerate grids
+])
+def test_field_and_residuals_bit_exact_vs_fp32_mirror(s, rows, cols, sweeps, hints):
+    u0 = I.jacobi_grid(rows, cols, seed=1)
+    u, res = run_sweeps(s, u0, sweeps, hints=hints)
+    um, rm = O.jacobi_run(u0, sweeps, mirror_f32=True)
+    assert np.array_equal(u.view(np.uint32), um.view(np.uint32))
+    assert np.array_equal(res.view(np.uint32), rm.view(np.uint32))
+
+
+@pytest.mark.parametrize("teams,units,sched,chunk", [(5, 256, 0, 0), (3, 64, 0, 2), (7, 128, 1, 1),
+                                                     (0, 0, 1, 3), (1, 32, 0, 0)])
+def test_schedules_over_tiles(s, teams, units, sched, chunk):
+    u0 = I.jacobi_grid(150, 332, seed=4)
+    u, res = run_sweeps(s, u0, 3, teams=teams, units=units, sched=sched, chunk=chunk)
+    um, rm = O.jacobi_run(u0, 3, mirror_f32=True)
+    assert np.array_equal(u, um) and np.array_equal(res, rm)
+
+
+def test_graph_submission_matches(s):
+    u0 = I.jacobi_grid(96, 128, seed=2)
+    u, res = run_sweeps(s, u0, 6, graph=True)
+    um, rm = O.jacobi_run(u0, 6, mirror_f32=True)
+    assert np.array_equal(u, um) and np.array_equal(res, rm)
+
+
+def test_full_workload_4096_100_sweeps(s):
+    u0 = I.jacobi_grid(4096, seed=1)
+    u, res = run_sweeps(s, u0, 100)
+    um, rm = O.jacobi_run(u0, 100, mirror_f32=True)
+    assert np.array_equal(u.view(np.uint32), um.view(np.uint32))
+    assert np.array_equal(res.view(np.uint32), rm.view(np.uint32))
+    u64, r64 = O.jacobi_run(u0, 100)
+    assert np.max(np.abs(u.astype(np.float64) - u64)) <= ABS_F64
+    assert np.max(np.abs(res.astype(np.float64) - r64)) <= 4e-5
+
+
+def test_harmonic_field_fixed_point(s):
+    r, c = np.meshgrid(np.arange(40), np.arange(64), indexing="ij")
+    u0 = ((3 + 2 * r + 5 * c + r * c) * 2.0 ** -12).astype(np.float32)
+    u, res = run_sweeps(s, u0, 2)
+    assert np.array_equal(u, u0) and np.all(res == 0.0)
+
+
+def test_min_reduction_and_partial_row_range(s):
+    u0 = I.jacobi_grid(70, 72, seed=5)
+    a, b = u0.copy(), u0.copy()
+    res = np.array([np.inf], np.float32)
+    ha, hb, hr = s.map(a, U.UPIR_MAP_TO), s.map(b, U.UPIR_MAP_TOFROM), s.map(res, U.UPIR_MAP_TOFROM)
+    s.run([jacobi_loop(ha, hb, 70, 72, hres=hr, op=U.UPIR_RED_MIN, lb=10, ub=50)])
+    for h in (ha, hb, hr):
+        s.unmap(h)
+    v, _ = O.jacobi_sweep_f32(u0)
+    want = u0.copy()
+    want[10:50, 1:-1] = v[10:50, 1:-1]
+    assert np.array_equal(b, want)
+    assert res[0] == np.min(np.abs(v[10:50, 1:-1] - u0[10:50, 1:-1]))

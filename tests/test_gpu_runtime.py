@@ -1,0 +1,186 @@
+"""Runtime behaviour on the GPU: mapping semantics (§4.1), argument checks,
+ownership errors, graphs, batches, timing and the bounded device wait."""
+import numpy as np
+import pytest
+
+import upir_inputs as I
+from oracle import upir_oracle as O
+
+pytestmark = pytest.mark.gpu
+
+U = pytest.importorskip("paper_2209_10643_b300")
+from upir_helpers import Session, axpy_loop, jacobi_loop  # noqa: E402
+
+
+@pytest.fixture()
+def s():
+    sess = Session()
+    yield sess
+    sess.close()
+
+
+def test_map_kinds(s):
+    host = np.arange(8, dtype=np.float32)
+    h_to = s.map(host, U.UPIR_MAP_TO)
+    out = np.zeros(8, np.float32)
+    h_from = s.map(out, U.UPIR_MAP_FROM)
+    # y = 1 * x + y on the FROM buffer would read undefined data; copy through AXPY with a=1 on TOFROM
+    y = np.zeros(8, np.float32)
+    h_y = s.map(y, U.UPIR_MAP_TOFROM)
+    s.run([axpy_loop(h_to, h_y, 8, a=1.0)])
+    s.unmap(h_y)
+    assert np.array_equal(y, host)
+    # TO is not copied back
+    s.unmap(h_to)
+    assert np.array_equal(host, np.arange(8, dtype=np.float32))
+    s.unmap(h_from)  # FROM copies whatever the device holds; size and call must succeed
+
+
+def test_data_update_round_trip(s):
+    x = np.ones(16, np.float32)
+    y = np.zeros(16, np.float32)
+    hx, hy = s.map(x, U.UPIR_MAP_TO), s.map(y, U.UPIR_MAP_ALLOC)
+    y[:] = 5.0
+    U.upir_data_update(s.ctx, hy, U.UPIR_MAP_TO)
+    s.run([axpy_loop(hx, hy, 16, a=2.0)])
+    y[:] = 0
+    U.upir_data_update(s.ctx, hy, U.UPIR_MAP_FROM)
+    assert np.all(y == 7.0)
+    s.unmap(hx)
+    s.unmap(hy)
+
+
+def test_validation_errors(s):
+    x = np.ones(10, np.float32)
+    hx, hy = s.map(x, U.UPIR_MAP_TO), s.map(x.copy(), U.UPIR_MAP_TOFROM)
+    r = U.upir_spmd_region(s.ctx, 0, 0)
+    bad = [
+        dict(axpy_loop(hx, hy, 10), step=0),                       # step 0
+        dict(axpy_loop(hx, hy, 11)),                               # past the end of x
+        dict(axpy_loop(hx, hy, 10), chunk=-1),
+        dict(axpy_loop(hx, hy, 10), sched=7),
+        dict(axpy_loop(hx, hy, 10), body=99),
+        dict(axpy_loop(hx, hy, 10), lb=-(1 << 63), ub=(1 << 63) - 1),  # trip overflow
+        dict(axpy_loop(hx, hy, 10), hints=[(77, 1)]),
+        dict(axpy_loop(hx, hy, 10), bufs=[hx]),
+        dict(axpy_loop(hx, hy, 10), reductions=[(9, U.UPIR_F32, U.UPIR_TERM_Y, hy, 0)]),
+        dict(axpy_loop(hx, hy, 10), reductions=[(1, U.UPIR_F32, U.UPIR_TERM_Y, hy, 10)]),
+        dict(axpy_loop(hx, hy, 10), reductions=[(1, U.UPIR_I64, U.UPIR_TERM_RESID, hy, 0)]),
+    ]
+    for d in bad:
+        with pytest.raises(U.UpirError) as e:
+            U.upir_loop_checked(s.ctx, r, U.make_loop_desc(**d))
+        assert e.value.status == U.UPIR_EINVAL, d
+    with pytest.raises(U.UpirError) as e:
+        U.upir_spmd_region(s.ctx, 1, 2048)
+    assert e.value.status == U.UPIR_EINVAL
+    U.upir_region_destroy(r)
+    s.unmap(hx)
+    s.unmap(hy)
+
+
+def test_unmap_while_in_use_and_stale_handles(s):
+    x = np.ones(10, np.float32)
+    hx, hy = s.map(x, U.UPIR_MAP_TO), s.map(x.copy(), U.UPIR_MAP_TOFROM)
+    r = U.upir_spmd_region(s.ctx, 0, 0)
+    U.upir_loop_checked(s.ctx, r, U.make_loop_desc(**axpy_loop(hx, hy, 10)))
+    with pytest.raises(U.UpirError) as e:
+        U.upir_data_unmap(s.ctx, hx)
+    assert e.value.status == U.UPIR_EBUSY
+    U.upir_region_destroy(r)
+    s.unmap(hx)
+    with pytest.raises(U.UpirError) as e:
+        U.upir_data_unmap(s.ctx, hx)
+    assert e.value.status == U.UPIR_ENOTMAPPED
+    r = U.upir_spmd_region(s.ctx, 0, 0)
+    with pytest.raises(U.UpirError) as e:
+        U.upir_loop_checked(s.ctx, r, U.make_loop_desc(**axpy_loop(hx, hy, 10)))
+    assert e.value.status == U.UPIR_ENOTMAPPED
+    U.upir_region_destroy(r)
+    s.unmap(hy)
+
+
+def test_bounded_wait_times_out_and_context_survives(s):
+    U.upir_selftest_bounded_wait(s.ctx, 1 << 12)
+    with pytest.raises(U.UpirError) as e:
+        U.upir_ctx_wait(s.ctx)
+    assert e.value.status == U.UPIR_ETIMEDOUT
+    U.upir_ctx_wait(s.ctx)  # error word cleared
+    x, y = I.axpy_inputs(1000)
+    want = O.axpy(2.5, x, y)
+    hx, hy = s.map(x, U.UPIR_MAP_TO), s.map(y, U.UPIR_MAP_TOFROM)
+    s.run([axpy_loop(hx, hy, 1000)])
+    s.unmap(hx)
+    s.unmap(hy)
+    assert np.array_equal(y, want)
+
+
+def test_region_resubmit_graph_and_timing(s):
+    n = 100_000
+    x, y = I.axpy_inputs(n)
+    y0 = y.copy()
+    hx, hy = s.map(x, U.UPIR_MAP_TO), s.map(y, U.UPIR_MAP_TOFROM)
+    r = U.upir_spmd_region(s.ctx, 0, 0)
+    U.upir_loop_checked(s.ctx, r, U.make_loop_desc(**axpy_loop(hx, hy, n, a=1.0)))
+    U.upir_ctx_set_timing(s.ctx, True)
+    U.upir_region_submit(r, 0)
+    U.upir_region_submit(r, U.UPIR_SUBMIT_GRAPH)
+    U.upir_region_submit(r, U.UPIR_SUBMIT_GRAPH)
+    t = U.upir_ctx_timings(s.ctx)
+    U.upir_ctx_set_timing(s.ctx, False)
+    assert len(t) == 3 and t[0][0] == U.UPIR_BODY_AXPY and all(ms > 0 for _, ms in t)
+    U.upir_region_destroy(r)
+    s.unmap(hx)
+    s.unmap(hy)
+    want = y0
+    for _ in range(3):
+        want = O.axpy(1.0, x, want)
+    assert np.array_equal(y, want)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_batch_of_regions_equals_each_region(s, mode):
+    specs = I.batched_region_specs(12, seed=6, t_hi=2e5, max_side=300, max_rows=600, max_cols=600)
+    regions, checks, keep = [], [], []
+    for sp in specs:
+        arr = I.region_arrays(sp)
+        r = U.upir_spmd_region(s.ctx, 0, 0)
+        if sp["op"] == I.OP_AXPY_DOT:
+            dot = np.zeros(1, np.float32)
+            hx, hy, hd = s.map(arr["x"], 0), s.map(arr["y"], 2), s.map(dot, 2)
+            U.upir_loop_checked(s.ctx, r, U.make_loop_desc(**axpy_loop(
+                hx, hy, sp["n"], reds=[(U.UPIR_RED_ADD, U.UPIR_F32, U.UPIR_TERM_XY, hd, 0)])))
+            want = O.axpy(2.5, arr["x"], arr["y"])
+            checks.append(("axpy", arr, want, dot, (hx, hy, hd)))
+        elif sp["op"] == I.OP_JACOBI:
+            res = np.full(1, -np.inf, np.float32)
+            side = sp["side"]
+            h0, h1, hr = s.map(arr["u0"], 0), s.map(arr["u1"], 2), s.map(res, 2)
+            U.upir_loop_checked(s.ctx, r, U.make_loop_desc(**jacobi_loop(h0, h1, side, side, hres=hr)))
+            checks.append(("jacobi", arr, O.jacobi_sweep_f32(arr["u0"]), res, (h0, h1, hr)))
+        else:
+            y = np.zeros(sp["rows"], np.float32)
+            ha, hx, hy = s.map(arr["A"], 0), s.map(arr["x"], 0), s.map(y, 2)
+            U.upir_loop_checked(s.ctx, r, U.make_loop_desc(
+                lb=0, ub=sp["rows"], body=U.UPIR_BODY_MATVEC, bufs=[ha, hx, hy],
+                scalars=[sp["rows"], sp["cols"]]))
+            checks.append(("matvec", arr, O.matvec(arr["A"], arr["x"]), y, (ha, hx, hy)))
+        regions.append(r)
+    b = U.upir_batch_create(s.ctx, regions, mode)
+    U.upir_batch_submit(b)
+    U.upir_ctx_wait(s.ctx)
+    U.upir_batch_destroy(b)
+    for r in regions:
+        U.upir_region_destroy(r)
+    for kind, arr, want, out, hs in checks:
+        for h in hs:
+            s.unmap(h)
+        if kind == "axpy":
+            assert np.array_equal(arr["y"], want)
+            ref = O.reduce_f64(O.RED_ADD, 0.0, arr["x"].astype(np.float64) * want)
+            assert abs(out[0] - ref) <= 1e-5 * abs(ref)
+        elif kind == "jacobi":
+            v, r0 = want
+            assert np.array_equal(arr["u1"], v) and out[0] == r0
+        else:
+            assert np.linalg.norm(out - want) <= 1e-5 * np.linalg.norm(want)
