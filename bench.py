@@ -111,8 +111,11 @@ class Runtime:
         import paper_2209_10643_b300 as U
         self.U, self.torch = U, torch
         torch.cuda.set_device(device)
-        # enqueue on torch's current stream so torch events bracket the launches
-        self.ctx = U.upir_init(device, torch.cuda.current_stream().cuda_stream)
+        # a dedicated stream, made torch's current one, so that torch events and
+        # the library's launches share it (the legacy default stream has handle 0)
+        self.stream = torch.cuda.Stream(device=device)
+        torch.cuda.set_stream(self.stream)
+        self.ctx = U.upir_init(device, self.stream.cuda_stream)
         self.flush_buf = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
         self.host = []
 

@@ -207,7 +207,8 @@ typedef enum {
     UPIR_HINT_VARIANT   = 1, /* kernel variant of the body (body-specific, 0 = default)       */
     UPIR_HINT_TILE_M    = 2, /* tile rows (JACOBI5 tiled variant, GEMM)                       */
     UPIR_HINT_TILE_N    = 3, /* tile cols                                                     */
-    UPIR_HINT_VEC       = 4  /* iterations per vector access for AXPY (1 or 4)                */
+    UPIR_HINT_VEC       = 4, /* iterations per worker the planner aims for (1, 4, 8 or 16)    */
+    UPIR_HINT_STAGES    = 5  /* shared-memory pipeline depth of the tiled JACOBI5 (1..4)      */
 } upir_hint_key;
 
 /* The canonical loop with its worksharing parallelization (§3.2).

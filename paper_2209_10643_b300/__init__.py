@@ -2,8 +2,8 @@
 
 Argument marshalling only: every function here calls the C function of the same
 name and turns a negative status into ``UpirError``.  All computation runs in the
-library's CUDA kernels.  The library must be built (``python -m
-paper_2209_10643_b300.build``); importing this package without it raises
+library's CUDA kernels.  The library must be built (``python
+paper_2209_10643_b300/build.py``); importing this package without it raises
 ImportError — there is no fallback path.
 """
 from __future__ import annotations
@@ -14,7 +14,7 @@ import os
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libupir.so")
 if not os.path.exists(LIB_PATH):
-    raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_2209_10643_b300.build`")
+    raise ImportError(f"{LIB_PATH} is missing: build it with `python paper_2209_10643_b300/build.py`")
 lib = C.CDLL(LIB_PATH)
 
 # ----------------------------------------------------------------- constants --
@@ -27,7 +27,7 @@ UPIR_F32, UPIR_I64 = 0, 1
 (UPIR_BODY_AXPY, UPIR_BODY_IMOD, UPIR_BODY_JACOBI5, UPIR_BODY_MATVEC, UPIR_BODY_GEMM_F32,
  UPIR_BODY_GEMM_BF16, UPIR_BODY_GEMM_BF16X3, UPIR_BODY_COVERAGE, UPIR_BODY_SPLIT_BF16) = range(9)
 UPIR_TERM_Y, UPIR_TERM_XY, UPIR_TERM_IMOD, UPIR_TERM_IV, UPIR_TERM_RESID = range(5)
-UPIR_HINT_VARIANT, UPIR_HINT_TILE_M, UPIR_HINT_TILE_N, UPIR_HINT_VEC = 1, 2, 3, 4
+UPIR_HINT_VARIANT, UPIR_HINT_TILE_M, UPIR_HINT_TILE_N, UPIR_HINT_VEC, UPIR_HINT_STAGES = 1, 2, 3, 4, 5
 UPIR_SYNC_BARRIER, UPIR_SYNC_TASKWAIT = 0, 1
 UPIR_SUBMIT_GRAPH = 1
 UPIR_BATCH_LAUNCHES, UPIR_BATCH_GRAPH, UPIR_BATCH_PERSISTENT = 0, 1, 2

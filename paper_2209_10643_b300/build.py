@@ -5,7 +5,7 @@ it or a header is newer than its object) and the objects are linked into
 ``paper_2209_10643_b300/libupir.so`` with the CUDA runtime linked statically,
 so the library loads without a CUDA runtime library on the path.
 
-    python -m paper_2209_10643_b300.build [--force] [--verbose]
+    python paper_2209_10643_b300/build.py [--force] [--verbose] [--ptxas-v]
 """
 from __future__ import annotations
 

@@ -4,6 +4,7 @@
 #pragma once
 
 #include <cstdint>
+#include <utility>
 #include <cuda_runtime.h>
 #include "upir_internal.h"
 
@@ -173,70 +174,6 @@ __device__ __forceinline__ void write_reduction_vars(const RedVars& rv, const Pa
     if (rv.ivar) *rv.ivar = iacc_combine(*rv.ivar, fin.i, rv.iop);
 }
 
-// Static schedules: block partial -> slot blockIdx.x; the last block of each
-// group of kGroup blocks folds its group, the last group folds the groups.
-// The counters are returned to zero by the blocks that finish with them.
-__device__ __forceinline__ void finish_static(const RedVars& rv, const Scratch& sc,
-                                              const Partial& block_p) {
-    __shared__ int last_in_group, last_overall;
-    const int64_t nblocks = gridDim.x;
-    const int64_t b = blockIdx.x;
-    const int64_t g = b / kGroup;
-    const int64_t ngroups = (nblocks + kGroup - 1) / kGroup;
-    if (threadIdx.x == 0) {
-        sc.partials[b] = block_p;
-        __threadfence();
-        const unsigned gsize = (unsigned)(kGroup < nblocks - g * kGroup ? (int64_t)kGroup : nblocks - g * kGroup);
-        const unsigned t = atomicAdd(sc.group_tickets + g, 1u);
-        last_in_group = (t == gsize - 1);
-    }
-    __syncthreads();
-    if (!last_in_group) return;
-    __threadfence();
-    const int64_t gsize = (kGroup < nblocks - g * kGroup ? (int64_t)kGroup : nblocks - g * kGroup);
-    const Partial gp = block_reduce_slots(sc.partials + g * kGroup, gsize, rv.fop, rv.iop);
-    if (threadIdx.x == 0) {
-        sc.group_tickets[g] = 0;
-        sc.group_partials[g] = gp;
-        __threadfence();
-        const unsigned t = atomicAdd(sc.ticket, 1u);
-        last_overall = (t == (unsigned)ngroups - 1);
-    }
-    __syncthreads();
-    if (!last_overall) return;
-    __threadfence();
-    const Partial fin = block_reduce_slots(sc.group_partials, ngroups, rv.fop, rv.iop);
-    if (threadIdx.x == 0) {
-        *sc.ticket = 0;
-        write_reduction_vars(rv, fin);
-    }
-}
-
-// Dynamic schedules: partials are per chunk (written by the thread that ran
-// the chunk); the last block to finish folds all chunk slots in index order
-// and resets the chunk counter.
-__device__ __forceinline__ void finish_dynamic(const RedVars& rv, const Scratch& sc,
-                                               int64_t nchunks, bool has_red) {
-    __shared__ int last;
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        const unsigned t = atomicAdd(sc.ticket, 1u);
-        last = (t == gridDim.x - 1);
-    }
-    __syncthreads();
-    if (!last) return;
-    __threadfence();
-    if (has_red) {
-        const Partial fin = block_reduce_slots(sc.partials, nchunks, rv.fop, rv.iop);
-        if (threadIdx.x == 0) write_reduction_vars(rv, fin);
-    }
-    if (threadIdx.x == 0) {
-        *sc.ticket = 0;
-        *sc.chunk_counter = 0;
-    }
-}
-
 // Warp-aggregated claim of the next dynamic chunk: the active lanes take
 // consecutive tickets with one atomic.
 __device__ __forceinline__ unsigned long long claim_chunk(unsigned long long* counter) {
@@ -257,19 +194,48 @@ __device__ __forceinline__ unsigned long long claim_chunk(unsigned long long* co
 // ----------------------------------------------------------------------------
 
 template <class F>
-__device__ __forceinline__ void static_ranges(int64_t trip, int64_t chunk, int64_t W,
-                                              int64_t w, F&& f) {
+__device__ __forceinline__ void static_ranges(const SchedConst& sk, int64_t trip, int64_t chunk,
+                                              int64_t W, int64_t w, F&& f) {
     if (chunk > 0) {
-        for (int64_t j = w; j < (trip + chunk - 1) / chunk; j += W) {
+        for (int64_t j = w; j < sk.nchunks; j += W) {
             const int64_t k0 = j * chunk;
             f(k0, min(k0 + chunk, trip));
         }
     } else {
-        const int64_t base = trip / W, extra = trip % W;
-        const int64_t start = w * base + min(w, extra);
-        const int64_t len = base + (w < extra ? 1 : 0);
+        const int64_t start = w * sk.base + min(w, sk.extra);
+        const int64_t len = sk.base + (w < sk.extra ? 1 : 0);
         if (len > 0) f(start, start + len);
     }
+}
+
+// Programmatic dependent launch (PTX griddepcontrol): a kernel launched with
+// programmatic stream serialization may start while the previous kernel of
+// the stream drains; ``griddep_wait`` blocks until that kernel has completed
+// and its memory is visible (the implicit barrier after a worksharing loop).
+__device__ __forceinline__ void griddep_wait() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+__device__ __forceinline__ void griddep_launch_dependents() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// Launch with programmatic stream serialization, so the kernel's launch and
+// prologue overlap the tail of the previous kernel on the stream.
+template <typename... Exp, typename... Act>
+inline cudaError_t launch_pdl(void (*kern)(Exp...), dim3 grid, dim3 block, size_t smem,
+                              cudaStream_t s, Act&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, std::forward<Act>(args)...);
 }
 
 // ----------------------------------------------------------------------------

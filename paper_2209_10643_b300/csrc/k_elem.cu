@@ -1,185 +1,99 @@
-// Element-granular worksharing loops: the worker is one SPMD unit (a thread),
-// the work item one iteration of the canonical loop (§3.2).  Bodies: AXPY
-// (§6), the empty IMOD body (reduction terms only), the COVERAGE
-// instrumentation body and the per-point 5-point Jacobi sweep.
-#include "device_common.cuh"
+// Element-granular loop kernels other than AXPY (IMOD, COVERAGE, per-point
+// JACOBI5), the reduction finalize kernel and the dispatch of all of them.
+#include "elem_kernel.cuh"
 
 namespace upir {
 
 namespace {
 
-__device__ __forceinline__ long long imod_first(long long mul, long long iv, long long m) {
-    const long long r = (mul * iv) % m;  // the runtime rejects products that overflow
-    return r < 0 ? r + m : r;
-}
-
-__device__ __forceinline__ long long imod_next(long long t, long long inc, long long m) {
-    t += inc;
-    return t >= m ? t - m : t;
-}
-
-// Per-thread accumulation state of the loop's reduction clauses.
-struct Terms {
-    FAcc f;
-    long long i;
-    long long imod;  // (mul * iv) mod m of the current iteration
-};
-
-template <bool HI>
-__device__ __forceinline__ void add_int_term(const ElemParams& p, Terms& t, int64_t iv) {
-    if (HI) {
-        const long long v = p.rv.iterm == UPIR_TERM_IMOD ? t.imod : (long long)iv;
-        t.i = iacc_combine(t.i, v, p.rv.iop);
-        if (p.rv.iterm == UPIR_TERM_IMOD) t.imod = imod_next(t.imod, p.imod_inc, p.imod_mod);
-    }
-}
-
-template <bool HF, bool HI>
-__device__ __forceinline__ void axpy_one(const ElemParams& p, Terms& t, int64_t iv) {
-    const float xv = p.x[iv];
-    const float yn = __fmaf_rn(p.a, xv, p.y[iv]);
-    p.y[iv] = yn;
-    if (HF) {
-        if (p.rv.fterm == UPIR_TERM_Y) {
-            facc_add(t.f, yn, p.rv.fop);
-        } else {  // x * y, with the exact product error (TwoProduct via FMA)
-            const float pr = __fmul_rn(xv, yn);
-            facc_add(t.f, pr, p.rv.fop, __fmaf_rn(xv, yn, -pr));
+// Deterministic finalization of a loop's reductions (the reduction sync fused
+// with the loop's closing barrier, §3.1.2): block g folds partial slots
+// [g * kFinSeg, (g + 1) * kFinSeg) in a fixed order; with several blocks the
+// last one to finish (atomic ticket) folds the group results in index order,
+// combines them with the variables' values before the loop and stores them.
+// It runs after the loop kernel completes (programmatic dependent launch +
+// griddepcontrol.wait) and also returns the dynamic chunk counter to zero.
+__global__ void __launch_bounds__(256) finalize_kernel(const RedVars rv, const Scratch sc,
+                                                       int64_t nslots, int reset_counter) {
+    __shared__ int last;
+    griddep_wait();
+    const int64_t G = gridDim.x, g = blockIdx.x;
+    const int64_t s0 = g * kFinSeg;
+    const int64_t rem = nslots - s0;
+    const int64_t n = rem <= 0 ? 0 : (rem < kFinSeg ? rem : (int64_t)kFinSeg);
+    const Partial gp = block_reduce_slots(sc.partials + s0, n, rv.fop, rv.iop);
+    if (G == 1) {
+        if (threadIdx.x == 0) {
+            write_reduction_vars(rv, gp);
+            if (reset_counter) *sc.chunk_counter = 0;
         }
-    }
-    add_int_term<HI>(p, t, iv);
-}
-
-template <bool HF, bool HI>
-__device__ __forceinline__ void axpy_range(const ElemParams& p, Terms& t, int64_t k0, int64_t k1) {
-    if (p.step != 1) {
-        for (int64_t k = k0; k < k1; ++k) axpy_one<HF, HI>(p, t, p.lb + k * p.step);
         return;
     }
-    int64_t i = p.lb + k0;
-    const int64_t iend = p.lb + k1;
-    const bool same_phase =
-        ((reinterpret_cast<uintptr_t>(p.x + i) ^ reinterpret_cast<uintptr_t>(p.y + i)) & 15) == 0;
-    if (same_phase) {
-        while (i < iend && (reinterpret_cast<uintptr_t>(p.x + i) & 15)) axpy_one<HF, HI>(p, t, i++);
-        for (; i + 4 <= iend; i += 4) {
-            const float4 xv = __ldcs(reinterpret_cast<const float4*>(p.x + i));
-            const float4 yv = __ldcs(reinterpret_cast<const float4*>(p.y + i));
-            float4 yn;
-            yn.x = __fmaf_rn(p.a, xv.x, yv.x);
-            yn.y = __fmaf_rn(p.a, xv.y, yv.y);
-            yn.z = __fmaf_rn(p.a, xv.z, yv.z);
-            yn.w = __fmaf_rn(p.a, xv.w, yv.w);
-            __stcs(reinterpret_cast<float4*>(p.y + i), yn);
-            if (HF) {
-                const float xs[4] = {xv.x, xv.y, xv.z, xv.w};
-                const float ys[4] = {yn.x, yn.y, yn.z, yn.w};
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    if (p.rv.fterm == UPIR_TERM_Y) {
-                        facc_add(t.f, ys[j], p.rv.fop);
-                    } else {
-                        const float pr = __fmul_rn(xs[j], ys[j]);
-                        facc_add(t.f, pr, p.rv.fop, __fmaf_rn(xs[j], ys[j], -pr));
-                    }
-                }
-            }
-            if (HI) {
-#pragma unroll
-                for (int j = 0; j < 4; ++j) add_int_term<HI>(p, t, i + j);
-            }
-        }
+    if (threadIdx.x == 0) {
+        sc.group_partials[g] = gp;
+        __threadfence();
+        last = atomicAdd(sc.ticket, 1u) == (unsigned)G - 1;
     }
-    while (i < iend) axpy_one<HF, HI>(p, t, i++);
-}
-
-template <bool HF>
-__device__ __forceinline__ void jacobi_point(const ElemParams& p, Terms& t, int64_t k) {
-    const int64_t inner = p.cols - 2;
-    const int64_t r = p.lb + k / inner, c = 1 + k % inner;
-    const float* u = p.uin;
-    const int64_t at = r * p.cols + c;
-    const float ns = __fadd_rn(u[at - p.cols], u[at + p.cols]);
-    const float we = __fadd_rn(u[at - 1], u[at + 1]);
-    const float v = __fmul_rn(0.25f, __fadd_rn(ns, we));
-    p.uout[at] = v;
-    if (HF) facc_add(t.f, fabsf(__fsub_rn(v, u[at])), p.rv.fop);
-}
-
-template <int BODY, bool HF, bool HI>
-__device__ __forceinline__ void body_range(const ElemParams& p, Terms& t, int64_t k0, int64_t k1,
-                                           int64_t worker) {
-    if (k0 >= k1) return;
-    if (HI && p.rv.iterm == UPIR_TERM_IMOD)
-        t.imod = imod_first(p.imod_mul, p.lb + k0 * p.step, p.imod_mod);
-    if (BODY == UPIR_BODY_AXPY) {
-        axpy_range<HF, HI>(p, t, k0, k1);
-    } else if (BODY == UPIR_BODY_JACOBI5) {
-        for (int64_t k = k0; k < k1; ++k) jacobi_point<HF>(p, t, k);
-    } else if (BODY == UPIR_BODY_COVERAGE) {
-        for (int64_t k = k0; k < k1; ++k) {
-            p.owner[k] = worker;
-            atomicAdd(p.count + k, 1ull);
-            add_int_term<HI>(p, t, p.lb + k * p.step);
-        }
-    } else {  // IMOD: reduction terms only
-        for (int64_t k = k0; k < k1; ++k) add_int_term<HI>(p, t, p.lb + k * p.step);
-    }
-}
-
-template <int BODY, bool DYN, bool HF, bool HI>
-__global__ void __launch_bounds__(1024, 1) elem_kernel(const ElemParams p) {
-    constexpr bool HR = HF || HI;
-    const int64_t W = (int64_t)gridDim.x * blockDim.x;
-    const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (!DYN) {
-        Terms t{facc_identity(p.rv.fop), iacc_identity(p.rv.iop), 0};
-        static_ranges(p.trip, p.chunk, W, w,
-                      [&](int64_t k0, int64_t k1) { body_range<BODY, HF, HI>(p, t, k0, k1, w); });
-        if (HR) {
-            const Partial bp = block_reduce_partial(make_partial(t.f, t.i), p.rv.fop, p.rv.iop);
-            finish_static(p.rv, p.sc, bp);
-        }
-    } else {
-        const int64_t c = p.chunk > 0 ? p.chunk : 1;
-        for (;;) {
-            const int64_t k = (int64_t)claim_chunk(p.sc.chunk_counter);
-            if (k >= p.nchunks) break;
-            Terms t{facc_identity(p.rv.fop), iacc_identity(p.rv.iop), 0};
-            body_range<BODY, HF, HI>(p, t, k * c, min(k * c + c, p.trip), w);
-            if (HR) p.sc.partials[k] = make_partial(t.f, t.i);
-        }
-        finish_dynamic(p.rv, p.sc, p.nchunks, HR);
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    const Partial fin = block_reduce_slots(sc.group_partials, G, rv.fop, rv.iop);
+    if (threadIdx.x == 0) {
+        write_reduction_vars(rv, fin);
+        *sc.ticket = 0;
+        if (reset_counter) *sc.chunk_counter = 0;
     }
 }
 
 template <int BODY, bool DYN>
-cudaError_t launch_3(bool hf, bool hi, int teams, int units, const ElemParams& p, cudaStream_t s) {
-    if (hf && hi) elem_kernel<BODY, DYN, true, true><<<teams, units, 0, s>>>(p);
-    else if (hf) elem_kernel<BODY, DYN, true, false><<<teams, units, 0, s>>>(p);
-    else if (hi) elem_kernel<BODY, DYN, false, true><<<teams, units, 0, s>>>(p);
-    else elem_kernel<BODY, DYN, false, false><<<teams, units, 0, s>>>(p);
-    return cudaGetLastError();
-}
-
-template <int BODY>
-cudaError_t launch_2(bool dyn, bool hf, bool hi, int teams, int units, const ElemParams& p,
-                     cudaStream_t s) {
-    return dyn ? launch_3<BODY, true>(hf, hi, teams, units, p, s)
-               : launch_3<BODY, false>(hf, hi, teams, units, p, s);
+cudaError_t launch_fop(int fop, int iop, int teams, int units, const ElemParams& p, cudaStream_t s) {
+    switch (fop) {
+        case 0: return launch_elem_iop<BODY, DYN, 0>(iop, teams, units, p, s);
+        case UPIR_RED_ADD: return launch_elem_iop<BODY, DYN, UPIR_RED_ADD>(iop, teams, units, p, s);
+        case UPIR_RED_MUL: return launch_elem_iop<BODY, DYN, UPIR_RED_MUL>(iop, teams, units, p, s);
+        case UPIR_RED_MAX: return launch_elem_iop<BODY, DYN, UPIR_RED_MAX>(iop, teams, units, p, s);
+        case UPIR_RED_MIN: return launch_elem_iop<BODY, DYN, UPIR_RED_MIN>(iop, teams, units, p, s);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 }  // namespace
 
-cudaError_t launch_elem(int body, bool dyn, bool hf, bool hi, int teams, int units,
-                        const ElemParams& p, cudaStream_t s) {
+cudaError_t launch_axpy_main(bool dyn, int fop, int iop, int teams, int units, const ElemParams& p,
+                             cudaStream_t s);
+
+int64_t finalize_groups(int64_t nslots) { return nslots > 0 ? (nslots + kFinSeg - 1) / kFinSeg : 1; }
+
+cudaError_t launch_finalize(const RedVars& rv, const Scratch& sc, int64_t nslots, bool reset_counter,
+                            cudaStream_t s) {
+    return launch_pdl(finalize_kernel, (unsigned)finalize_groups(nslots), 256, 0, s, rv, sc, nslots,
+                      reset_counter ? 1 : 0);
+}
+
+cudaError_t launch_elem_main(int body, bool dyn, int fop, int iop, int teams, int units,
+                             const ElemParams& p, cudaStream_t s) {
     switch (body) {
-        case UPIR_BODY_AXPY: return launch_2<UPIR_BODY_AXPY>(dyn, hf, hi, teams, units, p, s);
-        case UPIR_BODY_IMOD: return launch_2<UPIR_BODY_IMOD>(dyn, hf, hi, teams, units, p, s);
-        case UPIR_BODY_COVERAGE: return launch_2<UPIR_BODY_COVERAGE>(dyn, hf, hi, teams, units, p, s);
-        case UPIR_BODY_JACOBI5: return launch_2<UPIR_BODY_JACOBI5>(dyn, hf, false, teams, units, p, s);
+        case UPIR_BODY_AXPY: return launch_axpy_main(dyn, fop, iop, teams, units, p, s);
+        case UPIR_BODY_IMOD:
+            return dyn ? launch_elem_iop<UPIR_BODY_IMOD, true, 0>(iop, teams, units, p, s)
+                       : launch_elem_iop<UPIR_BODY_IMOD, false, 0>(iop, teams, units, p, s);
+        case UPIR_BODY_COVERAGE:
+            return dyn ? launch_elem_iop<UPIR_BODY_COVERAGE, true, 0>(iop, teams, units, p, s)
+                       : launch_elem_iop<UPIR_BODY_COVERAGE, false, 0>(iop, teams, units, p, s);
+        case UPIR_BODY_JACOBI5:
+            return dyn ? launch_fop<UPIR_BODY_JACOBI5, true>(fop, 0, teams, units, p, s)
+                       : launch_fop<UPIR_BODY_JACOBI5, false>(fop, 0, teams, units, p, s);
         default: return cudaErrorInvalidValue;
     }
+}
+
+cudaError_t launch_elem(int body, bool dyn, int fop, int iop, int teams, int units,
+                        const ElemParams& p, cudaStream_t s) {
+    cudaError_t e = launch_elem_main(body, dyn, fop, iop, teams, units, p, s);
+    if (e != cudaSuccess) return e;
+    if (fop || iop) return launch_finalize(p.rv, p.sc, dyn ? p.nchunks : teams, dyn, s);
+    if (dyn) return launch_finalize(p.rv, p.sc, 0, true, s);
+    return cudaSuccess;
 }
 
 }  // namespace upir

@@ -114,7 +114,7 @@ __global__ void __launch_bounds__(256) gemm_f32_kernel(const GemmParams p) {
             }
         }
     } else {
-        static_ranges(ntiles, p.chunk, gridDim.x, blockIdx.x, [&](int64_t t0, int64_t t1) {
+        static_ranges(p.sk, ntiles, p.chunk, gridDim.x, blockIdx.x, [&](int64_t t0, int64_t t1) {
             for (int64_t tile = t0; tile < t1; ++tile) do_tile(tile);
         });
     }

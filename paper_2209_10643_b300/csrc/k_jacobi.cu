@@ -2,11 +2,14 @@
 // The canonical loop collapse(2) over the interior is tiled by the runtime
 // (tiling is one of the loop transformations the separation of loop and
 // loop_parallel allows, §3.2) and the tile loop is workshared over teams.
-// Each team stages a (TM + 2) x (TN + 8) halo box of u_in into shared memory
-// with one TMA copy, computes TM x TN points from it and writes them with
-// 128-bit stores.  The per-sweep max-norm residual is folded into the
-// reduction variable with one atomic per team (max/min are exact in any
-// order, so the result does not depend on the team order).
+//
+// Each team walks its tiles through an S-deep shared-memory ring: one thread
+// issues the TMA copy of the (TM + 2) x (TN + 8) halo box of the tile S - 1
+// positions ahead, while all threads compute the current tile (TM x TN points,
+// 128-bit shared loads, 128-bit streaming global stores).  The per-sweep
+// max-norm residual is folded into the reduction variable with one atomic per
+// team; max/min are exact in any order, so the result does not depend on
+// which team finishes first.
 #include <cstring>
 
 #include "device_common.cuh"
@@ -51,145 +54,240 @@ __device__ __forceinline__ float block_fold(float v, int op) {
     return v;  // valid in thread 0
 }
 
+// The sequence of tiles one team owns under the loop's schedule, produced on
+// demand by the single thread that issues the copies.
+struct TileIter {
+    int64_t next, end;  // current contiguous run [next, end)
+    int64_t chunk_j;    // static chunked: next chunk index
+    bool done;
+};
+
+__device__ __forceinline__ int64_t tile_iter_next(TileIter& it, const JacobiParams& p) {
+    for (;;) {
+        if (it.done) return -1;
+        if (it.next < it.end) return it.next++;
+        if (p.sched == UPIR_SCHED_DYNAMIC) {
+            const int64_t c = p.chunk > 0 ? p.chunk : 1;
+            const int64_t j = (int64_t)atomicAdd(p.sc.chunk_counter, 1ull);
+            if (j * c >= p.ntiles) {
+                it.done = true;
+                return -1;
+            }
+            it.next = j * c;
+            it.end = min(j * c + c, p.ntiles);
+        } else if (p.chunk > 0) {
+            if (it.chunk_j >= p.sk.nchunks) {
+                it.done = true;
+                return -1;
+            }
+            it.next = it.chunk_j * p.chunk;
+            it.end = min(it.next + p.chunk, p.ntiles);
+            it.chunk_j += gridDim.x;
+        } else {
+            it.done = true;  // the blocked run was set up front
+            return -1;
+        }
+    }
+}
+
+template <int S, int ROP>
 __global__ void __launch_bounds__(1024) jacobi_tma_kernel(const JacobiParams p,
                                                          const __grid_constant__ CUtensorMap tmap) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    // the TMA destination starts on a 1024-byte boundary (the launch adds 1 KB of slack)
-    float* tile = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    __shared__ __align__(8) uint64_t bar;
-    __shared__ int64_t next_tile;
+    __shared__ __align__(8) uint64_t bar[S];
+    __shared__ int2 stage_rc[S];  // (first row, first column) of the tile in each stage; x < 0: none
+    __shared__ int last_team;
     const int TM = p.tile_m, TN = p.tile_n, SW = TN + 8;
+    const int stage_floats = ((TM + 2) * SW + 255) / 256 * 256;  // 1 KB multiples
+    // stage 0 starts on a 1024-byte boundary (the launch adds 1 KB of slack)
+    float* ring = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const int tpr = TN / 4;                    // threads per tile row (4 columns each)
     const int tx = threadIdx.x % tpr, ty = threadIdx.x / tpr;
     const int nty = blockDim.x / tpr;          // thread rows
     const bool active = threadIdx.x < nty * tpr;
     const uint32_t box_bytes = (uint32_t)((TM + 2) * SW * sizeof(float));
-    const bool has_red = p.rvar != nullptr;
-    float racc = p.rop == UPIR_RED_MIN ? __int_as_float(0x7f800000) : -__int_as_float(0x7f800000);
+    const int cols = (int)p.cols, r_ub = (int)p.r_ub;
+    float racc = ROP == UPIR_RED_MIN ? __int_as_float(0x7f800000) : -__int_as_float(0x7f800000);
+
+    TileIter it{0, 0, (int64_t)blockIdx.x, false};
+    if (p.sched == UPIR_SCHED_STATIC && p.chunk == 0) {
+        const int64_t w = blockIdx.x;
+        it.next = w * p.sk.base + min(w, p.sk.extra);
+        it.end = it.next + p.sk.base + (w < p.sk.extra ? 1 : 0);
+    }
+    // producer side (one thread): next tile -> (row, column), then its copy
+    auto issue_next = [&](int s) {
+        const int64_t t = tile_iter_next(it, p);
+        if (t < 0) {
+            stage_rc[s] = make_int2(-1, -1);
+            return;
+        }
+        const int tr = (int)(t / p.tiles_c), tc = (int)(t - (int64_t)tr * p.tiles_c);
+        const int r0 = (int)p.r_lb + tr * TM, c0 = tc * TN;
+        stage_rc[s] = make_int2(r0, c0);
+        mbar_arrive_expect_tx(&bar[s], box_bytes);
+        tma_load_2d(ring + s * stage_floats, &tmap, &bar[s], c0 - 4, r0 - 1);
+    };
 
     if (threadIdx.x == 0) {
         prefetch_tmap(&tmap);
-        mbar_init(&bar, 1);
+#pragma unroll
+        for (int s = 0; s < S; ++s) mbar_init(&bar[s], 1);
         fence_mbar_init();
     }
+    // the previous sweep's output is this sweep's input: wait for it
+    if (p.wait_prior) griddep_wait();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int s = 0; s < S; ++s) issue_next(s);
+    }
     __syncthreads();
-    uint32_t phase = 0;
-    bool failed = false;
+    griddep_launch_dependents();
 
-    auto do_tile = [&](int64_t t) -> bool {
-        const int64_t tr = t / p.tiles_c, tc = t % p.tiles_c;
-        const int64_t r0 = p.r_lb + tr * TM;
-        const int64_t c0 = tc * TN;
-        if (threadIdx.x == 0) {
-            mbar_arrive_expect_tx(&bar, box_bytes);
-            tma_load_2d(tile, &tmap, &bar, (int32_t)(c0 - 4), (int32_t)(r0 - 1));
+    bool failed = false;
+    int s = 0;
+    uint32_t parity = 0;
+    for (;;) {
+        const int2 rc = stage_rc[s];
+        if (rc.x < 0) break;
+        if (!__syncthreads_and(mbar_wait_bounded(&bar[s], parity, p.spin_limit, p.err_word))) {
+            failed = true;
+            break;
         }
-        const bool ok = __syncthreads_and(mbar_wait_bounded(&bar, phase, p.spin_limit, p.err_word));
-        phase ^= 1u;
-        if (!ok) return false;
         if (active) {
-            const int64_t rend = min(r0 + TM, p.r_ub);
-            for (int i = ty; r0 + i < rend; i += nty) {
-                const float* cen = tile + (i + 1) * SW + 4 + 4 * tx;
+            const float* cen = ring + s * stage_floats + (ty + 1) * SW + 4 + 4 * tx;
+            const int c = rc.y + 4 * tx;
+            const bool full = c >= 1 && c + 3 <= cols - 2;
+            const int nrows = min(TM, r_ub - rc.x);
+            float* out = p.uout + (size_t)(rc.x + ty) * cols + c;
+            const size_t out_step = (size_t)nty * cols;
+#pragma unroll 4
+            for (int i2 = ty; i2 < nrows; i2 += nty, cen += nty * SW, out += out_step) {
                 const float4 C = *reinterpret_cast<const float4*>(cen);
                 const float4 N = *reinterpret_cast<const float4*>(cen - SW);
-                const float4 S = *reinterpret_cast<const float4*>(cen + SW);
+                const float4 Sv = *reinterpret_cast<const float4*>(cen + SW);
                 const float Wl = cen[-1], Er = cen[4];
                 float4 v;
-                v.x = __fmul_rn(0.25f, __fadd_rn(__fadd_rn(N.x, S.x), __fadd_rn(Wl, C.y)));
-                v.y = __fmul_rn(0.25f, __fadd_rn(__fadd_rn(N.y, S.y), __fadd_rn(C.x, C.z)));
-                v.z = __fmul_rn(0.25f, __fadd_rn(__fadd_rn(N.z, S.z), __fadd_rn(C.y, C.w)));
-                v.w = __fmul_rn(0.25f, __fadd_rn(__fadd_rn(N.w, S.w), __fadd_rn(C.z, Er)));
-                const int64_t c = c0 + 4 * tx;
-                const int64_t r = r0 + i;
-                float* out = p.uout + r * p.cols + c;
-                if (c >= 1 && c + 3 <= p.cols - 2) {
+                v.x = __fmul_rn(0.25f, __fadd_rn(__fadd_rn(N.x, Sv.x), __fadd_rn(Wl, C.y)));
+                v.y = __fmul_rn(0.25f, __fadd_rn(__fadd_rn(N.y, Sv.y), __fadd_rn(C.x, C.z)));
+                v.z = __fmul_rn(0.25f, __fadd_rn(__fadd_rn(N.z, Sv.z), __fadd_rn(C.y, C.w)));
+                v.w = __fmul_rn(0.25f, __fadd_rn(__fadd_rn(N.w, Sv.w), __fadd_rn(C.z, Er)));
+                if (full) {
                     __stcs(reinterpret_cast<float4*>(out), v);
-                    if (has_red) {
-                        racc = fold(racc, fabsf(__fsub_rn(v.x, C.x)), p.rop);
-                        racc = fold(racc, fabsf(__fsub_rn(v.y, C.y)), p.rop);
-                        racc = fold(racc, fabsf(__fsub_rn(v.z, C.z)), p.rop);
-                        racc = fold(racc, fabsf(__fsub_rn(v.w, C.w)), p.rop);
+                    if (ROP) {
+                        racc = fold(racc, fabsf(__fsub_rn(v.x, C.x)), ROP);
+                        racc = fold(racc, fabsf(__fsub_rn(v.y, C.y)), ROP);
+                        racc = fold(racc, fabsf(__fsub_rn(v.z, C.z)), ROP);
+                        racc = fold(racc, fabsf(__fsub_rn(v.w, C.w)), ROP);
                     }
                 } else {
                     const float vs[4] = {v.x, v.y, v.z, v.w};
                     const float cs[4] = {C.x, C.y, C.z, C.w};
 #pragma unroll
                     for (int j = 0; j < 4; ++j) {
-                        if (c + j >= 1 && c + j <= p.cols - 2) {
+                        if (c + j >= 1 && c + j <= cols - 2) {
                             out[j] = vs[j];
-                            if (has_red) racc = fold(racc, fabsf(__fsub_rn(vs[j], cs[j])), p.rop);
+                            if (ROP) racc = fold(racc, fabsf(__fsub_rn(vs[j], cs[j])), ROP);
                         }
                     }
                 }
             }
         }
-        __syncthreads();  // the next copy overwrites the tile
-        return true;
-    };
-
-    if (p.sched == UPIR_SCHED_DYNAMIC) {
-        const int64_t c = p.chunk > 0 ? p.chunk : 1;
-        const int64_t nchunks = (p.ntiles + c - 1) / c;
-        for (;;) {
-            if (threadIdx.x == 0) next_tile = (int64_t)atomicAdd(p.sc.chunk_counter, 1ull);
-            __syncthreads();
-            const int64_t j = next_tile;
-            __syncthreads();
-            if (j >= nchunks) break;
-            for (int64_t t = j * c; t < min(j * c + c, p.ntiles) && !failed; ++t) failed = !do_tile(t);
-            if (failed) break;
+        __syncthreads();  // every thread is done with stage s
+        if (threadIdx.x == 0) issue_next(s);
+        __syncthreads();  // stage_rc[s] is read again (at once when S == 1)
+        if (++s == S) {
+            s = 0;
+            parity ^= 1u;
         }
-    } else {
-        static_ranges(p.ntiles, p.chunk, gridDim.x, blockIdx.x, [&](int64_t t0, int64_t t1) {
-            for (int64_t t = t0; t < t1 && !failed; ++t) failed = !do_tile(t);
-        });
     }
 
-    if (has_red && !failed) {
-        const float b = block_fold(racc, p.rop);
-        if (threadIdx.x == 0) atomic_fold_minmax(p.rvar, b, p.rop);
+    if (ROP && !failed) {
+        const float b = block_fold(racc, ROP);
+        if (threadIdx.x == 0) atomic_fold_minmax(p.rvar, b, ROP);
     }
     if (p.sched == UPIR_SCHED_DYNAMIC) {
         // the last team returns the tile counter to zero for the next launch
-        __shared__ int last;
         __syncthreads();
         if (threadIdx.x == 0) {
             __threadfence();
-            last = atomicAdd(p.sc.ticket, 1u) == gridDim.x - 1;
-            if (last) {
+            last_team = atomicAdd(p.sc.ticket, 1u) == gridDim.x - 1;
+            if (last_team) {
                 *p.sc.ticket = 0;
                 *p.sc.chunk_counter = 0;
             }
         }
     }
     if (failed && threadIdx.x == 0) {
-        // give a copy still in flight a bounded chance to land before the
+        // copies still in flight get a bounded chance to land before the
         // shared memory is released
-        mbar_wait_bounded(&bar, phase ^ 1u, p.spin_limit, nullptr);
+        for (int k = 0; k < S; ++k) {
+            if (stage_rc[k].x < 0) continue;
+            if (!mbar_wait_bounded(&bar[k], 0, p.spin_limit, nullptr))
+                mbar_wait_bounded(&bar[k], 1, p.spin_limit, nullptr);
+        }
     }
+}
+
+using JacobiKernel = void (*)(const JacobiParams, const CUtensorMap);
+
+template <int S>
+JacobiKernel pick_rop(int rop) {
+    if (rop == UPIR_RED_MAX) return jacobi_tma_kernel<S, UPIR_RED_MAX>;
+    if (rop == UPIR_RED_MIN) return jacobi_tma_kernel<S, UPIR_RED_MIN>;
+    return jacobi_tma_kernel<S, 0>;
+}
+
+JacobiKernel pick_kernel(int stages, int rop) {
+    switch (stages) {
+        case 1: return pick_rop<1>(rop);
+        case 2: return pick_rop<2>(rop);
+        case 3: return pick_rop<3>(rop);
+        default: return pick_rop<4>(rop);
+    }
+}
+
+bool configure_jacobi(JacobiKernel k) {
+    // each instantiation gets the large dynamic shared memory window once
+    static JacobiKernel done[16] = {};
+    for (auto& d : done) {
+        if (d == k) return true;
+        if (!d) {
+            if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024) != cudaSuccess)
+                return false;
+            d = k;
+            return true;
+        }
+    }
+    return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024) == cudaSuccess;
 }
 
 }  // namespace
 
-size_t jacobi_tma_smem_bytes(int tile_m, int tile_n) {
-    return (size_t)(tile_m + 2) * (tile_n + 8) * sizeof(float);
+size_t jacobi_tma_smem_bytes(int tile_m, int tile_n, int stages) {
+    const size_t stage_floats = ((size_t)(tile_m + 2) * (tile_n + 8) + 255) / 256 * 256;
+    return stage_floats * sizeof(float) * stages + 1024;
+}
+
+int jacobi_tma_max_teams_per_sm(int units, int tile_m, int tile_n, int stages) {
+    JacobiKernel k = pick_kernel(stages, UPIR_RED_MAX);
+    if (!configure_jacobi(k)) return 0;
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, units,
+                                                      jacobi_tma_smem_bytes(tile_m, tile_n, stages)) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return n;
 }
 
 cudaError_t launch_jacobi_tma(int teams, int units, const JacobiParams& p, const void* tmap,
                               cudaStream_t s) {
-    const size_t smem = jacobi_tma_smem_bytes(p.tile_m, p.tile_n) + 1024;
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(jacobi_tma_kernel,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, 201 * 1024);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
+    JacobiKernel k = pick_kernel(p.stages, p.rvar ? p.rop : 0);
+    if (!configure_jacobi(k)) return cudaGetLastError();
     CUtensorMap m;
     memcpy(&m, tmap, sizeof(m));
-    jacobi_tma_kernel<<<teams, units, smem, s>>>(p, m);
-    return cudaGetLastError();
+    return launch_pdl(k, teams, units, jacobi_tma_smem_bytes(p.tile_m, p.tile_n, p.stages), s, p, m);
 }
 
 }  // namespace upir

@@ -65,6 +65,8 @@ __global__ void __launch_bounds__(1024) matvec_kernel(const MatvecParams p) {
     const int64_t wpb = blockDim.x >> 5;
     const int64_t W = (int64_t)gridDim.x * wpb;
     const int64_t w = (int64_t)blockIdx.x * wpb + (threadIdx.x >> 5);
+    if (p.wait_prior) griddep_wait();
+    griddep_launch_dependents();
     auto rows = [&](int64_t k0, int64_t k1) {
         for (int64_t k = k0; k < k1; ++k) {
             const int64_t r = p.lb + k * p.step;
@@ -93,15 +95,14 @@ __global__ void __launch_bounds__(1024) matvec_kernel(const MatvecParams p) {
             }
         }
     } else {
-        static_ranges(p.trip, p.chunk, W, w, rows);
+        static_ranges(p.sk, p.trip, p.chunk, W, w, rows);
     }
 }
 
 }  // namespace
 
 cudaError_t launch_matvec(int teams, int units, const MatvecParams& p, cudaStream_t s) {
-    matvec_kernel<<<teams, units, 0, s>>>(p);
-    return cudaGetLastError();
+    return launch_pdl(matvec_kernel, teams, units, 0, s, p);
 }
 
 }  // namespace upir

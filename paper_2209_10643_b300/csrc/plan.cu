@@ -148,7 +148,8 @@ upir_status plan_loop(upir_region r, const upir_loop_desc* d, LoopRec& lp) {
         if (k == UPIR_HINT_VARIANT) ok(v >= 0 && v <= 3, UPIR_EINVAL, "variant hint out of range"), lp.variant = (int)v;
         else if (k == UPIR_HINT_TILE_M) ok(v >= 1 && v <= 254, UPIR_EINVAL, "tile_m hint out of range"), lp.tile_m = (int)v;
         else if (k == UPIR_HINT_TILE_N) ok(v >= 4 && v <= 248 && v % 4 == 0, UPIR_EINVAL, "tile_n hint must be a multiple of 4 in [4, 248]"), lp.tile_n = (int)v;
-        else if (k == UPIR_HINT_VEC) ok(v == 1 || v == 4, UPIR_EINVAL, "vec hint must be 1 or 4"), lp.vec = (int)v;
+        else if (k == UPIR_HINT_VEC) ok(v == 1 || v == 4 || v == 8 || v == 16, UPIR_EINVAL, "vec hint must be 1, 4, 8 or 16"), lp.vec = (int)v;
+        else if (k == UPIR_HINT_STAGES) ok(v >= 1 && v <= 4, UPIR_EINVAL, "stages hint must be in [1, 4]"), lp.stages = (int)v;
         else ok(false, UPIR_EINVAL, "unknown hint key");
     }
     if (ok.st) return ok.st;
@@ -210,6 +211,8 @@ upir_status plan_loop(upir_region r, const upir_loop_desc* d, LoopRec& lp) {
     };
 
     const int U0 = r->units, T0 = r->teams;
+    // implicit barrier after the previous loop of the region unless it was nowait
+    const int wait_prior = (r->loops.empty() || !r->loops.back()->nowait) ? 1 : 0;
     lp.units = U0 ? U0 : 256;
     lp.kind = LK_ELEM;
     ElemParams& ep = lp.ep;
@@ -220,6 +223,7 @@ upir_status plan_loop(upir_region r, const upir_loop_desc* d, LoopRec& lp) {
     ep.chunk = lp.chunk;
     ep.rv = rv;
     ep.imod_mod = 1;
+    ep.wait_prior = wait_prior;
 
     switch (lp.body) {
         case UPIR_BODY_AXPY: {
@@ -282,9 +286,15 @@ upir_status plan_loop(upir_region r, const upir_loop_desc* d, LoopRec& lp) {
                 lp.kind = LK_JACOBI_TMA;
                 JacobiParams& jp = lp.jp;
                 memset(&jp, 0, sizeof(jp));
-                lp.tile_m = lp.tile_m ? lp.tile_m : 32;
+                lp.tile_m = lp.tile_m ? lp.tile_m : 64;
                 lp.tile_n = lp.tile_n ? lp.tile_n : 128;
                 lp.tile_n = (int)std::min<int64_t>(lp.tile_n, 4 * (int64_t)lp.units);
+                jp.stages = lp.stages ? lp.stages : 3;
+                while (jp.stages > 1 && jacobi_tma_smem_bytes(lp.tile_m, lp.tile_n, jp.stages) > 220 * 1024)
+                    --jp.stages;
+                lp.smem = jacobi_tma_smem_bytes(lp.tile_m, lp.tile_n, jp.stages);
+                if (!ok(lp.smem <= 220 * 1024, UPIR_EINVAL, "Jacobi tile too large for shared memory"))
+                    return ok.st;
                 jp.uin = uin;
                 jp.uout = uout;
                 jp.rows = R;
@@ -302,21 +312,26 @@ upir_status plan_loop(upir_region r, const upir_loop_desc* d, LoopRec& lp) {
                 jp.rop = rv.fop == UPIR_RED_MIN ? UPIR_RED_MIN : UPIR_RED_MAX;
                 jp.spin_limit = ctx->spin_limit;
                 jp.err_word = ctx->err_word;
-                lp.smem = jacobi_tma_smem_bytes(lp.tile_m, lp.tile_n);
-                if (!ok(lp.smem <= 200 * 1024, UPIR_EINVAL, "Jacobi tile too large for shared memory"))
-                    return ok.st;
+                jp.wait_prior = wait_prior;
                 if (lp.trip) {
                     upir_status st = encode_tmap_2d(ctx, &lp.tmap[0], uin, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4,
                                                     (uint64_t)C, (uint64_t)R, (uint32_t)(lp.tile_n + 8),
                                                     (uint32_t)(lp.tile_m + 2), 0);
                     if (st != UPIR_OK) return st;
                 }
+                // persistent teams: as many as are resident at once, balanced so
+                // every team gets the same number of tiles (to within one)
+                const int per_sm = std::max(1, jacobi_tma_max_teams_per_sm(lp.units, lp.tile_m, lp.tile_n, jp.stages));
+                const int64_t slots = (int64_t)kNumSMs * per_sm;
                 const int64_t c = lp.chunk > 0 ? lp.chunk : 1;
                 if (T0) lp.teams = T0;
-                else if (lp.sched == UPIR_SCHED_STATIC && lp.chunk == 0)
-                    lp.teams = (int)std::min<int64_t>(std::max<int64_t>(jp.ntiles, 1), 0x7fffffff);
-                else
-                    lp.teams = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(jp.ntiles, c), kNumSMs * 8));
+                else if (lp.sched == UPIR_SCHED_STATIC && lp.chunk == 0) {
+                    const int64_t per = std::max<int64_t>(1, ceil_div(jp.ntiles, slots));
+                    lp.teams = (int)std::max<int64_t>(1, ceil_div(jp.ntiles, per));
+                } else {
+                    lp.teams = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(jp.ntiles, c), slots));
+                }
+                jp.sk = make_sched_const(jp.ntiles, lp.chunk, lp.teams);
                 if (lp.sched == UPIR_SCHED_DYNAMIC) {
                     upir_status st = alloc_scratch(ctx, lp, 0, 0, &jp.sc);
                     if (st != UPIR_OK) return st;
@@ -374,6 +389,8 @@ upir_status plan_loop(upir_region r, const upir_loop_desc* d, LoopRec& lp) {
                 lp.teams = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(ceil_div(lp.trip, c), wpb),
                                                                        resident_warps / wpb));
             }
+            mp.sk = make_sched_const(lp.trip, lp.chunk, (int64_t)lp.teams * wpb);
+            mp.wait_prior = wait_prior;
             if (lp.sched == UPIR_SCHED_DYNAMIC) {
                 upir_status st = alloc_scratch(ctx, lp, 0, 0, &mp.sc);
                 if (st != UPIR_OK) return st;
@@ -424,6 +441,7 @@ upir_status plan_loop(upir_region r, const upir_loop_desc* d, LoopRec& lp) {
                     lp.teams = (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, 0x7fffffff));
                 else
                     lp.teams = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(ntiles, c), kNumSMs * 2));
+                gp.sk = make_sched_const(ntiles, lp.chunk, lp.teams);
                 if (lp.sched == UPIR_SCHED_DYNAMIC) {
                     upir_status st = alloc_scratch(ctx, lp, 0, 0, &gp.sc);
                     if (st != UPIR_OK) return st;
@@ -472,6 +490,7 @@ upir_status plan_loop(upir_region r, const upir_loop_desc* d, LoopRec& lp) {
     ep.imod_mul = imod_mul;
     ep.imod_mod = imod_mod;
     ep.imod_inc = imod_inc;
+    ep.imod_minv = imod_mod >= 2 ? (unsigned long long)(((unsigned __int128)1 << 64) / (unsigned long long)imod_mod) : 0;
     const int64_t trip = lp.trip;
     const int U = lp.units;
     const int64_t V = (lp.body == UPIR_BODY_AXPY && lp.step == 1) ? lp.vec : (lp.body == UPIR_BODY_IMOD ? 4 : 1);
@@ -479,9 +498,9 @@ upir_status plan_loop(upir_region r, const upir_loop_desc* d, LoopRec& lp) {
         if (T0) lp.teams = T0;
         else if (lp.chunk == 0) lp.teams = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(trip, U * V), 0x7fffffff));
         else lp.teams = default_teams_for_chunks(ceil_div(trip, lp.chunk), U);
+        ep.sk = make_sched_const(trip, lp.chunk, (int64_t)lp.teams * U);
         if (has_red) {
-            const int64_t ng = ceil_div(lp.teams, kGroup);
-            upir_status st = alloc_scratch(ctx, lp, ng, lp.teams, &ep.sc);
+            upir_status st = alloc_scratch(ctx, lp, finalize_groups(lp.teams), lp.teams, &ep.sc);
             if (st != UPIR_OK) return st;
         }
     } else {
@@ -491,7 +510,8 @@ upir_status plan_loop(upir_region r, const upir_loop_desc* d, LoopRec& lp) {
                            "dynamic reductions need at most 2^27 chunks (raise the chunk)"))
             return ok.st;
         lp.teams = T0 ? T0 : default_teams_for_chunks(ep.nchunks, U);
-        upir_status st = alloc_scratch(ctx, lp, 0, has_red ? ep.nchunks : 0, &ep.sc);
+        const int64_t nslots = has_red ? ep.nchunks : 0;
+        upir_status st = alloc_scratch(ctx, lp, finalize_groups(nslots), nslots, &ep.sc);
         if (st != UPIR_OK) return st;
     }
     lp.skip = trip == 0;
@@ -501,8 +521,8 @@ upir_status plan_loop(upir_region r, const upir_loop_desc* d, LoopRec& lp) {
 cudaError_t launch_loop(upir_ctx ctx, LoopRec& lp, cudaStream_t s) {
     switch (lp.kind) {
         case LK_ELEM:
-            return launch_elem(lp.body, lp.sched == UPIR_SCHED_DYNAMIC, lp.ep.rv.fvar != nullptr,
-                               lp.ep.rv.ivar != nullptr, lp.teams, lp.units, lp.ep, s);
+            return launch_elem(lp.body, lp.sched == UPIR_SCHED_DYNAMIC, lp.ep.rv.fvar ? lp.ep.rv.fop : 0,
+                               lp.ep.rv.ivar ? lp.ep.rv.iop : 0, lp.teams, lp.units, lp.ep, s);
         case LK_JACOBI_TMA: return launch_jacobi_tma(lp.teams, lp.units, lp.jp, &lp.tmap[0], s);
         case LK_MATVEC: return launch_matvec(lp.teams, lp.units, lp.mp, s);
         case LK_GEMM_F32: return launch_gemm_f32(lp.teams, lp.units, lp.gp, s);

@@ -11,6 +11,7 @@
 namespace upir {
 
 constexpr int kGroup = 1024;             // blocks per first-level group of a static reduction
+constexpr int kFinSeg = 2048;            // partial slots folded by one finalize block
 constexpr int UPIR_ERR_WAIT_TIMEOUT = 1;  // device error word: a bounded wait ran out
 constexpr int kNumSMs = 148;
 
@@ -26,6 +27,21 @@ struct RedVars {
     int fop, iop;      // upir_red_op of each
     int fterm, iterm;  // upir_term of each
 };
+
+// Static-schedule constants, computed on the host for the launched worker
+// count W: blocked schedules give worker w [w*base + min(w, extra), +base +
+// (w < extra)); chunked ones hand out chunks w, w + W, ... < nchunks.
+struct SchedConst {
+    int64_t base, extra, nchunks;
+};
+
+inline SchedConst make_sched_const(int64_t trip, int64_t chunk, int64_t workers) {
+    SchedConst s;
+    s.base = workers > 0 ? trip / workers : 0;
+    s.extra = workers > 0 ? trip % workers : 0;
+    s.nchunks = chunk > 0 ? (trip + chunk - 1) / chunk : 0;
+    return s;
+}
 
 // Per-loop device scratch for reductions and dynamic schedules.
 struct Scratch {
@@ -48,6 +64,9 @@ struct ElemParams {
     float* uout;
     int64_t rows, cols;
     long long imod_mul, imod_mod, imod_inc;  // imod_inc = (mul * step) mod m, in [0, m)
+    unsigned long long imod_minv;            // floor(2^64 / m) for Barrett reduction (m >= 2)
+    SchedConst sk;
+    int wait_prior;                          // wait for the previous kernel (implicit barrier)
     RedVars rv;
     Scratch sc;
 };
@@ -64,8 +83,11 @@ struct JacobiParams {
     int sched;
     float* rvar;  // reduction variable (max/min of |u_out - u_in|), or nullptr
     int rop;
+    int stages;   // shared-memory pipeline depth
     long long spin_limit;
     int* err_word;
+    SchedConst sk;
+    int wait_prior;
     Scratch sc;
 };
 
@@ -76,6 +98,8 @@ struct MatvecParams {
     int64_t rows, cols;
     int64_t lb, step, trip, chunk;
     int sched;
+    SchedConst sk;
+    int wait_prior;
     Scratch sc;
 };
 
@@ -87,6 +111,7 @@ struct GemmParams {
     int64_t row_lb, row_ub;
     int64_t chunk;
     int sched;
+    SchedConst sk;
     Scratch sc;
 };
 
@@ -100,12 +125,18 @@ struct SplitParams {
 };
 
 // Host-side launchers (one per kernel family).
-cudaError_t launch_elem(int body, bool dynamic, bool has_f, bool has_i, int teams, int units,
+// fop / iop: the loop's FP32 / int64 reduction operator, 0 when it has none.
+cudaError_t launch_elem(int body, bool dynamic, int fop, int iop, int teams, int units,
                         const ElemParams& p, cudaStream_t s);
+cudaError_t launch_elem_main(int body, bool dynamic, int fop, int iop, int teams, int units,
+                             const ElemParams& p, cudaStream_t s);
+cudaError_t launch_finalize(const RedVars& rv, const Scratch& sc, int64_t nslots, bool reset_counter,
+                            cudaStream_t s);
+int64_t finalize_groups(int64_t nslots);
 cudaError_t launch_jacobi_tma(int teams, int units, const JacobiParams& p, const void* tmap,
                               cudaStream_t s);
-cudaError_t launch_jacobi_direct(int teams, int units, const JacobiParams& p, cudaStream_t s);
-size_t jacobi_tma_smem_bytes(int tile_m, int tile_n);
+size_t jacobi_tma_smem_bytes(int tile_m, int tile_n, int stages);
+int jacobi_tma_max_teams_per_sm(int units, int tile_m, int tile_n, int stages);
 cudaError_t launch_matvec(int teams, int units, const MatvecParams& p, cudaStream_t s);
 cudaError_t launch_gemm_f32(int teams, int units, const GemmParams& p, cudaStream_t s);
 cudaError_t launch_split_bf16(int teams, int units, const SplitParams& p, cudaStream_t s);
