@@ -257,7 +257,6 @@ upir_status plan_loop(upir_region r, const upir_loop_desc* d, LoopRec& lp) {
             check_int_terms(0);
             ep.owner = static_cast<long long*>(lp.bufs[0]->dev);
             ep.count = static_cast<unsigned long long*>(lp.bufs[1]->dev);
-            lp.vec = 1;
             break;
         }
         case UPIR_BODY_JACOBI5: {
@@ -493,7 +492,12 @@ upir_status plan_loop(upir_region r, const upir_loop_desc* d, LoopRec& lp) {
     ep.imod_minv = imod_mod >= 2 ? (unsigned long long)(((unsigned __int128)1 << 64) / (unsigned long long)imod_mod) : 0;
     const int64_t trip = lp.trip;
     const int U = lp.units;
-    const int64_t V = (lp.body == UPIR_BODY_AXPY && lp.step == 1) ? lp.vec : (lp.body == UPIR_BODY_IMOD ? 4 : 1);
+    // iterations per worker the blocked schedule aims for: 4 (one 128-bit access)
+    // without reductions, 8 with them (halves the per-element share of the
+    // warp-level reduction tree at the same coalescing)
+    const int64_t vdef = has_red ? 8 : 4;
+    const int64_t V = (lp.body == UPIR_BODY_AXPY && lp.step == 1) ? (lp.vec ? lp.vec : vdef)
+                      : (lp.body == UPIR_BODY_IMOD ? vdef : 1);
     if (lp.sched == UPIR_SCHED_STATIC) {
         if (T0) lp.teams = T0;
         else if (lp.chunk == 0) lp.teams = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(trip, U * V), 0x7fffffff));

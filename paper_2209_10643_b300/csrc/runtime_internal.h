@@ -32,7 +32,7 @@ struct LoopRec {
     std::vector<upir_buf> bufs;
     std::vector<double> scalars;
     std::vector<upir_reduction> reds;
-    int variant = 0, tile_m = 0, tile_n = 0, vec = 4, stages = 0;
+    int variant = 0, tile_m = 0, tile_n = 0, vec = 0, stages = 0;  // 0: planner default
     int teams = 0, units = 0;
     int kind = LK_ELEM;
     bool skip = false;       // zero-trip loop: nothing to launch
