@@ -312,6 +312,36 @@ upir_status upir_selftest_bounded_wait(upir_ctx ctx, int64_t spin_limit);
  * settable with the environment variable UPIR_SPIN_LIMIT. */
 upir_status upir_ctx_set_spin_limit(upir_ctx ctx, int64_t spin_limit);
 
+/* ------------------------------------------- allocation-free AXPY variant -- */
+/* The paper has no counterpart to this call; it serves callers that cannot
+ * allocate device memory: code whose device memory is fully reserved by its
+ * own pool, latency-critical paths where a cudaMalloc would synchronize the
+ * device, and embedders that cannot create a context (upir_init allocates) or
+ * hand the library an allocator.
+ *
+ * y[i] = fma(a, x[i], y[i]) for 0 <= i < n, then
+ *   *sum_y    += sum of the updated y[i]        (FP32, compensated, fixed order)
+ *   *imod_sum += sum of (imod_mul * i) mod imod_mod  (int64, exact)
+ * with the same kernels, geometry and therefore the same bits as an AXPY loop
+ * recorded through upir_loop with a static schedule, chunk 0, planner geometry
+ * and those two reduction clauses.  x, y, sum_y and imod_sum are device
+ * pointers owned by the caller; the work is enqueued on `cuda_stream` (NULL:
+ * the legacy default stream) of the current device and the call returns
+ * without waiting.  Nothing is allocated: the reduction scratch is one fixed
+ * array of about 512 KiB inside the library's device image, which every GPU
+ * that loads the library holds until the process exits.
+ *
+ * Limits and errors: n <= 67,108,864 (2^26) and 1 <= imod_mod < 2^62 with
+ * |imod_mul| * (n - 1) < 2^62, else UPIR_EINVAL; NULL pointers: UPIR_EINVAL;
+ * n == 0 leaves the variables unchanged.  The first call on a device looks up
+ * the array's device address (once per device, with that device current), so
+ * make that first call before any stream capture.  Every call shares the one
+ * array: calls whose work overlaps on the GPU (other streams, other threads)
+ * race and give wrong results; serialize them. */
+upir_status upir_axpy_reduce_noalloc(const float* x, float* y, int64_t n, float a,
+                                     int64_t imod_mul, int64_t imod_mod, float* sum_y,
+                                     int64_t* imod_sum, void* cuda_stream);
+
 /* ------------------------------------------------------ learned cost model -- */
 /* A 12 -> 64 -> 64 -> 1 ReLU MLP predicting log2 of a loop's time from its
  * features; weights used in bfloat16, FP32 accumulation and FP32 master

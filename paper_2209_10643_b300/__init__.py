@@ -87,6 +87,7 @@ _SIGS = {
     "upir_region_loop_geometry": (_i32, [_vp, _i32, _P(_i32), _P(_i32)]),
     "upir_selftest_bounded_wait": (_i32, [_vp, _i64]),
     "upir_ctx_set_spin_limit": (_i32, [_vp, _i64]),
+    "upir_axpy_reduce_noalloc": (_i32, [_vp, _vp, _i64, C.c_float, _i64, _i64, _vp, _vp, _vp]),
     "upir_mlp_forward": (_i32, [_vp, _vp, _vp, _i32, _vp]),
     "upir_mlp_backward": (_i32, [_vp, _vp, _vp, _vp, _i32, _vp, _vp]),
     "upir_mlp_sgd": (_i32, [_vp, _vp, _vp, C.c_float]),
@@ -251,6 +252,13 @@ def upir_selftest_bounded_wait(ctx: int, spin_limit: int) -> None:
 
 def upir_ctx_set_spin_limit(ctx: int, spin_limit: int) -> None:
     _chk(ctx, lib.upir_ctx_set_spin_limit(ctx, spin_limit), "upir_ctx_set_spin_limit")
+
+
+def upir_axpy_reduce_noalloc(x: int, y: int, n: int, a: float, imod_mul: int, imod_mod: int,
+                             sum_y: int, imod_sum: int, stream: int | None = None) -> None:
+    st = lib.upir_axpy_reduce_noalloc(x, y, n, a, imod_mul, imod_mod, sum_y, imod_sum, stream)
+    if st != UPIR_OK:
+        raise UpirError(st, "upir_axpy_reduce_noalloc")
 
 
 def upir_mlp_forward(ctx: int, params: int, x: int, batch: int, pred: int) -> None:
