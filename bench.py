@@ -118,10 +118,14 @@ class Runtime:
         self.ctx = U.upir_init(device, self.stream.cuda_stream)
         self.flush_buf = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
         self.host = []
+        self.handles = []
 
-    def map(self, arr, kind):
+    def map(self, arr, kind, track=False):
         self.host.append(arr)
-        return self.U.upir_data_map(self.ctx, arr.ctypes.data, arr.nbytes, kind)
+        h = self.U.upir_data_map(self.ctx, arr.ctypes.data, arr.nbytes, kind)
+        if track:
+            self.handles.append(h)
+        return h
 
     def flush_l2(self):
         self.flush_buf.fill_(1.0)
@@ -319,6 +323,59 @@ def extra_gemm_f32(rt: Runtime) -> dict:
             "frac_fp32_peak": tf / fp32_peak}
 
 
+def extra_batch(rt: Runtime, count: int = 512) -> dict:
+    """512 uneven independent regions (40 % AXPY+dot, 30 % one Jacobi sweep,
+    30 % matvec; trip counts log-uniform in [1e3, 1e7], seed 6): regions/s of
+    one launch per loop, of those launches in one CUDA graph, and of the
+    persistent executor (tile shapes autotuned), all with data resident."""
+    U = rt.U
+    specs = I.batched_region_specs(count, seed=6)
+    regions, total_bytes = [], 0.0
+    for sp in specs:
+        arr = I.region_arrays(sp)
+        r = U.upir_spmd_region(rt.ctx, 0, 0)
+        if sp["op"] == I.OP_AXPY_DOT:
+            dot = np.zeros(1, np.float32)
+            hx, hy, hd = rt.map(arr["x"], 0, True), rt.map(arr["y"], 2, True), rt.map(dot, 2, True)
+            lp = dict(lb=0, ub=sp["n"], body=U.UPIR_BODY_AXPY, bufs=[hx, hy], scalars=[2.5],
+                      reductions=[(U.UPIR_RED_ADD, U.UPIR_F32, U.UPIR_TERM_XY, hd, 0)])
+            total_bytes += 12 * sp["n"]
+        elif sp["op"] == I.OP_JACOBI:
+            side = sp["side"]
+            res = np.full(1, -np.inf, np.float32)
+            h0, h1, hr = rt.map(arr["u0"], 0, True), rt.map(arr["u1"], 2, True), rt.map(res, 2, True)
+            lp = dict(lb=1, ub=side - 1, collapse=2, body=U.UPIR_BODY_JACOBI5, bufs=[h0, h1],
+                      scalars=[side, side], reductions=[(U.UPIR_RED_MAX, U.UPIR_F32, U.UPIR_TERM_RESID, hr, 0)])
+            total_bytes += 8 * (side - 2) ** 2
+        else:
+            y = np.zeros(sp["rows"], np.float32)
+            ha, hx, hy = rt.map(arr["A"], 0, True), rt.map(arr["x"], 0, True), rt.map(y, 2, True)
+            lp = dict(lb=0, ub=sp["rows"], body=U.UPIR_BODY_MATVEC, bufs=[ha, hx, hy],
+                      scalars=[sp["rows"], sp["cols"]])
+            total_bytes += 4 * sp["rows"] * sp["cols"]
+        U.upir_loop_checked(rt.ctx, r, U.make_loop_desc(**lp))
+        regions.append(r)
+    out = {"regions": count, "algorithmic_GB": total_bytes / 1e9}
+    tiles = None
+    for name, mode in (("launches", U.UPIR_BATCH_LAUNCHES), ("graph", U.UPIR_BATCH_GRAPH),
+                       ("persistent", U.UPIR_BATCH_PERSISTENT)):
+        b = U.upir_batch_create(rt.ctx, regions, mode)
+        if mode == U.UPIR_BATCH_PERSISTENT:
+            tiles = U.upir_batch_autotune(b, 3)
+        ms, _, _ = rt.timed_submits(lambda: U.upir_batch_submit(b), 10)
+        U.upir_batch_destroy(b)
+        out[name] = {"ms": ms, "regions_per_s": count / (ms / 1e3), "GB/s": total_bytes / (ms / 1e3) / 1e9}
+    out["persistent_tiles"] = {"axpy_iters": tiles[0], "jacobi_rows": tiles[1], "matvec_rows": tiles[2]}
+    out["speedup_persistent_vs_launches"] = out["launches"]["ms"] / out["persistent"]["ms"]
+    out["speedup_persistent_vs_graph"] = out["graph"]["ms"] / out["persistent"]["ms"]
+    for r in regions:
+        U.upir_region_destroy(r)
+    for h in rt.handles:
+        U.upir_data_unmap(rt.ctx, h)
+    rt.handles.clear()
+    return out
+
+
 def cpu_baseline_jacobi(budget_s: float = 12.0) -> dict:
     """The oracle (FP64 numpy, single thread) on a bounded sample of the
     headline workload: the full 4096^2 grid for as many sweeps as fit the budget."""
@@ -350,7 +407,8 @@ def run_ours(args) -> None:
         for name, fn in (("axpy_2^20", lambda: extra_axpy(rt, 1 << 20, pk)),
                          ("axpy_2^28", lambda: extra_axpy(rt, 1 << 28, pk)),
                          ("matvec_16384", lambda: extra_matvec(rt, pk)),
-                         ("gemm_f32_4096", lambda: extra_gemm_f32(rt))):
+                         ("gemm_f32_4096", lambda: extra_gemm_f32(rt)),
+                         ("batch_512_regions", lambda: extra_batch(rt))):
             try:
                 extra[name] = fn()
             except Exception as e:  # report, keep the headline

@@ -270,17 +270,31 @@ upir_status upir_region_destroy(upir_region region);
  *   LAUNCHES   : one launch per loop, regions one after another on the stream
  *   GRAPH      : the same launches captured once in a CUDA graph and replayed
  *   PERSISTENT : one persistent kernel over a work list of (region, tile)
- *                items, longest first, claimed with an atomic counter; each
- *                region's reduction is finalized by its last tile (fixed
- *                order), and the launch is captured in a CUDA graph.
- * PERSISTENT accepts regions of single AXPY (reductions over TERM_Y / TERM_XY),
- * JACOBI5 (max residual) and MATVEC loops; others give EUNSUPPORTED. */
+ *                items, largest regions first, claimed one by one from an
+ *                atomic counter by as many teams as the GPU holds at once;
+ *                each region's FP32 "+" reduction is finalized by its last
+ *                tile, folding the tile partials in tile order.  The launch
+ *                is captured in a CUDA graph.
+ * PERSISTENT accepts regions holding exactly one loop: AXPY (step 1, at most
+ * one FP32 "+" clause over TERM_Y or TERM_XY), JACOBI5 (at most one max/min
+ * residual clause) or MATVEC (step 1); others give EUNSUPPORTED.  Results are
+ * those of the regions run alone (FP32 sums to rounding order).  A region in
+ * a batch cannot take more loops or be destroyed until the batch is (EBUSY). */
 typedef enum { UPIR_BATCH_LAUNCHES = 0, UPIR_BATCH_GRAPH = 1, UPIR_BATCH_PERSISTENT = 2 } upir_batch_mode;
 
 upir_status upir_batch_create(upir_ctx ctx, const upir_region* regions, int32_t n,
                               int32_t mode, upir_batch* out);
 upir_status upir_batch_submit(upir_batch batch);
 upir_status upir_batch_destroy(upir_batch batch);
+
+/* Autotune the tile shapes of a PERSISTENT batch: every candidate (AXPY
+ * iterations per tile 4096..32768, Jacobi rows per tile 8..32, matvec rows
+ * per tile 8..32) is run `reps` times after one warm-up and timed with CUDA
+ * events; the shapes with the least median time are kept.  The batch really
+ * runs each time, so loops that update in place (AXPY) see every run.
+ * tiles_out (may be NULL) receives the chosen {axpy_tile, jacobi_rows,
+ * matvec_rows}.  Blocks the host.  EINVAL for other modes or reps < 1. */
+upir_status upir_batch_autotune(upir_batch batch, int32_t reps, int64_t* tiles_out);
 
 /* Taskwait at context level: wait for the stream, then read and clear the
  * device error word (ETIMEDOUT if a bounded wait ran out). */

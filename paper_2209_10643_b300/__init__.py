@@ -81,6 +81,7 @@ _SIGS = {
     "upir_batch_create": (_i32, [_vp, _P(_vp), _i32, _i32, _P(_vp)]),
     "upir_batch_submit": (_i32, [_vp]),
     "upir_batch_destroy": (_i32, [_vp]),
+    "upir_batch_autotune": (_i32, [_vp, _i32, _P(_i64)]),
     "upir_ctx_wait": (_i32, [_vp]),
     "upir_ctx_set_timing": (_i32, [_vp, _i32]),
     "upir_ctx_timings": (_i32, [_vp, _P(C.c_float), _P(_i32), _i32, _P(_i32)]),
@@ -220,6 +221,14 @@ def upir_batch_submit(batch: int) -> None:
 
 def upir_batch_destroy(batch: int) -> None:
     lib.upir_batch_destroy(batch)
+
+
+def upir_batch_autotune(batch: int, reps: int = 3) -> tuple[int, int, int]:
+    out = (C.c_int64 * 3)()
+    st = lib.upir_batch_autotune(batch, reps, out)
+    if st != UPIR_OK:
+        raise UpirError(st, "upir_batch_autotune")
+    return out[0], out[1], out[2]
 
 
 def upir_ctx_wait(ctx: int) -> None:

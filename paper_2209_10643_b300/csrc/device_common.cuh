@@ -174,6 +174,47 @@ __device__ __forceinline__ void write_reduction_vars(const RedVars& rv, const Pa
     if (rv.ivar) *rv.ivar = iacc_combine(*rv.ivar, fin.i, rv.iop);
 }
 
+// ----------------------------------------------------------------------------
+// max / min folds (exact in any order), used where one atomic per team folds
+// a team result into the reduction variable.
+// ----------------------------------------------------------------------------
+
+// maxNum / minNum folded into *addr; NaN operands are ignored.
+__device__ __forceinline__ void atomic_fold_minmax(float* addr, float v, int op) {
+    if (isnan(v)) return;
+    int* ai = reinterpret_cast<int*>(addr);
+    int old = *reinterpret_cast<volatile int*>(ai);
+    for (;;) {
+        const float of = __int_as_float(old);
+        const bool better = op == UPIR_RED_MAX ? (v > of) : (v < of);
+        if (!isnan(of) && !better) return;
+        const int prev = atomicCAS(ai, old, __float_as_int(v));
+        if (prev == old) return;
+        old = prev;
+    }
+}
+
+__device__ __forceinline__ float fold(float a, float b, int op) {
+    return op == UPIR_RED_MIN ? fminf(a, b) : fmaxf(a, b);
+}
+
+__device__ __forceinline__ float block_fold(float v, int op) {
+    __shared__ float part[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int m = 16; m >= 1; m >>= 1) v = fold(v, __shfl_xor_sync(0xffffffffu, v, m), op);
+    if (lane == 0) part[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+        float q = lane < nw ? part[lane] : v;
+#pragma unroll
+        for (int m = 16; m >= 1; m >>= 1) q = fold(q, __shfl_xor_sync(0xffffffffu, q, m), op);
+        v = q;
+    }
+    return v;  // valid in thread 0
+}
+
 // Warp-aggregated claim of the next dynamic chunk: the active lanes take
 // consecutive tickets with one atomic.
 __device__ __forceinline__ unsigned long long claim_chunk(unsigned long long* counter) {

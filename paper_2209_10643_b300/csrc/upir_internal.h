@@ -124,6 +124,45 @@ struct SplitParams {
     int transpose;
 };
 
+// Persistent execution of a batch of single-loop regions: one entry per
+// region, one (region, tile) work item per tile.
+enum BatchOp { BOP_AXPY = 0, BOP_JACOBI = 1, BOP_MATVEC = 2 };
+
+struct BatchRegion {
+    int op;             // BatchOp
+    int fop;            // reduction operator of the FP32 clause, 0 if none
+    int fterm;          // AXPY: TERM_Y or TERM_XY
+    int pad;
+    const float* in0;   // AXPY x | JACOBI u_in | MATVEC A
+    const float* in1;   // MATVEC x
+    float* out;         // AXPY y | JACOBI u_out | MATVEC y
+    float a;
+    int pad2;
+    int64_t lb, trip;   // first index and count (AXPY) / first row and rows (JACOBI, MATVEC)
+    int64_t rows, cols; // JACOBI grid / MATVEC shape
+    int64_t tiles;      // work items of this region
+    int64_t tiles_c;    // JACOBI: tiles per row band
+    int64_t slot0;      // AXPY: first partial slot
+    float* fvar;        // reduction variable, or nullptr
+    unsigned* ticket;   // AXPY with a reduction: tiles finished so far
+};
+
+struct BatchParams {
+    const BatchRegion* regions;
+    const int2* items;             // (region, tile), largest regions first
+    int64_t nitems;
+    Partial* partials;
+    unsigned long long* counter;   // next work item
+    unsigned* exit_ticket;         // teams finished
+    int axpy_tile;                 // AXPY iterations per tile (multiple of 1024)
+    int jac_rows;                  // JACOBI rows per tile (tiles are 128 columns wide)
+    int mv_rows;                   // MATVEC rows per tile
+};
+
+constexpr int kBatchUnits = 256;
+constexpr int kBatchJacCols = 128;
+constexpr int kBatchMaxJacRows = 32;
+
 // Host-side launchers (one per kernel family).
 // fop / iop: the loop's FP32 / int64 reduction operator, 0 when it has none.
 cudaError_t launch_elem(int body, bool dynamic, int fop, int iop, int teams, int units,
@@ -141,5 +180,7 @@ cudaError_t launch_matvec(int teams, int units, const MatvecParams& p, cudaStrea
 cudaError_t launch_gemm_f32(int teams, int units, const GemmParams& p, cudaStream_t s);
 cudaError_t launch_split_bf16(int teams, int units, const SplitParams& p, cudaStream_t s);
 cudaError_t launch_bounded_wait_selftest(long long spin_limit, int* err_word, cudaStream_t s);
+cudaError_t launch_batch_persistent(int teams, const BatchParams& p, cudaStream_t s);
+int batch_persistent_teams_per_sm();
 
 }  // namespace upir

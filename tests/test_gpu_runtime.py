@@ -138,15 +138,16 @@ def test_region_resubmit_graph_and_timing(s):
     assert np.array_equal(y, want)
 
 
-@pytest.mark.parametrize("mode", [0, 1])
-def test_batch_of_regions_equals_each_region(s, mode):
-    specs = I.batched_region_specs(12, seed=6, t_hi=2e5, max_side=300, max_rows=600, max_cols=600)
+@pytest.mark.parametrize("mode,tune", [(0, False), (1, False), (2, False), (2, True)])
+def test_batch_of_regions_equals_each_region(s, mode, tune):
+    specs = I.batched_region_specs(24, seed=6, t_hi=3e5, max_side=300, max_rows=600, max_cols=600)
     regions, checks, keep = [], [], []
     for sp in specs:
         arr = I.region_arrays(sp)
         r = U.upir_spmd_region(s.ctx, 0, 0)
         if sp["op"] == I.OP_AXPY_DOT:
             dot = np.zeros(1, np.float32)
+            arr["y0"] = arr["y"].copy()
             hx, hy, hd = s.map(arr["x"], 0), s.map(arr["y"], 2), s.map(dot, 2)
             U.upir_loop_checked(s.ctx, r, U.make_loop_desc(**axpy_loop(
                 hx, hy, sp["n"], reds=[(U.UPIR_RED_ADD, U.UPIR_F32, U.UPIR_TERM_XY, hd, 0)])))
@@ -167,6 +168,16 @@ def test_batch_of_regions_equals_each_region(s, mode):
             checks.append(("matvec", arr, O.matvec(arr["A"], arr["x"]), y, (ha, hx, hy)))
         regions.append(r)
     b = U.upir_batch_create(s.ctx, regions, mode)
+    if tune:
+        # autotuning runs the batch many times: undo its in-place AXPY updates
+        tiles = U.upir_batch_autotune(b, 1)
+        assert tiles[0] in (4096, 8192, 16384, 32768) and tiles[1] in (8, 16, 32)
+        for kind, arr, want, out, hs in checks:
+            if kind == "axpy":
+                arr["y"][:] = arr["y0"]
+                U.upir_data_update(s.ctx, hs[1], U.UPIR_MAP_TO)
+                out[0] = 0.0
+                U.upir_data_update(s.ctx, hs[2], U.UPIR_MAP_TO)
     U.upir_batch_submit(b)
     U.upir_ctx_wait(s.ctx)
     U.upir_batch_destroy(b)
@@ -184,3 +195,21 @@ def test_batch_of_regions_equals_each_region(s, mode):
             assert np.array_equal(arr["u1"], v) and out[0] == r0
         else:
             assert np.linalg.norm(out - want) <= 1e-5 * np.linalg.norm(want)
+
+
+def test_persistent_batch_rejects_unsupported_regions(s):
+    x = np.ones(64, np.float32)
+    hx, hy = s.map(x, U.UPIR_MAP_TO), s.map(x.copy(), U.UPIR_MAP_TOFROM)
+    r = U.upir_spmd_region(s.ctx, 0, 0)
+    U.upir_loop_checked(s.ctx, r, U.make_loop_desc(**axpy_loop(hx, hy, 64, step=2)))
+    with pytest.raises(U.UpirError) as e:
+        U.upir_batch_create(s.ctx, [r], U.UPIR_BATCH_PERSISTENT)
+    assert e.value.status == U.UPIR_EUNSUPPORTED
+    b = U.upir_batch_create(s.ctx, [r], U.UPIR_BATCH_GRAPH)
+    with pytest.raises(U.UpirError) as e:
+        U.upir_region_destroy(r)
+    assert e.value.status == U.UPIR_EBUSY
+    U.upir_batch_destroy(b)
+    U.upir_region_destroy(r)
+    s.unmap(hx)
+    s.unmap(hy)
