@@ -323,6 +323,39 @@ def extra_gemm_f32(rt: Runtime) -> dict:
             "frac_fp32_peak": tf / fp32_peak}
 
 
+def extra_gemm_tc(rt: Runtime, pk: dict) -> dict:
+    """C = A B, 4096^3, A and B ~ N(0, 1/K): bfloat16 tensor cores with FP32
+    accumulation, and the split-bfloat16 (3 products) form.  The bfloat16
+    operands are prepared once by the SPLIT_BF16 loop, timed separately."""
+    U = rt.U
+    m = n = k = 4096
+    a, b = I.gemm_inputs(m, n, k)
+    ah, al = np.zeros(m * k, np.uint16), np.zeros(m * k, np.uint16)
+    bh, bl = np.zeros(n * k, np.uint16), np.zeros(n * k, np.uint16)
+    c = np.zeros((m, n), np.float32)
+    ha, hb = rt.map(a, U.UPIR_MAP_TO), rt.map(b, U.UPIR_MAP_TO)
+    hah, hal, hbh, hbl = (rt.map(v, U.UPIR_MAP_ALLOC) for v in (ah, al, bh, bl))
+    hc = rt.map(c, U.UPIR_MAP_ALLOC)
+    prep = rt.region([dict(lb=0, ub=m, body=U.UPIR_BODY_SPLIT_BF16, bufs=[ha, hah, hal], scalars=[m, k, 0]),
+                      dict(lb=0, ub=k, body=U.UPIR_BODY_SPLIT_BF16, bufs=[hb, hbh, hbl], scalars=[k, n, 1])])
+    pms, _, _ = rt.timed_submits(lambda: U.upir_region_submit(prep, 0), 5)
+    out = {"shape": [m, n, k], "split_ms": pms}
+    flops = 2.0 * m * n * k
+    for name, body, bufs, mult in (("bf16", U.UPIR_BODY_GEMM_BF16, [hah, hbh, hc], 1),
+                                   ("bf16x3", U.UPIR_BODY_GEMM_BF16X3, [hah, hal, hbh, hbl, hc], 3)):
+        r = rt.region([dict(lb=0, ub=m, collapse=2, body=body, bufs=bufs, scalars=[m, n, k])])
+        ms, _, _ = rt.timed_submits(lambda: U.upir_region_submit(r, 0), 10)
+        U.upir_region_destroy(r)
+        tf = flops / (ms / 1e3) / 1e12
+        out[name] = {"ms": ms, "TFLOP/s": tf, "tensor_TFLOP/s": tf * mult,
+                     "frac_bf16_peak": tf * mult / pk["bf16_tflops"]}
+    U.upir_region_destroy(prep)
+    for h in (ha, hb, hah, hal, hbh, hbl, hc):
+        U.upir_data_unmap(rt.ctx, h)
+    rt.host.clear()
+    return out
+
+
 def extra_batch(rt: Runtime, count: int = 512) -> dict:
     """512 uneven independent regions (40 % AXPY+dot, 30 % one Jacobi sweep,
     30 % matvec; trip counts log-uniform in [1e3, 1e7], seed 6): regions/s of
@@ -393,8 +426,21 @@ def cpu_baseline_jacobi(budget_s: float = 12.0) -> dict:
             "seconds": dt, "host_cores_available": os.cpu_count()}
 
 
+def extra_workloads(rt: Runtime, pk: dict) -> dict:
+    return {"axpy_2^20": lambda: extra_axpy(rt, 1 << 20, pk),
+            "axpy_2^28": lambda: extra_axpy(rt, 1 << 28, pk),
+            "matvec_16384": lambda: extra_matvec(rt, pk),
+            "gemm_f32_4096": lambda: extra_gemm_f32(rt),
+            "gemm_tc_4096": lambda: extra_gemm_tc(rt, pk),
+            "batch_512_regions": lambda: extra_batch(rt)}
+
+
 def run_ours(args) -> None:
     rank, local_rank, world = dist_env()
+    if args.extra_only:
+        rt = Runtime(local_rank)
+        print(json.dumps({args.extra_only: extra_workloads(rt, peaks())[args.extra_only]()}), flush=True)
+        return
     import torch
     import torch.distributed as dist
     if world > 1:
@@ -404,11 +450,7 @@ def run_ours(args) -> None:
     h = headline(rt, args.steps, args.warmup, pk, local_rank)
     extra = {}
     if rank == 0 and not args.no_extra:
-        for name, fn in (("axpy_2^20", lambda: extra_axpy(rt, 1 << 20, pk)),
-                         ("axpy_2^28", lambda: extra_axpy(rt, 1 << 28, pk)),
-                         ("matvec_16384", lambda: extra_matvec(rt, pk)),
-                         ("gemm_f32_4096", lambda: extra_gemm_f32(rt)),
-                         ("batch_512_regions", lambda: extra_batch(rt))):
+        for name, fn in extra_workloads(rt, pk).items():
             try:
                 extra[name] = fn()
             except Exception as e:  # report, keep the headline
@@ -476,6 +518,8 @@ def main() -> None:
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-extra", action="store_true", help="skip the extra workloads")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--extra-only", default=None,
+                    help="run only the named extra workload (e.g. gemm_tc_4096) and print its JSON")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
     if args.impl == "reference":

@@ -46,7 +46,7 @@ struct LoopRec {
     GemmParams gp{};
     SplitParams sp{};
     alignas(64) CUtensorMap tmap[4];
-    int tc_variant = 0;
+    alignas(16) unsigned char tc_params[256];  // tensor-core GEMM parameters
 };
 
 struct TimingRec {

@@ -131,3 +131,108 @@ def test_split_bf16_bit_exact(s, rows, cols, transpose):
     if transpose:
         wh, wl = wh.T.copy(), wl.T.copy()
     assert np.array_equal(hi, wh.ravel()) and np.array_equal(lo, wl.ravel())
+
+
+# --- tensor-core GEMM (tcgen05): bfloat16 and split-bfloat16 -----------------------
+
+def run_gemm_tc(s, a, b, x3=False, teams=0, chunk=0, lb=0, ub=None):
+    m, k = a.shape
+    n = b.shape[1]
+    ah, al = np.zeros(m * k, np.uint16), np.zeros(m * k, np.uint16)
+    bh, bl = np.zeros(n * k, np.uint16), np.zeros(n * k, np.uint16)
+    c = np.full((m, n), -3.0, np.float32)
+    ha, hb = s.map(a, U.UPIR_MAP_TO), s.map(b, U.UPIR_MAP_TO)
+    hah, hal, hbh, hbl = (s.map(v, U.UPIR_MAP_ALLOC) for v in (ah, al, bh, bl))
+    hc = s.map(c, U.UPIR_MAP_TOFROM)
+    # split A (row-major [m][k]) and B^T ([n][k], from B [k][n] transposed)
+    s.run([dict(lb=0, ub=m, body=U.UPIR_BODY_SPLIT_BF16, bufs=[ha, hah, hal], scalars=[m, k, 0]),
+           dict(lb=0, ub=k, body=U.UPIR_BODY_SPLIT_BF16, bufs=[hb, hbh, hbl], scalars=[k, n, 1])])
+    body = U.UPIR_BODY_GEMM_BF16X3 if x3 else U.UPIR_BODY_GEMM_BF16
+    bufs = [hah, hal, hbh, hbl, hc] if x3 else [hah, hbh, hc]
+    s.run([dict(lb=lb, ub=m if ub is None else ub, collapse=2, body=body, bufs=bufs, scalars=[m, n, k],
+                chunk=chunk)], teams, 0)
+    for h in (ha, hb, hah, hal, hbh, hbl, hc):
+        s.unmap(h)
+    return c
+
+
+@pytest.mark.parametrize("x3", [False, True])
+def test_gemm_tc_exact_small_integers(s, x3):
+    # integers in [-8, 8] are exact in bfloat16 and every partial sum is exact in FP32
+    a = I.small_int_matrix(200, 136, -8, 8, seed=1)
+    b = I.small_int_matrix(136, 300, -8, 8, seed=2)
+    assert np.array_equal(run_gemm_tc(s, a, b, x3), O.gemm(a, b))
+
+
+def check_tc(c, ref, absab, k):
+    """Normwise 1e-5 where the Frobenius norm averages many entries; for tiny
+    outputs the componentwise bound of the split-bfloat16 products
+    (3 * 2^-16 per product) plus FP32 accumulation, relative to |A||B|."""
+    if c.size >= 4096:
+        assert np.linalg.norm(c - ref) <= 1e-5 * np.linalg.norm(ref)
+    else:
+        assert np.all(np.abs(c - ref) <= (3 * 2.0 ** -16 + k * 2.0 ** -23) * absab)
+
+
+@pytest.mark.parametrize("m,n,k,teams,chunk", [(1, 1, 8, 0, 0), (129, 257, 72, 0, 0), (256, 512, 64, 3, 1),
+                                                (384, 256, 200, 2, 0), (300, 700, 1032, 0, 0)])
+def test_gemm_tc_ragged_shapes_and_schedules(s, m, n, k, teams, chunk):
+    a, b = I.gemm_inputs(m, n, k)
+    absab = np.abs(a.astype(np.float64)) @ np.abs(b.astype(np.float64))
+    c = run_gemm_tc(s, a, b, False, teams, chunk)
+    check_tc(c, O.gemm_bf16(a, b), absab, k)
+    c3 = run_gemm_tc(s, a, b, True, teams, chunk)
+    check_tc(c3, O.gemm(a, b), absab, k)
+
+
+def test_gemm_tc_row_subrange_touches_only_its_rows(s):
+    a, b = I.gemm_inputs(300, 256, 64)
+    c = run_gemm_tc(s, a, b, False, lb=50, ub=250)
+    ref = O.gemm_bf16(a, b)
+    assert np.linalg.norm(c[50:250] - ref[50:250]) <= 1e-5 * np.linalg.norm(ref[50:250])
+    assert np.all(c[:50] == -3.0) and np.all(c[250:] == -3.0)
+
+
+def test_gemm_tc_1024_accuracy_bounds(s):
+    a, b = I.gemm_inputs(1024, 1024, 1024)
+    ref64 = O.gemm(a, b)
+    c = run_gemm_tc(s, a, b, False)
+    # FP32 accumulation of exact bfloat16 products: close to the exactly summed bfloat16 product
+    refb = O.gemm_bf16(a, b)
+    assert np.linalg.norm(c - refb) <= 1e-5 * np.linalg.norm(refb)
+    # stated bound for the bfloat16 path against FP64
+    assert np.linalg.norm(c - ref64) <= 1e-2 * np.linalg.norm(ref64)
+    c3 = run_gemm_tc(s, a, b, True)
+    assert np.linalg.norm(c3 - ref64) <= 1e-5 * np.linalg.norm(ref64)
+
+
+def test_gemm_tc_full_size_sampled_and_freivalds(s):
+    a, b = I.gemm_inputs(4096, 4096, 4096)
+    g = np.random.default_rng(13)
+    rows, cols = g.integers(0, 4096, 4096), g.integers(0, 4096, 4096)
+    r = g.choice([-1.0, 1.0], 4096)
+    for x3 in (False, True):
+        c = run_gemm_tc(s, a, b, x3)
+        if x3:
+            ref = np.einsum("ik,ki->i", a[rows].astype(np.float64), b[:, cols].astype(np.float64))
+            rhs = a.astype(np.float64) @ (b.astype(np.float64) @ r)
+        else:
+            ab, bb = O.bf16_round(a).astype(np.float64), O.bf16_round(b).astype(np.float64)
+            ref = np.einsum("ik,ki->i", ab[rows], bb[:, cols])
+            rhs = ab @ (bb @ r)
+        assert np.linalg.norm(c[rows, cols] - ref) <= 1e-5 * np.linalg.norm(ref)
+        assert np.linalg.norm(c.astype(np.float64) @ r - rhs) <= 1e-5 * np.linalg.norm(rhs)
+
+
+def test_gemm_tc_rejects_unaligned_k(s):
+    a = np.zeros(64 * 12, np.uint16)
+    c = np.zeros(64 * 64, np.float32)
+    ha, hc = s.map(a, U.UPIR_MAP_TO), s.map(c, U.UPIR_MAP_TO)
+    r = U.upir_spmd_region(s.ctx, 0, 0)
+    with pytest.raises(U.UpirError) as e:
+        U.upir_loop_checked(s.ctx, r, U.make_loop_desc(0, 64, collapse=2, body=U.UPIR_BODY_GEMM_BF16,
+                                                       bufs=[ha, ha, hc], scalars=[64, 64, 12]))
+    assert e.value.status == U.UPIR_EUNSUPPORTED
+    U.upir_region_destroy(r)
+    s.unmap(ha)
+    s.unmap(hc)

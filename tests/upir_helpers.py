@@ -27,7 +27,10 @@ class Session:
         r = U.upir_spmd_region(self.ctx, teams, units)
         for lp in loops:
             U.upir_loop_checked(self.ctx, r, U.make_loop_desc(**lp))
-        U.upir_region_submit(r, flags)
+        try:
+            U.upir_region_submit(r, flags)
+        except U.UpirError as e:
+            raise U.UpirError(e.status, "upir_region_submit: " + U.lib.upir_last_error(self.ctx).decode())
         U.upir_ctx_wait(self.ctx)
         if keep:
             return r
