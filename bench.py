@@ -409,6 +409,14 @@ def extra_batch(rt: Runtime, count: int = 512) -> dict:
     return out
 
 
+def extra_costmodel(rt: Runtime) -> dict:
+    """Learned schedule cost model: trained on ~17k timed variants of 800
+    AXPY/Jacobi/matvec regions, ranking the candidate schedules of 1000 unseen
+    regions drawn like the batched-region workload (seed 7)."""
+    from paper_2209_10643_b300 import costmodel as CM
+    return CM.run_protocol(rt.ctx)
+
+
 def cpu_baseline_jacobi(budget_s: float = 12.0) -> dict:
     """The oracle (FP64 numpy, single thread) on a bounded sample of the
     headline workload: the full 4096^2 grid for as many sweeps as fit the budget."""
@@ -432,7 +440,8 @@ def extra_workloads(rt: Runtime, pk: dict) -> dict:
             "matvec_16384": lambda: extra_matvec(rt, pk),
             "gemm_f32_4096": lambda: extra_gemm_f32(rt),
             "gemm_tc_4096": lambda: extra_gemm_tc(rt, pk),
-            "batch_512_regions": lambda: extra_batch(rt)}
+            "batch_512_regions": lambda: extra_batch(rt),
+            "cost_model": lambda: extra_costmodel(rt)}
 
 
 def run_ours(args) -> None:

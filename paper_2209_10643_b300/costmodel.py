@@ -1,0 +1,332 @@
+"""Learned schedule cost model for worksharing loops, built on the C ABI.
+
+For a loop region the model scores candidate schedules (schedule kind, chunk,
+units per team, teams) from 12 features and picks the one it predicts
+fastest.  Its training data are timings the runtime measures itself
+(exhaustive autotuning of candidate schedules with CUDA events); training runs
+on the GPU through the library's MLP forward/backward/SGD kernels.  The
+exhaustive autotuner remains the fallback and the judge of the model's regret.
+
+Features (12): op one-hot (AXPY, JACOBI5, MATVEC, GEMM), log2 trip count,
+bytes per iteration, flops per iteration, schedule one-hot (static, dynamic),
+log2(chunk + 1), log2 units per team, log2 teams.
+"""
+from __future__ import annotations
+
+import math
+import statistics
+
+import numpy as np
+
+import paper_2209_10643_b300 as U
+
+OP_AXPY, OP_JACOBI, OP_MATVEC, OP_GEMM = range(4)
+NFEAT = 12
+
+
+def features(op: int, trip: int, bytes_per_iter: float, flops_per_iter: float, sched: int,
+             chunk: int, units: int, teams: int) -> np.ndarray:
+    f = np.zeros(NFEAT, np.float32)
+    f[op] = 1.0
+    f[4] = math.log2(max(trip, 1))
+    f[5] = bytes_per_iter
+    f[6] = flops_per_iter
+    f[7 + sched] = 1.0
+    f[9] = math.log2(chunk + 1)
+    f[10] = math.log2(max(units, 1))
+    f[11] = math.log2(max(teams, 1))
+    return f
+
+
+def candidates(op: int) -> list[dict]:
+    """Candidate schedules per loop kind (teams = 0: the planner sizes the grid)."""
+    out = []
+    if op == OP_AXPY:
+        for units in (128, 256, 512, 1024):
+            for chunk in (0, 4, 64, 1024):
+                out.append(dict(sched=U.UPIR_SCHED_STATIC, chunk=chunk, units=units, teams=0))
+            for chunk in (256, 4096, 65536):
+                out.append(dict(sched=U.UPIR_SCHED_DYNAMIC, chunk=chunk, units=units, teams=0))
+    elif op == OP_JACOBI:
+        for units in (128, 256, 512):
+            for chunk in (0, 1, 4):
+                out.append(dict(sched=U.UPIR_SCHED_STATIC, chunk=chunk, units=units, teams=0))
+            for chunk in (1, 4):
+                out.append(dict(sched=U.UPIR_SCHED_DYNAMIC, chunk=chunk, units=units, teams=0))
+    else:
+        for units in (128, 256, 512, 1024):
+            for chunk in (0, 1, 8):
+                out.append(dict(sched=U.UPIR_SCHED_STATIC, chunk=chunk, units=units, teams=0))
+            for chunk in (1, 8):
+                out.append(dict(sched=U.UPIR_SCHED_DYNAMIC, chunk=chunk, units=units, teams=0))
+    return out
+
+
+def heuristic(op: int, trip: int) -> dict:
+    """The paper's CUDA geometry: 256 units per team, one iteration per unit
+    ((n + 255) / 256 teams), static schedule."""
+    teams = max(1, min((trip + 255) // 256, 2 ** 31 - 1)) if op == OP_AXPY else 0
+    return dict(sched=U.UPIR_SCHED_STATIC, chunk=0, units=256, teams=teams)
+
+
+class Pool:
+    """Device buffers large enough for every problem of a sweep; each problem
+    runs on prefixes of them (their values are seeded uniform[-1, 1), which
+    is all the timing needs)."""
+
+    def __init__(self, ctx: int, max_vec: int, max_grid: int, max_mat: int, seed: int = 11):
+        import torch
+        g = torch.Generator(device="cuda").manual_seed(seed)
+
+        def buf(n):
+            return (torch.rand(max(n, 1), device="cuda", generator=g) * 2 - 1).contiguous()
+
+        self.ctx = ctx
+        self.x, self.y = buf(max_vec), buf(max_vec)
+        self.u0, self.u1 = buf(max_grid), buf(max_grid)
+        self.a = buf(max_mat)
+        self.var = torch.zeros(16, device="cuda")
+        torch.cuda.synchronize()
+
+    def wrap(self, t, n: int, offset: int = 0) -> int:
+        return U.upir_data_map_device(self.ctx, t.data_ptr() + 4 * offset, 4 * n)
+
+
+class Problem:
+    """One region's loop on pool prefixes, run under candidate schedules."""
+
+    def __init__(self, pool: Pool, spec: dict):
+        self.ctx, self.spec, self.handles = pool.ctx, spec, []
+        op = spec["op"]
+        w = lambda t, n, o=0: self._h(pool.wrap(t, n, o))  # noqa: E731
+        if op == OP_AXPY:
+            n = spec["n"]
+            hx, hy, hd = w(pool.x, n), w(pool.y, n), w(pool.var, 1)
+            self.trip, self.bpi, self.fpi = n, 12.0, 4.0
+            self.loop = dict(lb=0, ub=n, body=U.UPIR_BODY_AXPY, bufs=[hx, hy], scalars=[2.5],
+                             reductions=[(U.UPIR_RED_ADD, U.UPIR_F32, U.UPIR_TERM_XY, hd, 0)])
+        elif op == OP_JACOBI:
+            side = spec["side"]
+            h0, h1, hr = w(pool.u0, side * side), w(pool.u1, side * side), w(pool.var, 1, 1)
+            self.trip, self.bpi, self.fpi = (side - 2) ** 2, 8.0, 6.0
+            self.loop = dict(lb=1, ub=side - 1, collapse=2, body=U.UPIR_BODY_JACOBI5, bufs=[h0, h1],
+                             scalars=[side, side],
+                             reductions=[(U.UPIR_RED_MAX, U.UPIR_F32, U.UPIR_TERM_RESID, hr, 0)])
+        else:
+            rows, cols = spec["rows"], spec["cols"]
+            ha, hx, hy = w(pool.a, rows * cols), w(pool.x, cols), w(pool.y, rows)
+            self.trip, self.bpi, self.fpi = rows, 4.0 * cols, 2.0 * cols
+            self.loop = dict(lb=0, ub=rows, body=U.UPIR_BODY_MATVEC, bufs=[ha, hx, hy],
+                             scalars=[rows, cols])
+        self.op = op
+
+    def _h(self, h):
+        self.handles.append(h)
+        return h
+
+    def region(self, cand: dict) -> int:
+        r = U.upir_spmd_region(self.ctx, cand["teams"], cand["units"])
+        try:
+            U.upir_loop_checked(self.ctx, r, U.make_loop_desc(**self.loop, sched=cand["sched"],
+                                                              chunk=cand["chunk"]))
+        except U.UpirError:
+            U.upir_region_destroy(r)
+            raise
+        return r
+
+    def measure(self, cand: dict, reps: int = 3) -> tuple[float, np.ndarray]:
+        """Median device time (ms) of the loop under `cand`, and its features."""
+        r = self.region(cand)
+        teams, units = U.upir_region_loop_geometry(r, 0)
+        U.upir_region_submit(r, 0)  # warm-up
+        U.upir_ctx_set_timing(self.ctx, True)
+        for _ in range(reps):
+            U.upir_region_submit(r, 0)
+        U.upir_ctx_set_timing(self.ctx, False)
+        rec = U.upir_ctx_timings(self.ctx)
+        U.upir_region_destroy(r)
+        ms = statistics.median(t for _, t in rec)
+        return ms, features(self.op, self.trip, self.bpi, self.fpi, cand["sched"], cand["chunk"],
+                            units, teams)
+
+    def close(self):
+        for h in self.handles:
+            U.upir_data_unmap(self.ctx, h)
+        self.handles.clear()
+
+
+def sweep(pool: Pool, specs: list[dict], reps: int = 3):
+    """Exhaustive autotuning of every candidate schedule of every region.
+
+    Returns per region its (candidate, ms, features) rows and the heuristic's
+    (ms, features)."""
+    out = []
+    for sp in specs:
+        pb = Problem(pool, sp)
+        rows = []
+        for cand in candidates(sp["op"]):
+            try:
+                ms, f = pb.measure(cand, reps)
+            except U.UpirError:
+                continue
+            rows.append((cand, ms, f))
+        try:
+            hms, hf = pb.measure(heuristic(sp["op"], pb.trip), reps)
+        except U.UpirError:
+            hms, hf = float("nan"), None
+        pb.close()
+        out.append({"spec": sp, "rows": rows, "heuristic": (hms, hf)})
+    return out
+
+
+def training_specs(count: int = 800, seed: int = 10) -> list[dict]:
+    """Regions like the AXPY, Jacobi and matvec workloads at log-spaced sizes."""
+    g = np.random.Generator(np.random.Philox(seed))
+    specs = []
+    for i in range(count):
+        op = i % 3
+        if op == OP_AXPY:
+            specs.append({"op": OP_AXPY, "n": int(2 ** g.uniform(10, 25))})
+        elif op == OP_JACOBI:
+            specs.append({"op": OP_JACOBI, "side": int(2 ** g.uniform(6, 12))})
+        else:
+            rows = int(2 ** g.uniform(8, 14))
+            cols = int(min(max(2 ** g.uniform(5, 24) // rows, 1), 16384))
+            specs.append({"op": OP_MATVEC, "rows": rows, "cols": cols})
+    return specs
+
+
+def dataset(results) -> tuple[np.ndarray, np.ndarray]:
+    """Features and log2(time in microseconds) of every measured variant."""
+    f = np.stack([r[2] for res in results for r in res["rows"]])
+    t = np.array([math.log2(r[1] * 1e3) for res in results for r in res["rows"]], np.float32)
+    return f, t
+
+
+class GpuMLP:
+    """The 12-64-64-1 MLP, its parameters and data resident on the GPU,
+    trained with the library's kernels."""
+
+    def __init__(self, ctx: int, params: dict):
+        import torch
+        self.ctx, self.torch = ctx, torch
+        flat = np.concatenate([params[k].astype(np.float32).ravel()
+                               for k in ("W1", "b1", "W2", "b2", "W3", "b3")])
+        assert flat.size == U.UPIR_MLP_NPARAM
+        self.p = torch.from_numpy(flat).cuda()
+        self.g = torch.zeros_like(self.p)
+        self.loss = torch.zeros(1, device="cuda")
+
+    def params(self) -> dict:
+        flat = self.p.cpu().numpy()
+        sizes = {"W1": (64, 12), "b1": (64,), "W2": (64, 64), "b2": (64,), "W3": (1, 64), "b3": (1,)}
+        out, o = {}, 0
+        for k, shp in sizes.items():
+            n = int(np.prod(shp))
+            out[k] = flat[o:o + n].reshape(shp).copy()
+            o += n
+        return out
+
+    def predict(self, x) -> "object":
+        x = self.torch.as_tensor(x, device="cuda", dtype=self.torch.float32).contiguous()
+        y = self.torch.empty(x.shape[0], device="cuda")
+        U.upir_mlp_forward(self.ctx, self.p.data_ptr(), x.data_ptr(), x.shape[0], y.data_ptr())
+        return y
+
+    def step(self, x, t, lr: float) -> None:
+        U.upir_mlp_backward(self.ctx, self.p.data_ptr(), x.data_ptr(), t.data_ptr(), x.shape[0],
+                            self.g.data_ptr(), self.loss.data_ptr())
+        U.upir_mlp_sgd(self.ctx, self.p.data_ptr(), self.g.data_ptr(), lr)
+
+    def train(self, x_np: np.ndarray, t_np: np.ndarray, epochs: int = 300, batch: int = 512,
+              lr: float = 0.05, seed: int = 0) -> list[float]:
+        torch = self.torch
+        x = torch.from_numpy(x_np.astype(np.float32)).cuda()
+        t = torch.from_numpy(t_np.astype(np.float32)).cuda()
+        g = np.random.Generator(np.random.Philox(seed))
+        n = x.shape[0]
+        losses = []
+        for ep in range(epochs):
+            perm = torch.from_numpy(g.permutation(n)).cuda()
+            lr_ep = lr * 0.5 * (1 + math.cos(math.pi * ep / epochs))  # cosine decay
+            for s in range(0, n, batch):
+                idx = perm[s:s + batch]
+                xb, tb = x[idx].contiguous(), t[idx].contiguous()
+                self.step(xb, tb, lr_ep)
+            losses.append(float(self.loss.item()))
+        return losses
+
+
+def standardize(f: np.ndarray, mean=None, std=None):
+    if mean is None:
+        mean, std = f.mean(axis=0), f.std(axis=0)
+        std = np.where(std > 0, std, 1.0)
+    return ((f - mean) / std).astype(np.float32), mean, std
+
+
+def regret_report(results, model: GpuMLP, mean, std) -> dict:
+    """Per region: the model's pick (argmin of predictions over the measured
+    candidates) against the exhaustive best, and the heuristic likewise."""
+    regrets, h_regrets = [], []
+    for res in results:
+        rows = res["rows"]
+        if not rows:
+            continue
+        f = np.stack([r[2] for r in rows])
+        pred = model.predict(standardize(f, mean, std)[0]).cpu().numpy()
+        times = np.array([r[1] for r in rows])
+        best = times.min()
+        regrets.append(times[int(np.argmin(pred))] / best - 1.0)
+        hms = res["heuristic"][0]
+        if not math.isnan(hms):
+            h_regrets.append(hms / best - 1.0)
+    r = np.array(regrets)
+    h = np.array(h_regrets)
+    return {"regions": int(r.size),
+            "model_regret": {"mean": float(r.mean()), "median": float(np.median(r)),
+                             "p90": float(np.quantile(r, 0.9))},
+            "heuristic_regret": {"mean": float(h.mean()), "median": float(np.median(h)),
+                                 "p90": float(np.quantile(h, 0.9))} if h.size else None}
+
+
+def run_protocol(ctx: int, n_train: int = 800, n_eval: int = 1000, epochs: int = 300, seed_eval: int = 7,
+                 eval_t_hi: float = 1e7, reps: int = 3) -> dict:
+    """Autotune the training regions exhaustively, train the MLP on the GPU,
+    then rank the candidate schedules of unseen regions (drawn like the
+    batched-region workload) and report its regret against the exhaustive
+    autotuner, next to the regret of the paper's default geometry."""
+    import time
+
+    import upir_inputs as I
+
+    t0 = time.perf_counter()
+    train_specs = training_specs(n_train)
+    eval_specs = I.batched_region_specs(n_eval, seed=seed_eval, t_hi=eval_t_hi)
+    max_vec = max([sp.get("n", 0) for sp in train_specs + eval_specs] + [16384])
+    max_grid = max(sp.get("side", 0) for sp in train_specs + eval_specs) ** 2
+    max_mat = max(sp.get("rows", 0) * sp.get("cols", 0) for sp in train_specs + eval_specs)
+    pool = Pool(ctx, max_vec, max_grid, max_mat)
+    train = sweep(pool, train_specs, reps)
+    t1 = time.perf_counter()
+    f, t = dataset(train)
+    fs, mean, std = standardize(f)
+    tmean = float(t.mean())
+    model = GpuMLP(ctx, I.mlp_init(seed=9))
+    losses = model.train(fs, t - tmean, epochs=epochs)
+    pred = model.predict(fs).cpu().numpy() + tmean
+    rmse = float(np.sqrt(np.mean((pred - t) ** 2)))
+    t2 = time.perf_counter()
+    ev = sweep(pool, eval_specs, reps)
+    t3 = time.perf_counter()
+
+    rep = regret_report(ev, model, mean, std)
+    fe, te = dataset(ev)
+    pe = model.predict(standardize(fe, mean, std)[0]).cpu().numpy() + tmean
+    rep.update({
+        "train_regions": len(train_specs), "train_variants": int(f.shape[0]),
+        "eval_variants": int(fe.shape[0]), "epochs": epochs,
+        "loss_first": losses[0], "loss_last": losses[-1],
+        "train_rmse_log2": rmse, "eval_rmse_log2": float(np.sqrt(np.mean((pe - te) ** 2))),
+        "seconds": {"autotune_train": t1 - t0, "train": t2 - t1, "autotune_eval": t3 - t2},
+    })
+    return rep

@@ -16,9 +16,11 @@
 //   warps 2..17 read the accumulator with tcgen05.ld (32 rows x 64 columns
 //               per warp) and release the buffer, so the MMAs of the next
 //               K segment (or tile) overlap this epilogue work.
-// K is accumulated in segments of kSegKB k-blocks: each segment starts a
+// K is accumulated in segments of seg_kb k-blocks: each segment starts a
 // fresh TMEM accumulator and the epilogue adds the segments in FP32 registers
-// (round to nearest).  The tensor core's own accumulation is not
+// (round to nearest, in segment order).  The split form uses segments of 1024
+// by default; the plain bfloat16 form one segment, its error being dominated
+// by the rounding of its operands to bfloat16.  The tensor core's own accumulation is not
 // round-to-nearest, so its error grows with the number of accumulation steps;
 // cutting the chain at every 1024 values of K keeps it near FP32 rounding.
 // Every mbarrier wait is bounded: when one runs out the team records the
@@ -37,7 +39,7 @@ constexpr int TC_BM = 128, TC_BN = 256, TC_BK = 64;
 constexpr int TC_THREADS = 576;  // producer warp, MMA warp, 16 epilogue warps
 constexpr int TC_EPI_THREADS = 512;
 constexpr int TC_EPI_COLS = 64;  // accumulator columns per epilogue warp
-constexpr int kSegKB = 16;       // k-blocks (of 64) per accumulation segment
+constexpr int kSegKB = 16;       // default k-blocks (of 64) per accumulation segment
 constexpr uint32_t TC_TMEM_COLS = 512;
 constexpr int TC_A_BYTES = TC_BM * TC_BK * 2;  // 16 KB
 constexpr int TC_B_BYTES = TC_BN * TC_BK * 2;  // 32 KB
@@ -51,6 +53,7 @@ struct TcParams {
     SchedConst sk;
     long long spin_limit;
     int* err_word;
+    int seg_kb;  // k-blocks per accumulation segment
 };
 
 template <bool X3>
@@ -103,6 +106,17 @@ __device__ __forceinline__ void tc_fence_before() {
 
 __device__ __forceinline__ void tc_fence_after() {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                   "=r"(r[7])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
 }
 
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
@@ -245,7 +259,7 @@ gemm_tc_kernel(const TcParams p, const __grid_constant__ CUtensorMap tm_ah,
             uint32_t ph = 0, aph = 0;
             bool issued_any = false, ok = true;
             for (int64_t t = tc_next_tile(it, p); t >= 0 && ok && !abort_flag; t = tc_next_tile(it, p)) {
-                for (int kb0 = 0; kb0 < nkb && ok; kb0 += kSegKB) {
+                for (int kb0 = 0; kb0 < nkb && ok; kb0 += p.seg_kb) {
                     // one K segment into a fresh accumulator buffer
                     if (!tc_wait(&tempty[acc], aph ^ 1u, p, &abort_flag)) {
                         ok = false;
@@ -253,7 +267,7 @@ gemm_tc_kernel(const TcParams p, const __grid_constant__ CUtensorMap tm_ah,
                     }
                     tc_fence_after();
                     const uint32_t d_tmem = tmem_base + (uint32_t)(acc * TC_BN);
-                    const int kb1 = min(kb0 + kSegKB, nkb);
+                    const int kb1 = min(kb0 + p.seg_kb, nkb);
                     for (int kb = kb0; kb < kb1; ++kb) {
                         if (!tc_wait(&full[s], ph, p, &abort_flag)) {
                             ok = false;
@@ -288,13 +302,13 @@ gemm_tc_kernel(const TcParams p, const __grid_constant__ CUtensorMap tm_ah,
         }
     } else {
         // ---------------- epilogue: TMEM -> FP32 registers -> C ----------------
-        const int q = warp & 3;             // TMEM lane quadrant this warp may access
+        const int q = warp & 3;               // TMEM lane quadrant this warp may access
         const int quarter = (warp - 2) >> 2;  // which 64 of the 256 columns
         TcTiles it = tc_first(p);
         int acc = 0;
         uint32_t aph = 0;
         const bool vec_ok = (p.N % 4) == 0;
-        const int nseg = (nkb + kSegKB - 1) / kSegKB;
+        const int nseg = (nkb + p.seg_kb - 1) / p.seg_kb;
         bool ok = true;
         for (int64_t t = tc_next_tile(it, p); t >= 0 && ok && !abort_flag; t = tc_next_tile(it, p)) {
             float sum[TC_EPI_COLS];
@@ -307,11 +321,11 @@ gemm_tc_kernel(const TcParams p, const __grid_constant__ CUtensorMap tm_ah,
                 const uint32_t taddr = tmem_base + ((uint32_t)(32 * q) << 16) +
                                        (uint32_t)(acc * TC_BN + quarter * TC_EPI_COLS);
 #pragma unroll
-                for (int c = 0; c < TC_EPI_COLS / 16; ++c) {
-                    float v[16];
-                    tmem_ld16(taddr + (uint32_t)(c * 16), v);
+                for (int c = 0; c < TC_EPI_COLS / 8; ++c) {
+                    float v[8];
+                    tmem_ld8(taddr + (uint32_t)(c * 8), v);
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) sum[c * 16 + j] = seg ? __fadd_rn(sum[c * 16 + j], v[j]) : v[j];
+                    for (int j = 0; j < 8; ++j) sum[c * 8 + j] = seg ? __fadd_rn(sum[c * 8 + j], v[j]) : v[j];
                 }
                 tc_fence_before();
                 mbar_arrive(&tempty[acc]);
@@ -407,6 +421,11 @@ upir_status plan_gemm_tc(upir_region r, LoopRec& lp, int64_t M, int64_t N, int64
     tp.chunk = lp.chunk;
     tp.spin_limit = ctx->spin_limit;
     tp.err_word = ctx->err_word;
+    // UPIR_HINT_TILE_M on a tensor-core GEMM: k-blocks of 64 per accumulation
+    // segment.  Default: one segment for GEMM_BF16 (its error is dominated by
+    // the bfloat16 rounding of the operands), 16 (K = 1024) for GEMM_BF16X3.
+    const int nkb = (int)ceil_div(K, TC_BK);
+    tp.seg_kb = lp.tile_m > 0 ? lp.tile_m : (x3 ? kSegKB : std::max(nkb, 1));
     lp.teams = r->teams ? r->teams : (int)std::max<int64_t>(1, std::min<int64_t>(tp.ntiles, kNumSMs));
     tp.sk = make_sched_const(tp.ntiles, lp.chunk, lp.teams);
     memcpy(lp.tc_params, &tp, sizeof(tp));

@@ -138,6 +138,7 @@ extern "C" upir_status upir_finalize(upir_ctx ctx) {
         cudaEventDestroy(t.b);
     }
     for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
+    dev_free(ctx, ctx->mlp_scratch, ctx->mlp_scratch_bytes);
     dev_free(ctx, ctx->err_word, 256);
     cudaStreamSynchronize(ctx->stream);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);

@@ -1,6 +1,7 @@
 // Host-side runtime objects behind the opaque C ABI handles.
 #pragma once
 
+#include <algorithm>
 #include <string>
 #include <unordered_set>
 #include <memory>
@@ -78,6 +79,8 @@ struct upir_ctx_s {
     bool timing = false;
     std::vector<upir::TimingRec> timings;
     std::vector<cudaEvent_t> event_pool;
+    void* mlp_scratch = nullptr;      // per-team gradient partials of the cost model
+    size_t mlp_scratch_bytes = 0;
 };
 
 namespace upir {

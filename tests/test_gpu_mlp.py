@@ -1,0 +1,96 @@
+"""The cost model's MLP kernels against the FP64 oracle: predictions, the
+loss, per-tensor gradients (normwise 1e-2, the stated bound for bfloat16
+weights with FP32 accumulation; measured far below), one SGD step, and
+bit-for-bit repeatability of the fixed-order batch reduction."""
+import numpy as np
+import pytest
+
+import upir_inputs as I
+from oracle import upir_oracle as O
+
+pytestmark = pytest.mark.gpu
+
+U = pytest.importorskip("paper_2209_10643_b300")
+torch = pytest.importorskip("torch")
+
+KEYS = ("W1", "b1", "W2", "b2", "W3", "b3")
+SHAPES = {"W1": (64, 12), "b1": (64,), "W2": (64, 64), "b2": (64,), "W3": (1, 64), "b3": (1,)}
+
+
+def flat(p):
+    return np.concatenate([p[k].astype(np.float32).ravel() for k in KEYS])
+
+
+def unflat(v):
+    out, o = {}, 0
+    for k in KEYS:
+        n = int(np.prod(SHAPES[k]))
+        out[k] = v[o:o + n].reshape(SHAPES[k])
+        o += n
+    return out
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = U.upir_init(0)
+    yield c
+    U.upir_finalize(c)
+
+
+@pytest.mark.parametrize("batch", [1, 63, 64, 65, 1000])
+def test_forward_backward_sgd_vs_oracle(ctx, batch):
+    p = I.mlp_init(seed=9)
+    # biases away from zero so every unit is exercised
+    g = np.random.default_rng(1)
+    p["b1"] = (g.standard_normal(64) * 0.1).astype(np.float32)
+    p["b2"] = (g.standard_normal(64) * 0.1).astype(np.float32)
+    x, t = I.mlp_dataset(batch, seed=8)
+    pd = torch.from_numpy(flat(p)).cuda()
+    xd, td = torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda()
+    pred = torch.empty(batch, device="cuda")
+    grad = torch.empty(U.UPIR_MLP_NPARAM, device="cuda")
+    loss = torch.empty(1, device="cuda")
+    U.upir_mlp_forward(ctx, pd.data_ptr(), xd.data_ptr(), batch, pred.data_ptr())
+    U.upir_mlp_backward(ctx, pd.data_ptr(), xd.data_ptr(), td.data_ptr(), batch, grad.data_ptr(),
+                        loss.data_ptr())
+    U.upir_ctx_wait(ctx)
+    yref, cache = O.mlp_forward(p, x)
+    assert np.max(np.abs(pred.cpu().numpy() - yref)) <= 1e-5 * max(1.0, np.max(np.abs(yref)))
+    assert abs(loss.item() - O.mlp_loss(yref, t)) <= 1e-5 * O.mlp_loss(yref, t)
+    gref = O.mlp_backward(cache, yref, t)
+    got = unflat(grad.cpu().numpy())
+    for k in KEYS:
+        err = np.linalg.norm(got[k] - gref[k]) / max(np.linalg.norm(gref[k]), 1e-30)
+        assert err <= 1e-2, (k, err)
+        assert err <= 1e-4, (k, err)  # what FP32 accumulation actually reaches here
+    lr = 0.01
+    U.upir_mlp_sgd(ctx, pd.data_ptr(), grad.data_ptr(), lr)
+    U.upir_ctx_wait(ctx)
+    new = unflat(pd.cpu().numpy())
+    want = O.mlp_sgd(p, gref, lr)
+    for k in KEYS:
+        assert np.linalg.norm(new[k] - want[k]) <= 1e-6 * max(np.linalg.norm(want[k]), 1.0), k
+
+
+def test_backward_is_bitwise_repeatable(ctx):
+    p = I.mlp_init(seed=3)
+    x, t = I.mlp_dataset(5000, seed=4)
+    pd = torch.from_numpy(flat(p)).cuda()
+    xd, td = torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda()
+    outs = []
+    for _ in range(2):
+        grad = torch.empty(U.UPIR_MLP_NPARAM, device="cuda")
+        U.upir_mlp_backward(ctx, pd.data_ptr(), xd.data_ptr(), td.data_ptr(), 5000, grad.data_ptr(), None)
+        U.upir_ctx_wait(ctx)
+        outs.append(grad.cpu().numpy())
+    assert np.array_equal(outs[0].view(np.uint32), outs[1].view(np.uint32))
+
+
+def test_training_reduces_the_loss_on_a_learnable_target(ctx):
+    from paper_2209_10643_b300.costmodel import GpuMLP
+    g = np.random.default_rng(2)
+    x = g.standard_normal((4096, 12)).astype(np.float32)
+    t = (x[:, 0] * 0.5 - x[:, 3] + 0.25 * x[:, 5] * x[:, 5]).astype(np.float32)
+    m = GpuMLP(ctx, I.mlp_init(seed=5))
+    losses = m.train(x, t, epochs=40, batch=256, lr=0.05)
+    assert losses[-1] < 0.1 * losses[0]
