@@ -7,8 +7,9 @@
 // 128 x 256 output tiles and the tile loop is workshared statically over
 // persistent teams, one per SM.  Each team is warp-specialised:
 //   warp 0      one thread issues TMA copies of the A and B^T k-blocks
-//               (128 x 64 and 256 x 64 bfloat16, 128-byte swizzle) into an
-//               S-stage shared-memory ring (full/empty mbarriers);
+//               (128 x BK and 256 x BK bfloat16, BK = 64 with the 128-byte
+//               swizzle, or 32 with the 64-byte swizzle for the split form)
+//               into a 4-stage shared-memory ring (full/empty mbarriers);
 //   warp 1      allocates 512 TMEM columns (two 128 x 256 FP32 accumulators)
 //               and one thread issues tcgen05.mma (M=128, N=256, K=16) from
 //               shared-memory descriptors, committing each stage back to the
@@ -35,14 +36,12 @@ namespace upir {
 
 namespace {
 
-constexpr int TC_BM = 128, TC_BN = 256, TC_BK = 64;
+constexpr int TC_BM = 128, TC_BN = 256;
 constexpr int TC_THREADS = 576;  // producer warp, MMA warp, 16 epilogue warps
 constexpr int TC_EPI_THREADS = 512;
 constexpr int TC_EPI_COLS = 64;  // accumulator columns per epilogue warp
-constexpr int kSegKB = 16;       // default k-blocks (of 64) per accumulation segment
+constexpr int kSegK = 1024;      // default K per accumulation segment of the split form
 constexpr uint32_t TC_TMEM_COLS = 512;
-constexpr int TC_A_BYTES = TC_BM * TC_BK * 2;  // 16 KB
-constexpr int TC_B_BYTES = TC_BN * TC_BK * 2;  // 32 KB
 
 struct TcParams {
     float* C;
@@ -54,12 +53,41 @@ struct TcParams {
     long long spin_limit;
     int* err_word;
     int seg_kb;  // k-blocks per accumulation segment
+    // work units: full tiles first, then `split_tiles` tiles cut into `parts`
+    // contiguous K ranges; parts > 0 land in `work`, added to C afterwards
+    int64_t full_tiles, split_tiles, nunits;
+    int parts;
+    float* work;
 };
 
+struct TcUnit {
+    int64_t tile;
+    int kb0, kb1, part;
+    int64_t split_idx;
+};
+
+__device__ __forceinline__ TcUnit tc_unit(int64_t u, const TcParams& p, int nkb) {
+    if (u < p.full_tiles) return TcUnit{u, 0, nkb, 0, -1};
+    const int64_t v = u - p.full_tiles;
+    const int64_t si = v / p.parts;
+    const int part = (int)(v - si * p.parts);
+    return TcUnit{p.full_tiles + si, (int)((int64_t)part * nkb / p.parts),
+                  (int)((int64_t)(part + 1) * nkb / p.parts), part, si};
+}
+
+// Per variant: bfloat16 uses 64-wide k-blocks (one 128-byte swizzled row,
+// 4 stages); the split form, three MMAs per k-step, uses 32-wide k-blocks
+// (64-byte swizzle, 4 stages of four operand tiles).
 template <bool X3>
 struct TcCfg {
-    static constexpr int STAGES = X3 ? 2 : 4;
-    static constexpr int STAGE_BYTES = X3 ? 2 * (TC_A_BYTES + TC_B_BYTES) : (TC_A_BYTES + TC_B_BYTES);
+    static constexpr int BK = X3 ? 32 : 64;
+    static constexpr int ROW_BYTES = BK * 2;                 // swizzle width
+    static constexpr uint32_t SBO = 8 * ROW_BYTES;           // 8-row swizzle atom
+    static constexpr uint64_t LAYOUT = X3 ? 4 : 2;           // 64- or 128-byte swizzle
+    static constexpr int A_BYTES = TC_BM * BK * 2;
+    static constexpr int B_BYTES = TC_BN * BK * 2;
+    static constexpr int STAGES = 4;
+    static constexpr int STAGE_BYTES = X3 ? 2 * (A_BYTES + B_BYTES) : (A_BYTES + B_BYTES);
     static constexpr size_t SMEM = (size_t)STAGES * STAGE_BYTES + 1024;
 };
 
@@ -74,15 +102,16 @@ constexpr uint32_t tc_idesc() {
 }
 
 // Shared-memory matrix descriptor of a K-major operand tile written by TMA
-// with the 128-byte swizzle: rows of 128 bytes, 8-row (1024-byte) swizzle
-// atoms stacked along M/N, so the stride between atoms is 1024 bytes.
+// with a 64- or 128-byte swizzle: rows of ROW_BYTES, 8-row swizzle atoms
+// stacked along M/N, so the stride between atoms is 8 * ROW_BYTES.
+template <class Cfg>
 __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
     uint64_t d = 0;
     d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);   // start address
-    d |= (uint64_t)(16u >> 4) << 16;            // leading byte offset (unused for this layout)
-    d |= (uint64_t)(1024u >> 4) << 32;          // stride byte offset
+    d |= (uint64_t)(16u >> 4) << 16;            // leading byte offset (unused for these layouts)
+    d |= (uint64_t)(Cfg::SBO >> 4) << 32;       // stride byte offset
     d |= (uint64_t)1 << 46;                     // descriptor version
-    d |= (uint64_t)2 << 61;                     // 128-byte swizzle
+    d |= Cfg::LAYOUT << 61;                     // swizzle mode
     return d;
 }
 
@@ -145,7 +174,7 @@ __device__ __forceinline__ bool tc_wait(uint64_t* bar, uint32_t parity, const Tc
     return false;
 }
 
-// Tiles of this team under the loop's static schedule, in order.
+// Work units of this team under the loop's static schedule, in order.
 struct TcTiles {
     int64_t next, end, chunk_j;
 };
@@ -154,7 +183,7 @@ __device__ __forceinline__ int64_t tc_next_tile(TcTiles& it, const TcParams& p) 
     if (it.next < it.end) return it.next++;
     if (p.chunk > 0 && it.chunk_j < p.sk.nchunks) {
         it.next = it.chunk_j * p.chunk;
-        it.end = min(it.next + p.chunk, p.ntiles);
+        it.end = min(it.next + p.chunk, p.nunits);
         it.chunk_j += gridDim.x;
         return it.next++;
     }
@@ -185,7 +214,7 @@ gemm_tc_kernel(const TcParams p, const __grid_constant__ CUtensorMap tm_ah,
     unsigned char* ring = reinterpret_cast<unsigned char*>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int nkb = (int)((p.K + TC_BK - 1) / TC_BK);
+    const int nkb = (int)((p.K + Cfg::BK - 1) / Cfg::BK);
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) {
@@ -213,7 +242,7 @@ gemm_tc_kernel(const TcParams p, const __grid_constant__ CUtensorMap tm_ah,
     const uint32_t tmem_base = tmem_base_sh;
 
     auto stage_a = [&](int s) { return ring + (size_t)s * Cfg::STAGE_BYTES; };
-    auto stage_b = [&](int s) { return ring + (size_t)s * Cfg::STAGE_BYTES + TC_A_BYTES * (X3 ? 2 : 1); };
+    auto stage_b = [&](int s) { return ring + (size_t)s * Cfg::STAGE_BYTES + Cfg::A_BYTES * (X3 ? 2 : 1); };
 
     if (warp == 0) {
         if (lane == 0) {
@@ -224,20 +253,21 @@ gemm_tc_kernel(const TcParams p, const __grid_constant__ CUtensorMap tm_ah,
             uint32_t issued_parity[S];
             bool issued[S];
             for (int k = 0; k < S; ++k) issued[k] = false, issued_parity[k] = 0;
-            for (int64_t t = tc_next_tile(it, p); t >= 0 && !abort_flag; t = tc_next_tile(it, p)) {
-                const int64_t mt = t % p.tiles_m, nt = t / p.tiles_m;
+            for (int64_t u = tc_next_tile(it, p); u >= 0 && !abort_flag; u = tc_next_tile(it, p)) {
+                const TcUnit w = tc_unit(u, p, nkb);
+                const int64_t mt = w.tile % p.tiles_m, nt = w.tile / p.tiles_m;
                 const int32_t m0 = (int32_t)(p.row_lb + mt * TC_BM), n0 = (int32_t)(nt * TC_BN);
-                for (int kb = 0; kb < nkb; ++kb) {
+                for (int kb = w.kb0; kb < w.kb1; ++kb) {
                     if (!tc_wait(&empty[s], ph ^ 1u, p, &abort_flag)) break;
                     mbar_arrive_expect_tx(&full[s], Cfg::STAGE_BYTES);
-                    const int32_t k0 = kb * TC_BK;
+                    const int32_t k0 = kb * Cfg::BK;
                     unsigned char* a = stage_a(s);
                     unsigned char* b = stage_b(s);
                     tma_load_2d(a, &tm_ah, &full[s], k0, m0);
                     tma_load_2d(b, &tm_bh, &full[s], k0, n0);
                     if (X3) {
-                        tma_load_2d(a + TC_A_BYTES, &tm_al, &full[s], k0, m0);
-                        tma_load_2d(b + TC_B_BYTES, &tm_bl, &full[s], k0, n0);
+                        tma_load_2d(a + Cfg::A_BYTES, &tm_al, &full[s], k0, m0);
+                        tma_load_2d(b + Cfg::B_BYTES, &tm_bl, &full[s], k0, n0);
                     }
                     issued[s] = true;
                     issued_parity[s] = ph;
@@ -258,8 +288,9 @@ gemm_tc_kernel(const TcParams p, const __grid_constant__ CUtensorMap tm_ah,
             int s = 0, acc = 0;
             uint32_t ph = 0, aph = 0;
             bool issued_any = false, ok = true;
-            for (int64_t t = tc_next_tile(it, p); t >= 0 && ok && !abort_flag; t = tc_next_tile(it, p)) {
-                for (int kb0 = 0; kb0 < nkb && ok; kb0 += p.seg_kb) {
+            for (int64_t u = tc_next_tile(it, p); u >= 0 && ok && !abort_flag; u = tc_next_tile(it, p)) {
+                const TcUnit w = tc_unit(u, p, nkb);
+                for (int kb0 = w.kb0; kb0 < w.kb1 && ok; kb0 += p.seg_kb) {
                     // one K segment into a fresh accumulator buffer
                     if (!tc_wait(&tempty[acc], aph ^ 1u, p, &abort_flag)) {
                         ok = false;
@@ -267,7 +298,7 @@ gemm_tc_kernel(const TcParams p, const __grid_constant__ CUtensorMap tm_ah,
                     }
                     tc_fence_after();
                     const uint32_t d_tmem = tmem_base + (uint32_t)(acc * TC_BN);
-                    const int kb1 = min(kb0 + p.seg_kb, nkb);
+                    const int kb1 = min(kb0 + p.seg_kb, w.kb1);
                     for (int kb = kb0; kb < kb1; ++kb) {
                         if (!tc_wait(&full[s], ph, p, &abort_flag)) {
                             ok = false;
@@ -276,13 +307,13 @@ gemm_tc_kernel(const TcParams p, const __grid_constant__ CUtensorMap tm_ah,
                         tc_fence_after();
                         const uint32_t a = smem_u32(stage_a(s)), b = smem_u32(stage_b(s));
 #pragma unroll
-                        for (int k = 0; k < TC_BK / 16; ++k) {
+                        for (int k = 0; k < Cfg::BK / 16; ++k) {
                             const uint32_t koff = (uint32_t)k * 32u;  // 16 bfloat16 along K
                             const uint32_t accum = (kb > kb0 || k > 0) ? 1u : 0u;
-                            tc_mma(d_tmem, smem_desc(a + koff), smem_desc(b + koff), idesc, accum);
+                            tc_mma(d_tmem, smem_desc<Cfg>(a + koff), smem_desc<Cfg>(b + koff), idesc, accum);
                             if (X3) {
-                                tc_mma(d_tmem, smem_desc(a + koff), smem_desc(b + TC_B_BYTES + koff), idesc, 1u);
-                                tc_mma(d_tmem, smem_desc(a + TC_A_BYTES + koff), smem_desc(b + koff), idesc, 1u);
+                                tc_mma(d_tmem, smem_desc<Cfg>(a + koff), smem_desc<Cfg>(b + Cfg::B_BYTES + koff), idesc, 1u);
+                                tc_mma(d_tmem, smem_desc<Cfg>(a + Cfg::A_BYTES + koff), smem_desc<Cfg>(b + koff), idesc, 1u);
                             }
                         }
                         issued_any = true;
@@ -308,9 +339,10 @@ gemm_tc_kernel(const TcParams p, const __grid_constant__ CUtensorMap tm_ah,
         int acc = 0;
         uint32_t aph = 0;
         const bool vec_ok = (p.N % 4) == 0;
-        const int nseg = (nkb + p.seg_kb - 1) / p.seg_kb;
         bool ok = true;
-        for (int64_t t = tc_next_tile(it, p); t >= 0 && ok && !abort_flag; t = tc_next_tile(it, p)) {
+        for (int64_t u = tc_next_tile(it, p); u >= 0 && ok && !abort_flag; u = tc_next_tile(it, p)) {
+            const TcUnit w = tc_unit(u, p, nkb);
+            const int nseg = (w.kb1 - w.kb0 + p.seg_kb - 1) / p.seg_kb;
             float sum[TC_EPI_COLS];
             for (int seg = 0; seg < nseg; ++seg) {
                 if (!tc_wait(&tfull[acc], aph, p, &abort_flag)) {
@@ -332,7 +364,16 @@ gemm_tc_kernel(const TcParams p, const __grid_constant__ CUtensorMap tm_ah,
                 if (++acc == 2) acc = 0, aph ^= 1u;
             }
             if (!ok) break;
-            const int64_t mt = t % p.tiles_m, nt = t / p.tiles_m;
+            if (w.part > 0) {
+                // a later K part of a split tile: to its workspace tile, added to C afterwards
+                float* dst = p.work + ((w.split_idx * (p.parts - 1) + (w.part - 1)) * TC_BM + 32 * q + lane) * TC_BN +
+                             quarter * TC_EPI_COLS;
+#pragma unroll
+                for (int c = 0; c < TC_EPI_COLS; c += 4)
+                    *reinterpret_cast<float4*>(dst + c) = make_float4(sum[c], sum[c + 1], sum[c + 2], sum[c + 3]);
+                continue;
+            }
+            const int64_t mt = w.tile % p.tiles_m, nt = w.tile / p.tiles_m;
             const int64_t row = p.row_lb + mt * TC_BM + 32 * q + lane;
             const int64_t n0 = nt * TC_BN + quarter * TC_EPI_COLS;
             if (row < p.row_ub) {
@@ -359,6 +400,24 @@ gemm_tc_kernel(const TcParams p, const __grid_constant__ CUtensorMap tm_ah,
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;"
                      ::"r"(tmem_base), "r"(TC_TMEM_COLS) : "memory");
+    }
+}
+
+// C += the later K parts of each split tile, in part order.
+__global__ void __launch_bounds__(256) tc_fixup_kernel(const TcParams p) {
+    const int64_t per_tile = (int64_t)TC_BM * TC_BN;
+    const int64_t total = p.split_tiles * per_tile;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t si = e / per_tile, r = (e % per_tile) / TC_BN, c = e % TC_BN;
+        const int64_t tile = p.full_tiles + si;
+        const int64_t mt = tile % p.tiles_m, nt = tile / p.tiles_m;
+        const int64_t row = p.row_lb + mt * TC_BM + r, col = nt * TC_BN + c;
+        if (row >= p.row_ub || col >= p.N) continue;
+        float v = p.C[row * p.N + col];
+        for (int part = 1; part < p.parts; ++part)
+            v = __fadd_rn(v, p.work[((si * (p.parts - 1) + part - 1) * TC_BM + r) * TC_BN + c]);
+        p.C[row * p.N + col] = v;
     }
 }
 
@@ -421,13 +480,54 @@ upir_status plan_gemm_tc(upir_region r, LoopRec& lp, int64_t M, int64_t N, int64
     tp.chunk = lp.chunk;
     tp.spin_limit = ctx->spin_limit;
     tp.err_word = ctx->err_word;
-    // UPIR_HINT_TILE_M on a tensor-core GEMM: k-blocks of 64 per accumulation
-    // segment.  Default: one segment for GEMM_BF16 (its error is dominated by
-    // the bfloat16 rounding of the operands), 16 (K = 1024) for GEMM_BF16X3.
-    const int nkb = (int)ceil_div(K, TC_BK);
-    tp.seg_kb = lp.tile_m > 0 ? lp.tile_m : (x3 ? kSegKB : std::max(nkb, 1));
+    // UPIR_HINT_TILE_M on a tensor-core GEMM: k-blocks per accumulation
+    // segment (64 wide for GEMM_BF16, 32 for GEMM_BF16X3).  Default: one
+    // segment for GEMM_BF16 (its error is dominated by the bfloat16 rounding of
+    // the operands), K = 1024 per segment for GEMM_BF16X3.
+    const int bk = x3 ? TcCfg<true>::BK : TcCfg<false>::BK;
+    const int nkb = (int)ceil_div(K, bk);
+    tp.seg_kb = lp.tile_m > 0 ? lp.tile_m : (x3 ? kSegK / bk : std::max(nkb, 1));
     lp.teams = r->teams ? r->teams : (int)std::max<int64_t>(1, std::min<int64_t>(tp.ntiles, kNumSMs));
-    tp.sk = make_sched_const(tp.ntiles, lp.chunk, lp.teams);
+    tp.full_tiles = tp.ntiles;
+    tp.split_tiles = 0;
+    tp.parts = 1;
+    tp.nunits = tp.ntiles;
+    int64_t chunk_eff = lp.chunk;
+    const int bk0 = x3 ? TcCfg<true>::BK : TcCfg<false>::BK;
+    const int nkb0 = (int)ceil_div(K, bk0);
+    if (!r->teams && lp.chunk == 0 && tp.ntiles > 0) {
+        // The planner sizes the grid.  The bfloat16 form (bound by
+        // shared-memory traffic, sensitive to L2 contention) takes the fewest
+        // teams that give every team the same number of tiles; the split form
+        // (three MMAs per operand load) keeps one team per SM and cuts the
+        // tiles of the last, partial wave into K parts for the idle teams.
+        // With fewer tiles than SMs both cut every tile into K parts.  Units
+        // are dealt round-robin (static, chunk 1).
+        const int64_t waves = ceil_div(tp.ntiles, kNumSMs);
+        if (!x3) lp.teams = (int)ceil_div(tp.ntiles, waves);
+        const int64_t T = kNumSMs;
+        const int64_t rem = (x3 || waves == 1) ? tp.ntiles % T : 0;
+        if (rem > 0 && rem * 2 <= T) {
+            const int64_t parts = std::min<int64_t>(std::min<int64_t>(T / rem, 4), std::max(nkb0 / 2, 1));
+            if (parts > 1) {
+                tp.split_tiles = rem;
+                tp.full_tiles = tp.ntiles - rem;
+                tp.parts = (int)parts;
+                tp.nunits = tp.full_tiles + rem * parts;
+                lp.teams = (int)std::min<int64_t>(T, tp.nunits);
+            }
+        }
+        chunk_eff = 1;
+    }
+    tp.chunk = chunk_eff;
+    tp.sk = make_sched_const(tp.nunits, chunk_eff, lp.teams);
+    if (tp.parts > 1) {
+        const size_t bytes = (size_t)tp.split_tiles * (tp.parts - 1) * TC_BM * TC_BN * sizeof(float);
+        lp.scratch = dev_alloc(ctx, bytes);
+        if (!lp.scratch) return fail(ctx, UPIR_ENOMEM, "upir_loop: GEMM split-K workspace of %zu bytes", bytes);
+        lp.scratch_bytes = bytes;
+        tp.work = static_cast<float*>(lp.scratch);
+    }
     memcpy(lp.tc_params, &tp, sizeof(tp));
     lp.skip = lp.trip == 0 || N == 0;
     if (lp.skip || K == 0) {
@@ -441,7 +541,7 @@ upir_status plan_gemm_tc(upir_region r, LoopRec& lp, int64_t M, int64_t N, int64
     const uint32_t box_rows[4] = {TC_BM, TC_BM, TC_BN, TC_BN};
     for (int i = 0; i < 4; ++i) {
         upir_status s2 = encode_tmap_2d(ctx, &lp.tmap[i], bases[i], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
-                                        (uint64_t)K, rows[i], TC_BK, box_rows[i], 1);
+                                        (uint64_t)K, rows[i], (uint32_t)bk, box_rows[i], bk * 2);
         if (s2 != UPIR_OK) return s2;
     }
     return UPIR_OK;
@@ -459,6 +559,10 @@ cudaError_t launch_gemm_tc_loop(upir_ctx, LoopRec& lp, cudaStream_t s) {
         if (!tc_configure<false>()) return cudaGetLastError();
         gemm_tc_kernel<false><<<lp.teams, TC_THREADS, TcCfg<false>::SMEM, s>>>(tp, m[0], m[1], m[2], m[3]);
     }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || tp.parts <= 1) return e;
+    const int64_t elems = tp.split_tiles * TC_BM * TC_BN;
+    tc_fixup_kernel<<<(unsigned)std::min<int64_t>((elems + 255) / 256, kNumSMs * 16), 256, 0, s>>>(tp);
     return cudaGetLastError();
 }
 

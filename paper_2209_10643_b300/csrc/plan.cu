@@ -75,7 +75,7 @@ using PFN_encodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32
 
 upir_status encode_tmap_2d(upir_ctx ctx, CUtensorMap* m, const void* base, int dtype_code,
                            int elem_bytes, uint64_t cols, uint64_t rows, uint32_t box_cols,
-                           uint32_t box_rows, int swizzle_128b) {
+                           uint32_t box_rows, int swizzle_bytes) {
     static PFN_encodeTiled fn = nullptr;
     if (!fn) {
         cudaDriverEntryPointQueryResult q;
@@ -92,7 +92,9 @@ upir_status encode_tmap_2d(upir_ctx ctx, CUtensorMap* m, const void* base, int d
     const cuuint32_t estr[2] = {1, 1};
     CUresult r = fn(m, (CUtensorMapDataType)dtype_code, 2, const_cast<void*>(base), dims, strides,
                     box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                    swizzle_128b ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
+                    swizzle_bytes == 128 ? CU_TENSOR_MAP_SWIZZLE_128B
+                    : swizzle_bytes == 64 ? CU_TENSOR_MAP_SWIZZLE_64B
+                    : swizzle_bytes == 32 ? CU_TENSOR_MAP_SWIZZLE_32B : CU_TENSOR_MAP_SWIZZLE_NONE,
                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return fail(ctx, UPIR_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
     return UPIR_OK;

@@ -102,9 +102,10 @@ upir_status plan_gemm_tc(upir_region r, LoopRec& lp, int64_t M, int64_t N, int64
 cudaError_t launch_gemm_tc_loop(upir_ctx ctx, LoopRec& lp, cudaStream_t s);
 void destroy_batch(upir_batch b);
 
-// Encode a 2D tiled TMA descriptor (row-major [rows][cols] of `elem_bytes`).
+// Encode a 2D tiled TMA descriptor (row-major [rows][cols] of `elem_bytes`);
+// swizzle_bytes is 0 (none), 32, 64 or 128.
 upir_status encode_tmap_2d(upir_ctx ctx, CUtensorMap* m, const void* base, int dtype_code,
                            int elem_bytes, uint64_t cols, uint64_t rows, uint32_t box_cols,
-                           uint32_t box_rows, int swizzle_128b);
+                           uint32_t box_rows, int swizzle_bytes);
 
 }  // namespace upir
