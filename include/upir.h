@@ -336,9 +336,11 @@ upir_status upir_ctx_set_spin_limit(upir_ctx ctx, int64_t spin_limit);
  * y[i] = fma(a, x[i], y[i]) for 0 <= i < n, then
  *   *sum_y    += sum of the updated y[i]        (FP32, compensated, fixed order)
  *   *imod_sum += sum of (imod_mul * i) mod imod_mod  (int64, exact)
- * with the same kernels, geometry and therefore the same bits as an AXPY loop
- * recorded through upir_loop with a static schedule, chunk 0, planner geometry
- * and those two reduction clauses.  x, y, sum_y and imod_sum are device
+ * with the same kernels as an AXPY loop recorded through upir_loop with a
+ * static schedule, chunk 0 and those two reduction clauses, on teams of 256
+ * units with 8 iterations per unit: y and *imod_sum are identical to that
+ * loop's; *sum_y may differ in its last bits when the loop runs in another
+ * geometry (the fixed summation order follows the teams).  x, y, sum_y and imod_sum are device
  * pointers owned by the caller; the work is enqueued on `cuda_stream` (NULL:
  * the legacy default stream) of the current device and the call returns
  * without waiting.  Nothing is allocated: the reduction scratch is one fixed

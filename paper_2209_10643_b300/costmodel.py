@@ -205,7 +205,11 @@ def dataset(results) -> tuple[np.ndarray, np.ndarray]:
 
 class GpuMLP:
     """The 12-64-64-1 MLP, its parameters and data resident on the GPU,
-    trained with the library's kernels."""
+    trained with the library's kernels.
+
+    Tensors are made by torch on its current stream and consumed by the
+    library on the context's stream (and the other way round), so every
+    hand-over synchronises the producing stream first."""
 
     def __init__(self, ctx: int, params: dict):
         import torch
@@ -216,8 +220,10 @@ class GpuMLP:
         self.p = torch.from_numpy(flat).cuda()
         self.g = torch.zeros_like(self.p)
         self.loss = torch.zeros(1, device="cuda")
+        torch.cuda.current_stream().synchronize()
 
     def params(self) -> dict:
+        U.upir_ctx_wait(self.ctx)
         flat = self.p.cpu().numpy()
         sizes = {"W1": (64, 12), "b1": (64,), "W2": (64, 64), "b2": (64,), "W3": (1, 64), "b3": (1,)}
         out, o = {}, 0
@@ -227,11 +233,21 @@ class GpuMLP:
             o += n
         return out
 
-    def predict(self, x) -> "object":
+    def predict(self, x):
         x = self.torch.as_tensor(x, device="cuda", dtype=self.torch.float32).contiguous()
         y = self.torch.empty(x.shape[0], device="cuda")
+        self.torch.cuda.current_stream().synchronize()
         U.upir_mlp_forward(self.ctx, self.p.data_ptr(), x.data_ptr(), x.shape[0], y.data_ptr())
+        U.upir_ctx_wait(self.ctx)
         return y
+
+    def full_loss(self, x, t) -> float:
+        """Mean squared error over all rows (a backward pass; the gradient is discarded)."""
+        self.torch.cuda.current_stream().synchronize()
+        U.upir_mlp_backward(self.ctx, self.p.data_ptr(), x.data_ptr(), t.data_ptr(), x.shape[0],
+                            self.g.data_ptr(), self.loss.data_ptr())
+        U.upir_ctx_wait(self.ctx)
+        return float(self.loss.item())
 
     def step(self, x, t, lr: float) -> None:
         U.upir_mlp_backward(self.ctx, self.p.data_ptr(), x.data_ptr(), t.data_ptr(), x.shape[0],
@@ -239,21 +255,28 @@ class GpuMLP:
         U.upir_mlp_sgd(self.ctx, self.p.data_ptr(), self.g.data_ptr(), lr)
 
     def train(self, x_np: np.ndarray, t_np: np.ndarray, epochs: int = 300, batch: int = 512,
-              lr: float = 0.05, seed: int = 0) -> list[float]:
+              lr: float = 0.05, seed: int = 0, log_every: int = 10) -> list[float]:
+        """Minibatch SGD with a cosine learning-rate decay.  Returns the
+        full-data loss before training and every `log_every` epochs."""
         torch = self.torch
         x = torch.from_numpy(x_np.astype(np.float32)).cuda()
         t = torch.from_numpy(t_np.astype(np.float32)).cuda()
         g = np.random.Generator(np.random.Philox(seed))
         n = x.shape[0]
-        losses = []
+        losses = [self.full_loss(x, t)]
         for ep in range(epochs):
             perm = torch.from_numpy(g.permutation(n)).cuda()
+            xs, ts = x[perm].contiguous(), t[perm].contiguous()
+            torch.cuda.current_stream().synchronize()  # the shuffled copies exist
             lr_ep = lr * 0.5 * (1 + math.cos(math.pi * ep / epochs))  # cosine decay
             for s in range(0, n, batch):
-                idx = perm[s:s + batch]
-                xb, tb = x[idx].contiguous(), t[idx].contiguous()
-                self.step(xb, tb, lr_ep)
-            losses.append(float(self.loss.item()))
+                m = min(batch, n - s)
+                U.upir_mlp_backward(self.ctx, self.p.data_ptr(), xs.data_ptr() + 4 * NFEAT * s,
+                                    ts.data_ptr() + 4 * s, m, self.g.data_ptr(), self.loss.data_ptr())
+                U.upir_mlp_sgd(self.ctx, self.p.data_ptr(), self.g.data_ptr(), lr_ep)
+            U.upir_ctx_wait(self.ctx)  # xs, ts stay alive until the kernels are done
+            if (ep + 1) % log_every == 0 or ep == epochs - 1:
+                losses.append(self.full_loss(x, t))
         return losses
 
 

@@ -84,6 +84,7 @@ __device__ __forceinline__ void axpy_range(const ElemParams& p, Terms& t, int64_
         ((reinterpret_cast<uintptr_t>(p.x + i) ^ reinterpret_cast<uintptr_t>(p.y + i)) & 15) == 0;
     if (same_phase) {
         while (i < iend && (reinterpret_cast<uintptr_t>(p.x + i) & 15)) axpy_one<FOP, IOP>(p, t, i++);
+#pragma unroll 2
         for (; i + 4 <= iend; i += 4) {
             const float4 xv = __ldcs(reinterpret_cast<const float4*>(p.x + i));
             const float4 yv = __ldcs(reinterpret_cast<const float4*>(p.y + i));

@@ -33,6 +33,7 @@ __device__ __forceinline__ void axpy_tile(const BatchParams& P, const BatchRegio
     const bool vec = ((reinterpret_cast<uintptr_t>(x + e0) | reinterpret_cast<uintptr_t>(y + e0)) & 15) == 0;
     if (vec) {
         const int64_t n4 = (e1 - e0) / 4;
+#pragma unroll 4
         for (int64_t g = threadIdx.x; g < n4; g += blockDim.x) {
             const float4 xv = __ldcs(reinterpret_cast<const float4*>(x + e0) + g);
             const float4 yv = __ldcs(reinterpret_cast<const float4*>(y + e0) + g);

@@ -493,11 +493,14 @@ upir_status plan_loop(upir_region r, const upir_loop_desc* d, LoopRec& lp) {
     ep.imod_inc = imod_inc;
     ep.imod_minv = imod_mod >= 2 ? (unsigned long long)(((unsigned __int128)1 << 64) / (unsigned long long)imod_mod) : 0;
     const int64_t trip = lp.trip;
-    const int U = lp.units;
     // iterations per worker the blocked schedule aims for: 4 (one 128-bit access)
     // without reductions, 8 with them (halves the per-element share of the
     // warp-level reduction tree at the same coalescing)
     const int64_t vdef = has_red ? 8 : 4;
+    // reducing element loops run better in smaller teams (more, shorter-lived
+    // blocks overlap their block-level reduction trees with other blocks' loads)
+    if (!U0 && has_red && lp.body == UPIR_BODY_AXPY) lp.units = 128;
+    const int U = lp.units;
     const int64_t V = (lp.body == UPIR_BODY_AXPY && lp.step == 1) ? (lp.vec ? lp.vec : vdef)
                       : (lp.body == UPIR_BODY_IMOD ? vdef : 1);
     if (lp.sched == UPIR_SCHED_STATIC) {

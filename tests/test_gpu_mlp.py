@@ -50,6 +50,7 @@ def test_forward_backward_sgd_vs_oracle(ctx, batch):
     pred = torch.empty(batch, device="cuda")
     grad = torch.empty(U.UPIR_MLP_NPARAM, device="cuda")
     loss = torch.empty(1, device="cuda")
+    torch.cuda.synchronize()  # torch's copies are done before the library's stream reads them
     U.upir_mlp_forward(ctx, pd.data_ptr(), xd.data_ptr(), batch, pred.data_ptr())
     U.upir_mlp_backward(ctx, pd.data_ptr(), xd.data_ptr(), td.data_ptr(), batch, grad.data_ptr(),
                         loss.data_ptr())
@@ -64,6 +65,7 @@ def test_forward_backward_sgd_vs_oracle(ctx, batch):
         assert err <= 1e-2, (k, err)
         assert err <= 1e-4, (k, err)  # what FP32 accumulation actually reaches here
     lr = 0.01
+    torch.cuda.synchronize()
     U.upir_mlp_sgd(ctx, pd.data_ptr(), grad.data_ptr(), lr)
     U.upir_ctx_wait(ctx)
     new = unflat(pd.cpu().numpy())
@@ -77,9 +79,11 @@ def test_backward_is_bitwise_repeatable(ctx):
     x, t = I.mlp_dataset(5000, seed=4)
     pd = torch.from_numpy(flat(p)).cuda()
     xd, td = torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda()
+    torch.cuda.synchronize()
     outs = []
     for _ in range(2):
         grad = torch.empty(U.UPIR_MLP_NPARAM, device="cuda")
+        torch.cuda.synchronize()
         U.upir_mlp_backward(ctx, pd.data_ptr(), xd.data_ptr(), td.data_ptr(), 5000, grad.data_ptr(), None)
         U.upir_ctx_wait(ctx)
         outs.append(grad.cpu().numpy())
