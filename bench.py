@@ -35,6 +35,9 @@ from paper_2209_10643_b300.sharding import aggregate_throughput, dist_env  # noq
 N_GRID = 4096
 SWEEPS = 100
 JACOBI_BYTES_PER_SWEEP = 8 * (N_GRID - 2) ** 2
+# DRAM bytes (read + write) of one launch of the sweep kernel on this grid, from
+# an ncu capture of the current kernel (cold launch, 3-stage ring, 64 x 128 tiles)
+JACOBI_TRAFFIC_BYTES = 70_092_544 + 11_383_808
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -227,7 +230,7 @@ def headline(rt: Runtime, steps: int, warmup: int, pk: dict, device: int):
                      "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": achieved / pk["hbm_gbs"],
                      "peak_source": pk["source"] + " (burst copy)",
                      "algorithmic_bytes_per_launch": JACOBI_BYTES_PER_SWEEP,
-                     "avg_launch_us": avg_kernel_s * 1e6, "traffic": None},
+                     "avg_launch_us": avg_kernel_s * 1e6, "traffic": JACOBI_TRAFFIC_BYTES},
         "per_launch": {"ms_per_step": lms, "avg_launch_us_with_events": per_launch_us,
                        "value": SWEEPS * JACOBI_BYTES_PER_SWEEP / (lms / 1e3) / 1e9},
         "e2e": e2e, "residual_last": float(res[-1]),

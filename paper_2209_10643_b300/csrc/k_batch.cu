@@ -78,29 +78,79 @@ __device__ __forceinline__ void axpy_tile(const BatchParams& P, const BatchRegio
     }
 }
 
+// Halo rows of the tile are staged in shared memory; shared column j holds
+// grid column c0 - 4 + j, so the tile's first column sits on a 16-byte
+// boundary.  Rows whose width is a multiple of 4 use 128-bit loads, stores
+// and shared-memory reads; other widths take the scalar path.
 __device__ __forceinline__ void jacobi_tile(const BatchParams& P, const BatchRegion& R, int64_t t,
                                             float* halo) {
-    constexpr int HW = kBatchJacCols + 2;
+    constexpr int HW = kBatchJacCols + 8;
     const int64_t band = t / R.tiles_c, tc = t - band * R.tiles_c;
     const int64_t r0 = R.lb + band * P.jac_rows;
     const int nr = (int)min((int64_t)P.jac_rows, R.lb + R.trip - r0);
     const int64_t c0 = tc * kBatchJacCols;
     const int64_t cols = R.cols;
     const float* u = R.in0;
-    for (int idx = threadIdx.x; idx < (nr + 2) * HW; idx += blockDim.x) {
-        const int64_t rr = r0 - 1 + idx / HW, cc = c0 - 1 + idx % HW;
-        halo[idx] = (cc >= 0 && cc < cols) ? u[rr * cols + cc] : 0.0f;
+    const bool vec = (cols & 3) == 0 && ((reinterpret_cast<uintptr_t>(u) | reinterpret_cast<uintptr_t>(R.out)) & 15) == 0;
+    if (vec) {
+        // all of this thread's loads are issued before any shared-memory
+        // store, so their DRAM latencies overlap instead of adding up
+        constexpr int kMaxLd = ((kBatchMaxJacRows + 2) * (HW / 4) + kBatchUnits - 1) / kBatchUnits;
+        const int n4 = (nr + 2) * (HW / 4);
+        float4 v[kMaxLd];
+#pragma unroll
+        for (int k = 0; k < kMaxLd; ++k) {
+            const int idx = threadIdx.x + k * kBatchUnits;
+            v[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (idx < n4) {
+                const int i = idx / (HW / 4), q = idx - i * (HW / 4);
+                const int64_t rr = r0 - 1 + i, cc = c0 - 4 + 4 * q;
+                if (cc >= 0 && cc + 3 < cols) v[k] = __ldcs(reinterpret_cast<const float4*>(u + rr * cols + cc));
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < kMaxLd; ++k) {
+            const int idx = threadIdx.x + k * kBatchUnits;
+            if (idx < n4) *reinterpret_cast<float4*>(halo + 4 * idx) = v[k];
+        }
+    } else {
+        for (int idx = threadIdx.x; idx < (nr + 2) * HW; idx += blockDim.x) {
+            const int i = idx / HW, j = idx - i * HW;
+            const int64_t rr = r0 - 1 + i, cc = c0 - 4 + j;
+            halo[idx] = (cc >= 0 && cc < cols) ? u[rr * cols + cc] : 0.0f;
+        }
     }
     __syncthreads();
     float racc = R.fop == UPIR_RED_MIN ? __int_as_float(0x7f800000) : -__int_as_float(0x7f800000);
-    for (int idx = threadIdx.x; idx < nr * kBatchJacCols; idx += blockDim.x) {
-        const int i = idx / kBatchJacCols, j = idx % kBatchJacCols;
-        const int64_t c = c0 + j;
-        if (c < 1 || c > cols - 2) continue;
-        const float* cen = halo + (i + 1) * HW + j + 1;
-        const float v = __fmul_rn(0.25f, __fadd_rn(__fadd_rn(cen[-HW], cen[HW]), __fadd_rn(cen[-1], cen[1])));
-        R.out[(r0 + i) * cols + c] = v;
-        if (R.fop) racc = fold(racc, fabsf(__fsub_rn(v, cen[0])), R.fop);
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5, nty = blockDim.x >> 5;
+    const int64_t c = c0 + 4 * tx;
+    const bool full = vec && c >= 1 && c + 3 <= cols - 2;
+    for (int i = ty; i < nr; i += nty) {
+        const float* cen = halo + (i + 1) * HW + 4 + 4 * tx;
+        const float4 C = *reinterpret_cast<const float4*>(cen);
+        const float4 N = *reinterpret_cast<const float4*>(cen - HW);
+        const float4 S = *reinterpret_cast<const float4*>(cen + HW);
+        const float Wl = cen[-1], Er = cen[4];
+        float vs[4], cs[4] = {C.x, C.y, C.z, C.w};
+        vs[0] = __fmul_rn(0.25f, __fadd_rn(__fadd_rn(N.x, S.x), __fadd_rn(Wl, C.y)));
+        vs[1] = __fmul_rn(0.25f, __fadd_rn(__fadd_rn(N.y, S.y), __fadd_rn(C.x, C.z)));
+        vs[2] = __fmul_rn(0.25f, __fadd_rn(__fadd_rn(N.z, S.z), __fadd_rn(C.y, C.w)));
+        vs[3] = __fmul_rn(0.25f, __fadd_rn(__fadd_rn(N.w, S.w), __fadd_rn(C.z, Er)));
+        float* out = R.out + (r0 + i) * cols + c;
+        if (full) {
+            __stcs(reinterpret_cast<float4*>(out), make_float4(vs[0], vs[1], vs[2], vs[3]));
+            if (R.fop)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) racc = fold(racc, fabsf(__fsub_rn(vs[j], cs[j])), R.fop);
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                if (c + j >= 1 && c + j <= cols - 2) {
+                    out[j] = vs[j];
+                    if (R.fop) racc = fold(racc, fabsf(__fsub_rn(vs[j], cs[j])), R.fop);
+                }
+            }
+        }
     }
     if (R.fop) {
         const float b = block_fold(racc, R.fop);
@@ -119,17 +169,18 @@ __device__ __forceinline__ void matvec_tile(const BatchParams& P, const BatchReg
     }
 }
 
-__global__ void __launch_bounds__(kBatchUnits) batch_persistent_kernel(const BatchParams P) {
-    __shared__ float halo[(kBatchMaxJacRows + 2) * (kBatchJacCols + 2)];
-    __shared__ int64_t item;
+__global__ void __launch_bounds__(kBatchUnits, 4) batch_persistent_kernel(const BatchParams P) {
+    __shared__ __align__(16) float halo[(kBatchMaxJacRows + 2) * (kBatchJacCols + 8)];
+    __shared__ int64_t item, next_item;
     __shared__ int last_team;
     griddep_wait();
+    if (threadIdx.x == 0) item = (int64_t)atomicAdd(P.counter, 1ull);
+    __syncthreads();
     for (;;) {
-        if (threadIdx.x == 0) item = (int64_t)atomicAdd(P.counter, 1ull);
-        __syncthreads();
         const int64_t k = item;
-        __syncthreads();
         if (k >= P.nitems) break;
+        // claim the following item now, so the atomic's latency overlaps this one
+        if (threadIdx.x == 0) next_item = (int64_t)atomicAdd(P.counter, 1ull);
         const int2 it = P.items[k];
         const BatchRegion& R = P.regions[it.x];
         switch (R.op) {
@@ -137,6 +188,9 @@ __global__ void __launch_bounds__(kBatchUnits) batch_persistent_kernel(const Bat
             case BOP_JACOBI: jacobi_tile(P, R, it.y, halo); break;
             default: matvec_tile(P, R, it.y); break;
         }
+        __syncthreads();  // every thread has read `item`
+        if (threadIdx.x == 0) item = next_item;
+        __syncthreads();
     }
     // the last team returns the work counter to zero for the next launch
     if (threadIdx.x == 0) {

@@ -213,3 +213,50 @@ def test_persistent_batch_rejects_unsupported_regions(s):
     U.upir_region_destroy(r)
     s.unmap(hx)
     s.unmap(hy)
+
+
+def test_allocator_failure_is_reported_without_leaks():
+    """Host-side fault injection: a caller-supplied allocator that fails on
+    its k-th call; the failing call returns UPIR_ENOMEM and every allocation
+    made is released by the time the context is finalized."""
+    import ctypes as C
+    import torch
+
+    live, calls = {}, [0]
+    fail_at = 4
+
+    @C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+    def alloc(nbytes, stream, user):
+        calls[0] += 1
+        if calls[0] == fail_at:
+            return None
+        t = torch.empty(max(int(nbytes), 1), dtype=torch.uint8, device="cuda")
+        live[t.data_ptr()] = t
+        return t.data_ptr()
+
+    @C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+    def free(ptr, nbytes, stream, user):
+        live.pop(ptr, None)
+
+    a = U.upir_allocator(alloc, free, None)
+    h = C.c_void_p()
+    torch.cuda.synchronize()
+    assert U.lib.upir_init(C.byref(h), 0, None, C.byref(a)) == U.UPIR_OK  # call 1: error word
+    ctx = h.value
+    x = np.ones(1024, np.float32)
+    bufs = []
+    statuses = []
+    for _ in range(4):  # calls 2, 3, 4 (fails), 5
+        b = C.c_void_p()
+        st = U.lib.upir_data_map(ctx, x.ctypes.data, x.nbytes, U.UPIR_MAP_TO, C.byref(b))
+        statuses.append(st)
+        if st == U.UPIR_OK:
+            bufs.append(b.value)
+    assert statuses == [U.UPIR_OK, U.UPIR_OK, U.UPIR_ENOMEM, U.UPIR_OK]
+    assert b"allocation" in U.lib.upir_last_error(ctx)
+    assert len(live) == 4  # error word + three mapped buffers
+    for b in bufs[:1]:
+        assert U.lib.upir_data_unmap(ctx, b) == U.UPIR_OK
+    assert len(live) == 3
+    U.lib.upir_finalize(ctx)  # frees the rest
+    assert len(live) == 0
