@@ -131,8 +131,11 @@ class Runtime:
         return h
 
     def flush_l2(self):
+        # Stream-ordered and not waited for: the GPU is still busy with the
+        # fill while the host enqueues the timed work, so the timed region
+        # starts with the GPU's own start of that work, not with the host's
+        # launch latency after an idle gap.
         self.flush_buf.fill_(1.0)
-        self.torch.cuda.synchronize()
 
     def region(self, loops, teams=0, units=0):
         r = self.U.upir_spmd_region(self.ctx, teams, units)

@@ -297,7 +297,10 @@ upir_status upir_batch_destroy(upir_batch batch);
 upir_status upir_batch_autotune(upir_batch batch, int32_t reps, int64_t* tiles_out);
 
 /* Taskwait at context level: wait for the stream, then read and clear the
- * device error word (ETIMEDOUT if a bounded wait ran out). */
+ * device error word (ETIMEDOUT if a bounded wait ran out).  On ETIMEDOUT the
+ * outputs of the launches in flight are undefined, and the scheduling
+ * counters of every live region's loops are cleared, so regions can be
+ * submitted again. */
 upir_status upir_ctx_wait(upir_ctx ctx);
 
 /* ------------------------------------------------------------ diagnostics -- */

@@ -16,7 +16,12 @@
 //               producer and each finished tile to the epilogue;
 //   warps 2..17 read the accumulator with tcgen05.ld (32 rows x 64 columns
 //               per warp) and release the buffer, so the MMAs of the next
-//               K segment (or tile) overlap this epilogue work.
+//               K segment (or tile) overlap this epilogue work; each thread
+//               writes its row of C with 32-byte stores (one full sector).
+// A last, partial wave of tiles is cut into 128-column halves (N = 128 MMAs)
+// so that the teams it would leave idle take a share; with fewer tiles than
+// SMs the tiles are cut along K instead, the last-finishing part of each
+// tile adding all parts in part order.
 // K is accumulated in segments of seg_kb k-blocks: each segment starts a
 // fresh TMEM accumulator and the epilogue adds the segments in FP32 registers
 // (round to nearest, in segment order).  The split form uses segments of 1024
@@ -53,26 +58,36 @@ struct TcParams {
     long long spin_limit;
     int* err_word;
     int seg_kb;  // k-blocks per accumulation segment
-    // work units: full tiles first, then `split_tiles` tiles cut into `parts`
-    // contiguous K ranges; parts > 0 land in `work`, added to C afterwards
-    int64_t full_tiles, split_tiles, nunits;
+    // work units: full tiles first, then either `half_tiles` tiles cut into
+    // two 128-column halves (N = 128 MMAs, nothing to add up), or
+    // `split_tiles` tiles cut into `parts` contiguous K ranges.  Every part of
+    // a K-split tile leaves its partial sums in `work`; the part that finishes
+    // last (per 32 x 64 block, counted in `tile_count`) adds all of them in
+    // part order and writes C.
+    int64_t full_tiles, half_tiles, split_tiles, nunits;
     int parts;
     float* work;
+    unsigned int* tile_count;
 };
+
+constexpr int TC_SUBS = (TC_BM / 32) * (TC_BN / TC_EPI_COLS);  // 32 x 64 blocks per tile, one per epilogue warp
+constexpr int TC_MAX_PARTS = 4;  // K parts of a split tile
 
 struct TcUnit {
     int64_t tile;
     int kb0, kb1, part;
     int64_t split_idx;
+    int half;  // 0: all 256 columns; 1, 2: the first or second 128
 };
 
 __device__ __forceinline__ TcUnit tc_unit(int64_t u, const TcParams& p, int nkb) {
-    if (u < p.full_tiles) return TcUnit{u, 0, nkb, 0, -1};
+    if (u < p.full_tiles) return TcUnit{u, 0, nkb, 0, -1, 0};
     const int64_t v = u - p.full_tiles;
+    if (p.half_tiles > 0) return TcUnit{p.full_tiles + (v >> 1), 0, nkb, 0, -1, 1 + (int)(v & 1)};
     const int64_t si = v / p.parts;
     const int part = (int)(v - si * p.parts);
     return TcUnit{p.full_tiles + si, (int)((int64_t)part * nkb / p.parts),
-                  (int)((int64_t)(part + 1) * nkb / p.parts), part, si};
+                  (int)((int64_t)(part + 1) * nkb / p.parts), part, si, 0};
 }
 
 // Per variant: bfloat16 uses 64-wide k-blocks (one 128-byte swizzled row,
@@ -83,21 +98,22 @@ struct TcCfg {
     static constexpr int BK = X3 ? 32 : 64;
     static constexpr int ROW_BYTES = BK * 2;                 // swizzle width
     static constexpr uint32_t SBO = 8 * ROW_BYTES;           // 8-row swizzle atom
-    static constexpr uint64_t LAYOUT = X3 ? 4 : 2;           // 64- or 128-byte swizzle
+    static constexpr uint64_t LAYOUT = ROW_BYTES == 128 ? 2 : 4;  // 128- or 64-byte swizzle
     static constexpr int A_BYTES = TC_BM * BK * 2;
     static constexpr int B_BYTES = TC_BN * BK * 2;
     static constexpr int STAGES = 4;
     static constexpr int STAGE_BYTES = X3 ? 2 * (A_BYTES + B_BYTES) : (A_BYTES + B_BYTES);
+    static constexpr int HALF_STAGE_BYTES = X3 ? 2 * (A_BYTES + B_BYTES / 2) : (A_BYTES + B_BYTES / 2);
     static constexpr size_t SMEM = (size_t)STAGES * STAGE_BYTES + 1024;
 };
 
 // kind::f16 instruction descriptor: FP32 accumulator, bfloat16 A and B, both
-// K-major, M = 128, N = 256.
-constexpr uint32_t tc_idesc() {
+// K-major, M = 128, N = 256 (or 128 for half tiles).
+constexpr uint32_t tc_idesc(int n = TC_BN) {
     return (1u << 4)                        // D format: FP32
            | (1u << 7)                      // A format: BF16
            | (1u << 10)                     // B format: BF16
-           | ((uint32_t)(TC_BN >> 3) << 17) // N / 8
+           | ((uint32_t)(n >> 3) << 17)     // N / 8
            | ((uint32_t)(TC_BM >> 4) << 24);// M / 16
 }
 
@@ -137,29 +153,71 @@ __device__ __forceinline__ void tc_fence_after() {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
 
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
-    uint32_t r[8];
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-                   "=r"(r[7])
-                 : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
-}
-
+// TMEM -> registers (32 lanes x N columns, one row per thread), with the
+// wait in the same statement so that no use of the registers can be moved
+// ahead of it.
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
     uint32_t r[16];
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
-        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-          "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr) : "memory");
 #pragma unroll
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr) : "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// 32-byte global accesses (one full sector per thread).
+__device__ __forceinline__ void st_v8_cs(float* p, const float* v) {
+    asm volatile("st.global.cs.v8.f32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};"
+                 ::"l"(p), "f"(v[0]), "f"(v[1]), "f"(v[2]), "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7])
+                 : "memory");
+}
+
+__device__ __forceinline__ void st_v8_cg(float* p, const float* v) {
+    asm volatile("st.global.cg.v8.f32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};"
+                 ::"l"(p), "f"(v[0]), "f"(v[1]), "f"(v[2]), "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7])
+                 : "memory");
+}
+
+__device__ __forceinline__ void ld_v8_cg(const float* p, float* v) {
+    asm volatile("ld.global.cg.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7])
+                 : "l"(p) : "memory");
+}
+
+// Columns [n0, n0 + n) of one row of C from v: 32-byte streaming stores when
+// the row segment is whole and aligned, else element by element up to N.
+__device__ __forceinline__ void store_row(float* crow, int64_t n0, int64_t N, bool full, const float* v, int n) {
+    if (full) {
+#pragma unroll
+        for (int c = 0; c < n; c += 8) st_v8_cs(crow + n0 + c, v + c);
+    } else {
+#pragma unroll
+        for (int c = 0; c < n; ++c)
+            if (n0 + c < N) crow[n0 + c] = v[c];
+    }
+}
+
+// Device-scope atomic add with acquire-release ordering.
+__device__ __forceinline__ unsigned int atomic_add_acq_rel(unsigned int* p, unsigned int v) {
+    unsigned int old;
+    asm volatile("atom.add.acq_rel.gpu.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
 }
 
 // Bounded wait that also gives up as soon as another role has given up.
@@ -200,11 +258,14 @@ __device__ __forceinline__ TcTiles tc_first(const TcParams& p) {
     return it;
 }
 
-template <bool X3>
+// MSEG: K may span several accumulation segments (a running sum is kept);
+// without it every unit is one segment and goes straight from TMEM out.
+template <bool X3, bool MSEG>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 gemm_tc_kernel(const TcParams p, const __grid_constant__ CUtensorMap tm_ah,
                const __grid_constant__ CUtensorMap tm_al, const __grid_constant__ CUtensorMap tm_bh,
-               const __grid_constant__ CUtensorMap tm_bl) {
+               const __grid_constant__ CUtensorMap tm_bl, const __grid_constant__ CUtensorMap tm_bh2,
+               const __grid_constant__ CUtensorMap tm_bl2) {
     using Cfg = TcCfg<X3>;
     constexpr int S = Cfg::STAGES;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -256,18 +317,23 @@ gemm_tc_kernel(const TcParams p, const __grid_constant__ CUtensorMap tm_ah,
             for (int64_t u = tc_next_tile(it, p); u >= 0 && !abort_flag; u = tc_next_tile(it, p)) {
                 const TcUnit w = tc_unit(u, p, nkb);
                 const int64_t mt = w.tile % p.tiles_m, nt = w.tile / p.tiles_m;
-                const int32_t m0 = (int32_t)(p.row_lb + mt * TC_BM), n0 = (int32_t)(nt * TC_BN);
+                const int32_t m0 = (int32_t)(p.row_lb + mt * TC_BM);
+                const int32_t n0 = (int32_t)(nt * TC_BN + (w.half == 2 ? TC_BN / 2 : 0));
+                // half tiles load 128 rows of B^T through the maps with the 128-row box
+                const CUtensorMap* mbh = w.half ? &tm_bh2 : &tm_bh;
+                const CUtensorMap* mbl = w.half ? &tm_bl2 : &tm_bl;
+                const uint32_t bytes = w.half ? Cfg::HALF_STAGE_BYTES : Cfg::STAGE_BYTES;
                 for (int kb = w.kb0; kb < w.kb1; ++kb) {
                     if (!tc_wait(&empty[s], ph ^ 1u, p, &abort_flag)) break;
-                    mbar_arrive_expect_tx(&full[s], Cfg::STAGE_BYTES);
+                    mbar_arrive_expect_tx(&full[s], bytes);
                     const int32_t k0 = kb * Cfg::BK;
                     unsigned char* a = stage_a(s);
                     unsigned char* b = stage_b(s);
                     tma_load_2d(a, &tm_ah, &full[s], k0, m0);
-                    tma_load_2d(b, &tm_bh, &full[s], k0, n0);
+                    tma_load_2d(b, mbh, &full[s], k0, n0);
                     if (X3) {
                         tma_load_2d(a + Cfg::A_BYTES, &tm_al, &full[s], k0, m0);
-                        tma_load_2d(b + Cfg::B_BYTES, &tm_bl, &full[s], k0, n0);
+                        tma_load_2d(b + Cfg::B_BYTES, mbl, &full[s], k0, n0);
                     }
                     issued[s] = true;
                     issued_parity[s] = ph;
@@ -283,13 +349,14 @@ gemm_tc_kernel(const TcParams p, const __grid_constant__ CUtensorMap tm_ah,
     } else if (warp == 1) {
         if (lane == 0) {
             // ---------------- MMA issuer ----------------
-            constexpr uint32_t idesc = tc_idesc();
+            constexpr uint32_t idesc_full = tc_idesc(), idesc_half = tc_idesc(TC_BN / 2);
             TcTiles it = tc_first(p);
             int s = 0, acc = 0;
             uint32_t ph = 0, aph = 0;
             bool issued_any = false, ok = true;
             for (int64_t u = tc_next_tile(it, p); u >= 0 && ok && !abort_flag; u = tc_next_tile(it, p)) {
                 const TcUnit w = tc_unit(u, p, nkb);
+                const uint32_t idesc = w.half ? idesc_half : idesc_full;
                 for (int kb0 = w.kb0; kb0 < w.kb1 && ok; kb0 += p.seg_kb) {
                     // one K segment into a fresh accumulator buffer
                     if (!tc_wait(&tempty[acc], aph ^ 1u, p, &abort_flag)) {
@@ -335,60 +402,122 @@ gemm_tc_kernel(const TcParams p, const __grid_constant__ CUtensorMap tm_ah,
         // ---------------- epilogue: TMEM -> FP32 registers -> C ----------------
         const int q = warp & 3;               // TMEM lane quadrant this warp may access
         const int quarter = (warp - 2) >> 2;  // which 64 of the 256 columns
+        const int sub = quarter * (TC_BM / 32) + q;
         TcTiles it = tc_first(p);
         int acc = 0;
         uint32_t aph = 0;
-        const bool vec_ok = (p.N % 4) == 0;
+        // rows of C start on 32-byte boundaries, so 8 columns go in one store
+        const bool v8_ok = (p.N % 8) == 0 && (reinterpret_cast<uintptr_t>(p.C) & 31) == 0;
         bool ok = true;
         for (int64_t u = tc_next_tile(it, p); u >= 0 && ok && !abort_flag; u = tc_next_tile(it, p)) {
             const TcUnit w = tc_unit(u, p, nkb);
             const int nseg = (w.kb1 - w.kb0 + p.seg_kb - 1) / p.seg_kb;
-            float sum[TC_EPI_COLS];
+            // each warp holds 32 rows x cw columns: 64 of a whole tile, 32 of a half
+            const int cw = w.half ? TC_EPI_COLS / 2 : TC_EPI_COLS;
+            const int64_t mt = w.tile % p.tiles_m, nt = w.tile / p.tiles_m;
+            const int64_t row = p.row_lb + mt * TC_BM + 32 * q + lane;
+            const int64_t n0 = nt * TC_BN + (w.half == 2 ? TC_BN / 2 : 0) + quarter * cw;
+            float* crow = row < p.row_ub ? p.C + row * p.N : nullptr;
+            const bool full_row = v8_ok && n0 + cw <= p.N;
+            const uint32_t tq = tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(quarter * cw);
+            // One K part of a split tile publishes its 32 x 64 block to the
+            // workspace instead of writing C.
+            const bool split = w.split_idx >= 0;
+            const int64_t part_stride = (int64_t)TC_SUBS * 32 * TC_EPI_COLS;
+            float* const work =
+                split ? p.work + ((w.split_idx * p.parts * TC_SUBS + sub) * 32 + lane) * TC_EPI_COLS : nullptr;
+            float sum[MSEG ? TC_EPI_COLS : 1];  // running sum of the earlier K segments
             for (int seg = 0; seg < nseg; ++seg) {
                 if (!tc_wait(&tfull[acc], aph, p, &abort_flag)) {
                     ok = false;
                     break;
                 }
                 tc_fence_after();
-                const uint32_t taddr = tmem_base + ((uint32_t)(32 * q) << 16) +
-                                       (uint32_t)(acc * TC_BN + quarter * TC_EPI_COLS);
+                const uint32_t ta = tq + (uint32_t)(acc * TC_BN);
+                if (MSEG && seg + 1 < nseg) {
 #pragma unroll
-                for (int c = 0; c < TC_EPI_COLS / 8; ++c) {
-                    float v[8];
-                    tmem_ld8(taddr + (uint32_t)(c * 8), v);
+                    for (int c = 0; c < TC_EPI_COLS; c += 16) {
+                        if (c < cw) {
+                            float v[16];
+                            tmem_ld16(ta + (uint32_t)c, v);
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) sum[c * 8 + j] = seg ? __fadd_rn(sum[c * 8 + j], v[j]) : v[j];
+                            for (int j = 0; j < 16; ++j)
+                                sum[MSEG ? c + j : 0] = seg ? __fadd_rn(sum[MSEG ? c + j : 0], v[j]) : v[j];
+                        }
+                    }
+                } else {
+                    // the last segment goes straight out, 32 columns at a time
+#pragma unroll
+                    for (int h = 0; h < TC_EPI_COLS; h += 32) {
+                        if (h < cw) {
+                            float v[32];
+                            tmem_ld32(ta + (uint32_t)h, v);
+                            if (MSEG && seg) {
+#pragma unroll
+                                for (int j = 0; j < 32; ++j) v[j] = __fadd_rn(sum[MSEG ? h + j : 0], v[j]);
+                            }
+                            if (split) {
+#pragma unroll
+                                for (int c = 0; c < 32; c += 8) st_v8_cg(work + w.part * part_stride + h + c, v + c);
+                            } else if (crow) {
+                                store_row(crow, n0 + h, p.N, full_row, v, 32);
+                            }
+                        }
+                    }
                 }
                 tc_fence_before();
                 mbar_arrive(&tempty[acc]);
                 if (++acc == 2) acc = 0, aph ^= 1u;
             }
             if (!ok) break;
-            if (w.part > 0) {
-                // a later K part of a split tile: to its workspace tile, added to C afterwards
-                float* dst = p.work + ((w.split_idx * (p.parts - 1) + (w.part - 1)) * TC_BM + 32 * q + lane) * TC_BN +
-                             quarter * TC_EPI_COLS;
-#pragma unroll
-                for (int c = 0; c < TC_EPI_COLS; c += 4)
-                    *reinterpret_cast<float4*>(dst + c) = make_float4(sum[c], sum[c + 1], sum[c + 2], sum[c + 3]);
-                continue;
+            if (!split) continue;
+            // Each warp takes a ticket for its block once its part is
+            // published; the warp holding the last ticket sums every part
+            // (its own included, from the workspace) in part order and writes
+            // C.  No barrier spans warps, so an aborting warp cannot strand
+            // the others.  The warp barrier orders every lane's stores before
+            // lane 0's release, and lane 0's acquire before the lanes' loads.
+            __syncwarp();
+            unsigned int last = 0;
+            if (lane == 0) {
+                unsigned int* ctr = p.tile_count + w.split_idx * TC_SUBS + sub;
+                last = atomic_add_acq_rel(ctr, 1u) == (unsigned int)(p.parts - 1) ? 1u : 0u;
+                if (last) atomicExch(ctr, 0u);  // every part has arrived: ready for the next launch
             }
-            const int64_t mt = w.tile % p.tiles_m, nt = w.tile / p.tiles_m;
-            const int64_t row = p.row_lb + mt * TC_BM + 32 * q + lane;
-            const int64_t n0 = nt * TC_BN + quarter * TC_EPI_COLS;
-            if (row < p.row_ub) {
-                float* crow = p.C + row * p.N;
+            if (!__shfl_sync(0xffffffffu, last, 0)) continue;
+            __syncwarp();
+            if (p.parts == 2) {
+                // 32 columns of both parts per round trip
 #pragma unroll
-                for (int c = 0; c < TC_EPI_COLS; c += 4) {
-                    const int64_t col = n0 + c;
-                    if (vec_ok && col + 4 <= p.N) {
-                        __stcs(reinterpret_cast<float4*>(crow + col),
-                               make_float4(sum[c], sum[c + 1], sum[c + 2], sum[c + 3]));
-                    } else {
+                for (int h = 0; h < TC_EPI_COLS; h += 32) {
+                    float a[32], b[32];
 #pragma unroll
-                        for (int j = 0; j < 4; ++j)
-                            if (col + j < p.N) crow[col + j] = sum[c + j];
+                    for (int c = 0; c < 32; c += 8) {
+                        ld_v8_cg(work + h + c, a + c);
+                        ld_v8_cg(work + part_stride + h + c, b + c);
                     }
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) a[j] = __fadd_rn(a[j], b[j]);
+                    if (crow) store_row(crow, n0 + h, p.N, full_row, a, 32);
+                }
+            } else {
+                // 16 columns of every part per round trip
+#pragma unroll
+                for (int c = 0; c < TC_EPI_COLS; c += 16) {
+                    float v[TC_MAX_PARTS][16];
+#pragma unroll
+                    for (int j = 0; j < TC_MAX_PARTS; ++j)
+                        if (j < p.parts) {
+                            ld_v8_cg(work + j * part_stride + c, v[j]);
+                            ld_v8_cg(work + j * part_stride + c + 8, v[j] + 8);
+                        }
+#pragma unroll
+                    for (int j = 1; j < TC_MAX_PARTS; ++j)
+                        if (j < p.parts) {
+#pragma unroll
+                            for (int i = 0; i < 16; ++i) v[0][i] = __fadd_rn(v[0][i], v[j][i]);
+                        }
+                    if (crow) store_row(crow, n0 + c, p.N, full_row, v[0], 16);
                 }
             }
         }
@@ -403,34 +532,17 @@ gemm_tc_kernel(const TcParams p, const __grid_constant__ CUtensorMap tm_ah,
     }
 }
 
-// C += the later K parts of each split tile, in part order.
-__global__ void __launch_bounds__(256) tc_fixup_kernel(const TcParams p) {
-    const int64_t per_tile = (int64_t)TC_BM * TC_BN;
-    const int64_t total = p.split_tiles * per_tile;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t si = e / per_tile, r = (e % per_tile) / TC_BN, c = e % TC_BN;
-        const int64_t tile = p.full_tiles + si;
-        const int64_t mt = tile % p.tiles_m, nt = tile / p.tiles_m;
-        const int64_t row = p.row_lb + mt * TC_BM + r, col = nt * TC_BN + c;
-        if (row >= p.row_ub || col >= p.N) continue;
-        float v = p.C[row * p.N + col];
-        for (int part = 1; part < p.parts; ++part)
-            v = __fadd_rn(v, p.work[((si * (p.parts - 1) + part - 1) * TC_BM + r) * TC_BN + c]);
-        p.C[row * p.N + col] = v;
+template <bool X3, bool MSEG>
+cudaError_t tc_launch(const TcParams& tp, int teams, const CUtensorMap* m, cudaStream_t s) {
+    static bool configured = false;
+    if (!configured) {
+        const cudaError_t e = cudaFuncSetAttribute(gemm_tc_kernel<X3, MSEG>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcCfg<X3>::SMEM);
+        if (e != cudaSuccess) return e;
+        configured = true;
     }
-}
-
-template <bool X3>
-bool tc_configure() {
-    static bool done = false;
-    if (!done) {
-        if (cudaFuncSetAttribute(gemm_tc_kernel<X3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)TcCfg<X3>::SMEM) != cudaSuccess)
-            return false;
-        done = true;
-    }
-    return true;
+    gemm_tc_kernel<X3, MSEG><<<teams, TC_THREADS, TcCfg<X3>::SMEM, s>>>(tp, m[0], m[1], m[2], m[3], m[4], m[5]);
+    return cudaGetLastError();
 }
 
 int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
@@ -438,7 +550,8 @@ int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 }  // namespace
 
 // The planned parameters live in the loop record's tc_params bytes; the four
-// tensor maps in its tmap[] array (A_hi, A_lo, B_hi, B_lo).
+// tensor maps in its tmap[] array (A_hi, A_lo, B_hi, B_lo, then B_hi and
+// B_lo again with a 128-row box for half tiles).
 static_assert(sizeof(TcParams) <= sizeof(LoopRec::tc_params), "TcParams must fit the loop record");
 
 upir_status plan_gemm_tc(upir_region r, LoopRec& lp, int64_t M, int64_t N, int64_t K, upir_status st) {
@@ -496,37 +609,62 @@ upir_status plan_gemm_tc(upir_region r, LoopRec& lp, int64_t M, int64_t N, int64
     const int bk0 = x3 ? TcCfg<true>::BK : TcCfg<false>::BK;
     const int nkb0 = (int)ceil_div(K, bk0);
     if (!r->teams && lp.chunk == 0 && tp.ntiles > 0) {
-        // The planner sizes the grid.  The bfloat16 form (bound by
-        // shared-memory traffic, sensitive to L2 contention) takes the fewest
-        // teams that give every team the same number of tiles; the split form
-        // (three MMAs per operand load) keeps one team per SM and cuts the
-        // tiles of the last, partial wave into K parts for the idle teams.
-        // With fewer tiles than SMs both cut every tile into K parts.  Units
-        // are dealt round-robin (static, chunk 1).
-        const int64_t waves = ceil_div(tp.ntiles, kNumSMs);
-        if (!x3) lp.teams = (int)ceil_div(tp.ntiles, waves);
+        // The planner sizes the grid.  The whole waves of tiles go one tile
+        // per team.  When a last, partial wave would leave at least half of
+        // the teams idle, its tiles are cut into two 128-column halves (N =
+        // 128 MMAs; a half takes about 2/3 of a whole tile's time, its
+        // operand traffic per flop being higher).  With fewer tiles than
+        // teams, every tile is cut into P contiguous K parts instead, P
+        // minimising the length of the wave (in tiles) plus a small charge
+        // per extra part for publishing and summing the partial tiles, with
+        // at least two k-blocks per part.  Without a split the grid is the
+        // fewest teams that give every team the same number of tiles (less
+        // L2 contention at equal wave count).  Units are dealt round-robin
+        // (static, chunk 1), so the pieces of one tile run side by side on
+        // neighbouring teams at the end.
         const int64_t T = kNumSMs;
-        const int64_t rem = (x3 || waves == 1) ? tp.ntiles % T : 0;
-        if (rem > 0 && rem * 2 <= T) {
-            const int64_t parts = std::min<int64_t>(std::min<int64_t>(T / rem, 4), std::max(nkb0 / 2, 1));
-            if (parts > 1) {
-                tp.split_tiles = rem;
-                tp.full_tiles = tp.ntiles - rem;
-                tp.parts = (int)parts;
-                tp.nunits = tp.full_tiles + rem * parts;
-                lp.teams = (int)std::min<int64_t>(T, tp.nunits);
+        const int64_t whole = tp.ntiles / T, rem = tp.ntiles % T;
+        int best_p = 1;
+        if (whole == 0) {
+            const int pmax = (int)std::min<int64_t>(TC_MAX_PARTS, std::max<int64_t>(nkb0 / 2, 1));
+            double best = 1.0;
+            for (int P = 2; P <= pmax; ++P) {
+                const double t = (double)ceil_div(rem * P, T) / P + 0.02 * (P - 1);
+                if (t < best - 1e-9) best = t, best_p = P;
             }
+        }
+        if (whole > 0 && rem > 0 && 2 * rem <= T) {
+            tp.half_tiles = rem;
+            tp.full_tiles = whole * T;
+            tp.nunits = tp.full_tiles + 2 * rem;
+            lp.teams = (int)std::min<int64_t>(T, tp.nunits);
+        } else if (best_p > 1) {
+            tp.split_tiles = rem;
+            tp.full_tiles = 0;
+            tp.parts = best_p;
+            tp.nunits = rem * best_p;
+            lp.teams = (int)std::min<int64_t>(T, tp.nunits);
+        } else {
+            lp.teams = (int)ceil_div(tp.ntiles, ceil_div(tp.ntiles, T));
         }
         chunk_eff = 1;
     }
     tp.chunk = chunk_eff;
     tp.sk = make_sched_const(tp.nunits, chunk_eff, lp.teams);
     if (tp.parts > 1) {
-        const size_t bytes = (size_t)tp.split_tiles * (tp.parts - 1) * TC_BM * TC_BN * sizeof(float);
+        // partial tiles of every part, then one arrival counter per 32 x 64 block
+        const size_t work_bytes = (size_t)tp.split_tiles * tp.parts * TC_BM * TC_BN * sizeof(float);
+        const size_t count_bytes = (size_t)tp.split_tiles * TC_SUBS * sizeof(unsigned int);
+        const size_t bytes = work_bytes + count_bytes;
         lp.scratch = dev_alloc(ctx, bytes);
         if (!lp.scratch) return fail(ctx, UPIR_ENOMEM, "upir_loop: GEMM split-K workspace of %zu bytes", bytes);
         lp.scratch_bytes = bytes;
+        lp.counter_off = work_bytes;
+        lp.counter_bytes = count_bytes;
         tp.work = static_cast<float*>(lp.scratch);
+        tp.tile_count = reinterpret_cast<unsigned int*>(static_cast<unsigned char*>(lp.scratch) + work_bytes);
+        const cudaError_t e = cudaMemsetAsync(tp.tile_count, 0, count_bytes, ctx->stream);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "upir_loop: clearing the GEMM split-K counters");
     }
     memcpy(lp.tc_params, &tp, sizeof(tp));
     lp.skip = lp.trip == 0 || N == 0;
@@ -535,11 +673,11 @@ upir_status plan_gemm_tc(upir_region r, LoopRec& lp, int64_t M, int64_t N, int64
             return fail(ctx, UPIR_EUNSUPPORTED, "upir_loop: tensor-core GEMM needs K > 0");
         return UPIR_OK;
     }
-    const void* bases[4] = {lp.bufs[0]->dev, lp.bufs[x3 ? 1 : 0]->dev, lp.bufs[na]->dev,
-                            lp.bufs[x3 ? na + 1 : na]->dev};
-    const uint64_t rows[4] = {(uint64_t)M, (uint64_t)M, (uint64_t)N, (uint64_t)N};
-    const uint32_t box_rows[4] = {TC_BM, TC_BM, TC_BN, TC_BN};
-    for (int i = 0; i < 4; ++i) {
+    const void* bases[6] = {lp.bufs[0]->dev, lp.bufs[x3 ? 1 : 0]->dev, lp.bufs[na]->dev,
+                            lp.bufs[x3 ? na + 1 : na]->dev, lp.bufs[na]->dev, lp.bufs[x3 ? na + 1 : na]->dev};
+    const uint64_t rows[6] = {(uint64_t)M, (uint64_t)M, (uint64_t)N, (uint64_t)N, (uint64_t)N, (uint64_t)N};
+    const uint32_t box_rows[6] = {TC_BM, TC_BM, TC_BN, TC_BN, TC_BN / 2, TC_BN / 2};
+    for (int i = 0; i < 6; ++i) {
         upir_status s2 = encode_tmap_2d(ctx, &lp.tmap[i], bases[i], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
                                         (uint64_t)K, rows[i], (uint32_t)bk, box_rows[i], bk * 2);
         if (s2 != UPIR_OK) return s2;
@@ -550,20 +688,14 @@ upir_status plan_gemm_tc(upir_region r, LoopRec& lp, int64_t M, int64_t N, int64
 cudaError_t launch_gemm_tc_loop(upir_ctx, LoopRec& lp, cudaStream_t s) {
     TcParams tp;
     memcpy(&tp, lp.tc_params, sizeof(tp));
-    CUtensorMap m[4];
+    CUtensorMap m[6];
     memcpy(m, lp.tmap, sizeof(m));
-    if (lp.body == UPIR_BODY_GEMM_BF16X3) {
-        if (!tc_configure<true>()) return cudaGetLastError();
-        gemm_tc_kernel<true><<<lp.teams, TC_THREADS, TcCfg<true>::SMEM, s>>>(tp, m[0], m[1], m[2], m[3]);
-    } else {
-        if (!tc_configure<false>()) return cudaGetLastError();
-        gemm_tc_kernel<false><<<lp.teams, TC_THREADS, TcCfg<false>::SMEM, s>>>(tp, m[0], m[1], m[2], m[3]);
-    }
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess || tp.parts <= 1) return e;
-    const int64_t elems = tp.split_tiles * TC_BM * TC_BN;
-    tc_fixup_kernel<<<(unsigned)std::min<int64_t>((elems + 255) / 256, kNumSMs * 16), 256, 0, s>>>(tp);
-    return cudaGetLastError();
+    const int nkb = (int)((tp.K + (lp.body == UPIR_BODY_GEMM_BF16X3 ? TcCfg<true>::BK : TcCfg<false>::BK) - 1) /
+                          (lp.body == UPIR_BODY_GEMM_BF16X3 ? TcCfg<true>::BK : TcCfg<false>::BK));
+    const bool mseg = tp.seg_kb < nkb;
+    if (lp.body == UPIR_BODY_GEMM_BF16X3)
+        return mseg ? tc_launch<true, true>(tp, lp.teams, m, s) : tc_launch<true, false>(tp, lp.teams, m, s);
+    return mseg ? tc_launch<false, true>(tp, lp.teams, m, s) : tc_launch<false, false>(tp, lp.teams, m, s);
 }
 
 }  // namespace upir

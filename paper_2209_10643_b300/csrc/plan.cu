@@ -51,6 +51,8 @@ upir_status alloc_scratch(upir_ctx ctx, LoopRec& lp, int64_t ngroups, int64_t ns
     }
     lp.scratch = p;
     lp.scratch_bytes = bytes;
+    lp.counter_off = 0;
+    lp.counter_bytes = head + gt;
     sc->chunk_counter = reinterpret_cast<unsigned long long*>(p);
     sc->ticket = reinterpret_cast<unsigned*>(p + 8);
     sc->group_tickets = reinterpret_cast<unsigned*>(p + head);

@@ -157,6 +157,12 @@ extern "C" upir_status upir_ctx_wait(upir_ctx ctx) {
     if (e != cudaSuccess) return cuda_fail(ctx, e, "reading the device error word");
     if (word != 0) {
         cudaMemsetAsync(ctx->err_word, 0, sizeof(int), ctx->stream);
+        // a launch that gave up may have left its self-clearing counters set
+        for (upir_region r : ctx->regions)
+            for (auto& lp : r->loops)
+                if (lp->scratch && lp->counter_bytes)
+                    cudaMemsetAsync(static_cast<char*>(lp->scratch) + lp->counter_off, 0, lp->counter_bytes,
+                                    ctx->stream);
         cudaStreamSynchronize(ctx->stream);
         return fail(ctx, UPIR_ETIMEDOUT, "a bounded device-side wait ran out (error word %d)", word);
     }

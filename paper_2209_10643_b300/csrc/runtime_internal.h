@@ -40,13 +40,18 @@ struct LoopRec {
     bool holds_refs = false;
     void* scratch = nullptr;
     size_t scratch_bytes = 0;
+    // Scratch bytes [counter_off, counter_off + counter_bytes) hold counters
+    // and tickets that each launch returns to zero itself; a launch that gave
+    // up on a bounded wait may leave them set, so they are cleared again when
+    // the context reports the timeout.
+    size_t counter_off = 0, counter_bytes = 0;
     size_t smem = 0;
     ElemParams ep{};
     JacobiParams jp{};
     MatvecParams mp{};
     GemmParams gp{};
     SplitParams sp{};
-    alignas(64) CUtensorMap tmap[4];
+    alignas(64) CUtensorMap tmap[6];
     alignas(16) unsigned char tc_params[256];  // tensor-core GEMM parameters
 };
 

@@ -164,6 +164,28 @@ def test_gemm_tc_exact_small_integers(s, x3):
     assert np.array_equal(run_gemm_tc(s, a, b, x3), O.gemm(a, b))
 
 
+@pytest.mark.parametrize("x3", [False, True])
+def test_gemm_tc_half_tiles_exact(s, x3):
+    # 19 x 8 = 152 tiles of 128 x 256: one whole wave on 148 SMs, then 4 tiles
+    # cut into 128-column halves; the last row and column of tiles are ragged
+    a = I.small_int_matrix(2382, 64, -8, 8, seed=3)
+    b = I.small_int_matrix(64, 1948, -8, 8, seed=4)
+    assert np.array_equal(run_gemm_tc(s, a, b, x3), O.gemm(a, b))
+
+
+@pytest.mark.parametrize("x3", [False, True])
+def test_gemm_tc_k_split_exact_and_repeatable(s, x3):
+    # 4 tiles on 148 SMs: every tile is cut into K parts that the last
+    # finishing part adds up in part order
+    a = I.small_int_matrix(256, 1024, -8, 8, seed=5)
+    b = I.small_int_matrix(1024, 512, -8, 8, seed=6)
+    assert np.array_equal(run_gemm_tc(s, a, b, x3), O.gemm(a, b))
+    a, b = I.gemm_inputs(256, 512, 1024)
+    c1 = run_gemm_tc(s, a, b, x3)
+    c2 = run_gemm_tc(s, a, b, x3)
+    assert np.array_equal(c1, c2)
+
+
 def tc_accum_tol(k):
     """Normwise tolerance for a single-segment tensor-core accumulation over K
     terms.  Its additions are not rounded to nearest, so the error grows
