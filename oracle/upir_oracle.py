@@ -10,8 +10,8 @@ generators (``upir_inputs``) feed both.
 Precision: floating-point results are computed in FP64 from the FP32 inputs
 ("FP64 mode", the reference for tolerances).  Where the CUDA path is required to
 reproduce FP32 rounding exactly (the AXPY update, the Jacobi field and its
-residuals), an FP32 "mirror" applies the same IEEE single-precision operations in
-the order the method's formula fixes.
+residuals, the 7 x 7 filter), an FP32 "mirror" applies the same IEEE
+single-precision operations in the order the method's formula fixes.
 
 Each function cites the passage of the paper it follows.  Where the paper is
 silent the reading taken is stated in the docstring.  Every function here is
@@ -341,6 +341,69 @@ def jacobi_run(u0: np.ndarray, sweeps: int, mirror_f32: bool = False):
     return u, np.array(res, dtype=np.float32 if mirror_f32 else np.float64)
 
 
+def jacobi_tb(uin: np.ndarray, lb: int, ub: int, sweeps: int, mirror_f32: bool = False):
+    """Time-blocked Jacobi body: ``sweeps`` successive 5-point sweeps of u_in
+    in which only rows [lb, ub) of the interior columns are updated and every
+    other point keeps its u_in value (the time loop of the §6 stencil nest
+    carried inside one loop body).
+
+    Each sweep is the sweep of ``jacobi_sweep_f64`` (or the FP32 mirror), its
+    values kept on the updated points only.  Returns the field after the last
+    sweep and, per sweep, the array of |new - old| over the updated points (the
+    terms of that sweep's reduction).
+    """
+    sweep = jacobi_sweep_f32 if mirror_f32 else jacobi_sweep_f64
+    dt = np.float32 if mirror_f32 else np.float64
+    u = np.asarray(uin).astype(dt)
+    terms = []
+    for _ in range(sweeps):
+        v, _ = sweep(u)
+        new = u.copy()
+        new[lb:ub, 1:-1] = v[lb:ub, 1:-1]
+        terms.append(np.abs(new[lb:ub, 1:-1] - u[lb:ub, 1:-1]).ravel())
+        u = new
+    return u, terms
+
+
+def fmaf(a: np.ndarray, b: np.ndarray, c: np.ndarray) -> np.ndarray:
+    """FP32 fused multiply-add, rounded once: a b is exact in FP64 (two 24-bit
+    significands), TwoSum recovers the FP64 sum's error, and the exact value is
+    rounded to FP32 once."""
+    p = np.asarray(a, dtype=np.float64) * np.asarray(b, dtype=np.float64)
+    hi, lo = two_sum(p, np.asarray(c, dtype=np.float64))
+    return round_f32_of_exact(hi, lo)
+
+
+def filter7_f64(x: np.ndarray, w: np.ndarray, r0: int, r1: int) -> np.ndarray:
+    """The 2D stencil with a filter of size 7 (§6, stencil evaluation: "filter
+    size = 7"), read as a 7 x 7 weighted window: for rows r in [r0, r1) and
+    columns c in [3, cols - 3),
+        out[r][c] = sum_{i=0..6} sum_{j=0..6} w[i][j] x[r + i - 3][c + j - 3]
+    in FP64.  Returns the [r1 - r0, cols - 6] block of outputs."""
+    x = np.asarray(x, dtype=np.float64)
+    w = np.asarray(w, dtype=np.float64).reshape(7, 7)
+    cols = x.shape[1]
+    out = np.zeros((r1 - r0, max(cols - 6, 0)))
+    for i in range(7):
+        for j in range(7):
+            out += w[i, j] * x[r0 + i - 3:r1 + i - 3, j:j + cols - 6]
+    return out
+
+
+def filter7_f32(x: np.ndarray, w: np.ndarray, r0: int, r1: int) -> np.ndarray:
+    """The same filter in FP32 with the summation order fixed: the accumulator
+    starts at 0 and takes w[i][j] x[...] by fused multiply-add, i outer and j
+    inner (row-major over the window), each step rounded once."""
+    x = np.asarray(x, dtype=np.float32)
+    w = np.asarray(w, dtype=np.float32).reshape(7, 7)
+    cols = x.shape[1]
+    acc = np.zeros((r1 - r0, max(cols - 6, 0)), dtype=np.float32)
+    for i in range(7):
+        for j in range(7):
+            acc = fmaf(w[i, j], x[r0 + i - 3:r1 + i - 3, j:j + cols - 6], acc)
+    return acc
+
+
 def matvec(a: np.ndarray, x: np.ndarray) -> np.ndarray:
     """y_i = sum_j A_ij x_j in FP64 (§6, matrix-vector multiplication)."""
     return a.astype(np.float64) @ x.astype(np.float64)
@@ -394,7 +457,8 @@ def gemm_bf16x3(a: np.ndarray, b: np.ndarray) -> np.ndarray:
 # ----------------------------------------------------------------------------
 
 BODY_AXPY, BODY_IMOD, BODY_JACOBI5, BODY_MATVEC, BODY_GEMM_F32, \
-    BODY_GEMM_BF16, BODY_GEMM_BF16X3, BODY_COVERAGE = range(8)
+    BODY_GEMM_BF16, BODY_GEMM_BF16X3, BODY_COVERAGE, BODY_SPLIT_BF16, \
+    BODY_JACOBI5_TB, BODY_FILTER7 = range(11)
 
 TERM_Y, TERM_XY, TERM_IMOD, TERM_IV, TERM_RESID = range(5)
 
@@ -453,6 +517,20 @@ def run_loop(dev: Device, teams: int, units: int, loop: Loop) -> dict:
         new = v[r0:r1, 1:-1]
         uout[r0:r1, 1:-1] = new.astype(np.float32)
         terms[TERM_RESID] = np.abs(new - uin[r0:r1, 1:-1].astype(np.float64)).ravel()
+    elif loop.body == BODY_JACOBI5_TB:
+        uin, uout = dev.array(loop.bufs[0]), dev.array(loop.bufs[1])
+        r0, r1 = loop.lb, loop.lb + trip * loop.step
+        if loop.step != 1 or r0 < 1 or r1 > uin.shape[0] - 1:
+            raise ValueError("Jacobi rows must be a unit-step sub-range of the interior")
+        u, sweep_terms = jacobi_tb(uin, r0, r1, int(loop.scalars[2]))
+        uout[r0:r1, 1:-1] = u[r0:r1, 1:-1].astype(np.float32)
+        terms["sweeps"] = sweep_terms
+    elif loop.body == BODY_FILTER7:
+        xin, xout = dev.array(loop.bufs[0]), dev.array(loop.bufs[1])
+        r0, r1 = loop.lb, loop.lb + trip * loop.step
+        if loop.step != 1 or r0 < 3 or r1 > xin.shape[0] - 3:
+            raise ValueError("filter rows must be a unit-step range inside [3, rows - 3)")
+        xout[r0:r1, 3:-3] = filter7_f64(xin, np.asarray(loop.scalars[2:51]), r0, r1).astype(np.float32)
     elif loop.body == BODY_MATVEC:
         a, x, y = (dev.array(h) for h in loop.bufs[:3])
         rows = [induction_value(loop.lb, loop.step, k) for k in range(trip)]
@@ -477,6 +555,13 @@ def run_loop(dev: Device, teams: int, units: int, loop: Loop) -> dict:
 
     for red in loop.reductions:
         var = dev.array(red.var)
+        if loop.body == BODY_JACOBI5_TB:
+            # one reduction per sweep, into consecutive elements of the variable
+            for k, t in enumerate(terms["sweeps"]):
+                out.setdefault("f64", {})[(red.var, red.index + k)] = reduce_f64(
+                    red.op, float(var[red.index + k]), np.asarray(t))
+                var[red.index + k] = np.float32(out["f64"][(red.var, red.index + k)])
+            continue
         if red.term in (TERM_IMOD, TERM_IV):
             if red.term == TERM_IMOD:
                 t = imod_terms(loop.lb, loop.step, trip, int(loop.scalars[-2]),

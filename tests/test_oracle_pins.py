@@ -439,3 +439,128 @@ def test_mlp_sgd_step_descends():
     l0 = O.mlp_loss(y0, t)
     p1 = O.mlp_sgd(p, O.mlp_backward(c0, y0, t), 1e-3)
     assert O.mlp_loss(O.mlp_forward(p1, x)[0], t) < l0
+
+
+# --- time-blocked Jacobi body -------------------------------------------------
+
+def test_jacobi_tb_hand_worked_5x5_two_sweeps():
+    g = gold("jacobi_5x5.json")
+    u0 = np.array(g["initial"], np.float32)
+    u, terms = O.jacobi_tb(u0, 1, 4, 2)
+    assert np.array_equal(u, np.array(g["after_sweep_2"]))
+    assert [t.max() for t in terms] == [g["residual_1"], g["residual_2"]]
+    um, tm = O.jacobi_tb(u0, 1, 4, 2, mirror_f32=True)
+    assert np.array_equal(um, np.array(g["after_sweep_2"], np.float32))
+    assert [np.float32(t.max()) for t in tm] == [np.float32(g["residual_1"]), np.float32(g["residual_2"])]
+
+
+def test_jacobi_tb_row_subrange_keeps_other_rows_fixed():
+    g = gold("jacobi_5x5_rows_1_to_2.json")
+    u0 = np.array(g["initial"], np.float32)
+    for mirror in (False, True):
+        u, terms = O.jacobi_tb(u0, g["lb"], g["ub"], g["sweeps"], mirror_f32=mirror)
+        assert np.array_equal(u, np.array(g["after"]))
+        assert [float(t.max()) for t in terms] == g["residuals"]
+
+
+@pytest.mark.parametrize("sweeps", [1, 3, 8])
+def test_jacobi_tb_harmonic_field_is_fixed_point(sweeps):
+    # u = (a + b r + c c' + d r c') / 2^k with small integers is discrete
+    # harmonic and exact in FP32: every sweep reproduces it, residuals 0
+    r, c = np.meshgrid(np.arange(17), np.arange(23), indexing="ij")
+    u0 = ((3 + 2 * r - 5 * c + r * c) / 64.0).astype(np.float32)
+    for mirror in (False, True):
+        u, terms = O.jacobi_tb(u0, 1, 16, sweeps, mirror_f32=mirror)
+        assert np.array_equal(u, u0)
+        assert all(float(t.max()) == 0.0 for t in terms)
+
+
+def test_jacobi_tb_no_rows_changes_nothing():
+    u0 = I.jacobi_grid(9, seed=1)
+    u, terms = O.jacobi_tb(u0, 4, 4, 3)
+    assert np.array_equal(u, u0) and all(t.size == 0 for t in terms)
+
+
+# --- 7 x 7 filter ---------------------------------------------------------------
+
+def _delta(i, j, v=1.0):
+    w = np.zeros((7, 7), np.float32)
+    w[i, j] = v
+    return w
+
+
+@pytest.mark.parametrize("i,j", [(3, 3), (0, 0), (6, 1), (2, 5)])
+def test_filter7_single_tap_is_a_shift(i, j):
+    # a single unit weight at (i, j) copies x[r + i - 3][c + j - 3]: pins the
+    # direction of both offsets and that the window is not transposed
+    x = np.arange(400, dtype=np.float32).reshape(20, 20)
+    want = x[3 + i - 3:17 + i - 3, j:j + 14]
+    assert np.array_equal(O.filter7_f64(x, _delta(i, j), 3, 17), want)
+    assert np.array_equal(O.filter7_f32(x, _delta(i, j), 3, 17), want)
+
+
+def test_filter7_matches_library_correlation():
+    from scipy.signal import correlate2d
+    g = np.random.default_rng(21)
+    x = g.standard_normal((40, 37))
+    w = g.standard_normal((7, 7))
+    want = correlate2d(x, w, mode="valid")          # [34, 31]: rows 3..36, cols 3..33
+    assert np.allclose(O.filter7_f64(x, w, 3, 37), want, rtol=0, atol=1e-12)
+    # a row sub-range takes the matching rows of the full result
+    assert np.allclose(O.filter7_f64(x, w, 10, 20), want[7:17], rtol=0, atol=1e-12)
+
+
+def test_filter7_linear_field_times_weight_sum():
+    # a symmetric all-ones window maps a linear field f to 49 f exactly
+    r, c = np.meshgrid(np.arange(16), np.arange(18), indexing="ij")
+    x = (5 + 3 * r - 2 * c).astype(np.float32)
+    w = np.ones((7, 7), np.float32)
+    want = 49 * x[3:13, 3:15]
+    assert np.array_equal(O.filter7_f64(x, w, 3, 13), want)
+    assert np.array_equal(O.filter7_f32(x, w, 3, 13), want)
+
+
+def test_filter7_mirror_rounds_each_tap_once():
+    # taps (3,3) then (3,4): fma(1 + 2^-12, 1 + 2^-12, -(1 + 2^-11)) = 2^-24
+    # exactly; a separately rounded product (a tie, to even) would give 0
+    x = np.zeros((7, 8), np.float32)
+    x[3, 3] = -(1 + 2.0 ** -11)
+    x[3, 4] = 1 + 2.0 ** -12
+    w = np.zeros((7, 7), np.float32)
+    w[3, 3] = 1.0
+    w[3, 3 + 1] = 1 + 2.0 ** -12
+    out = O.filter7_f32(x, w, 3, 4)
+    assert out[0, 0] == np.float32(2.0 ** -24)
+
+
+def test_filter7_mirror_within_forward_bound():
+    x = I.jacobi_grid(64, seed=3)
+    w = np.random.default_rng(4).random((7, 7)).astype(np.float32)
+    w /= w.sum()
+    exact = O.filter7_f64(x, w, 3, 61)
+    mirror = O.filter7_f32(x, w, 3, 61).astype(np.float64)
+    absw = O.filter7_f64(np.abs(x), np.abs(w), 3, 61)
+    assert np.all(np.abs(mirror - exact) <= 49 * 2.0 ** -24 * absw)
+
+
+def test_filter7_mirror_exact_on_small_integers():
+    g = np.random.default_rng(5)
+    x = g.integers(-50, 50, (30, 33)).astype(np.float32)
+    w = g.integers(-9, 10, (7, 7)).astype(np.float32)
+    assert np.array_equal(O.filter7_f32(x, w, 3, 27), O.filter7_f64(x, w, 3, 27))
+
+
+def test_region_interpreter_time_blocked_loop_reduces_per_sweep():
+    dev = O.Device()
+    u0 = I.jacobi_grid(12, seed=1)
+    a, b = dev.map(u0.copy(), O.MAP_TOFROM), dev.map(u0.copy(), O.MAP_TOFROM)
+    res = dev.map(np.full(6, -np.inf, np.float32), O.MAP_TOFROM)
+    lp = O.Loop(O.BODY_JACOBI5_TB, 2, 9, bufs=[a, b], scalars=[12, 12, 4],
+                reductions=[O.Reduction(O.RED_MAX, O.DT_F32, res, 1, O.TERM_RESID)])
+    O.run_region(dev, 1, 1, [lp])
+    want, terms = O.jacobi_tb(u0, 2, 9, 4)
+    assert np.array_equal(dev.array(b)[2:9, 1:-1], want[2:9, 1:-1].astype(np.float32))
+    assert np.array_equal(dev.array(b)[:2], u0[:2]) and np.array_equal(dev.array(a), u0)
+    r = dev.array(res)
+    assert r[0] == -np.inf and r[5] == -np.inf
+    assert np.array_equal(r[1:5], np.array([t.max() for t in terms], np.float32))
