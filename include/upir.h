@@ -167,13 +167,32 @@ typedef enum { UPIR_F32 = 0, UPIR_I64 = 1 } upir_dtype;
  *            transpose (0/1).  hi = bf16(src), lo = bf16(src - hi) (round to
  *            nearest even); with transpose the outputs are [cols*rows].
  *
+ *  JACOBI5_TB bufs u_in[rows*cols], u_out[rows*cols]; scalars rows, cols,
+ *            sweeps (1..8).  collapse(2) like JACOBI5; the loop carries `sweeps`
+ *            successive JACOBI5 sweeps of u_in in which only rows [lb, ub) of
+ *            the interior columns change and every other point keeps its u_in
+ *            value; u_out receives the last sweep's values on those points (no
+ *            other point is written).  Each sweep's arithmetic is JACOBI5's, so
+ *            when the buffers agree on the fixed points the result equals
+ *            `sweeps` JACOBI5 loops.  A TERM_RESID max/min reduction reduces
+ *            sweep k into element index + k (k < sweeps) of its variable.
+ *            Needs cols % 4 == 0 and 16-byte aligned buffers (EUNSUPPORTED).
+ *  FILTER7   bufs x_in[rows*cols], x_out[rows*cols]; scalars rows, cols, then
+ *            the 49 weights w[i][j] of the 7 x 7 window, row-major (the size-7
+ *            filter of the §6 stencil evaluation).  collapse(2) over rows
+ *            [lb, ub) (3 <= lb, ub <= rows-3, step 1) and columns [3, cols-3):
+ *            x_out[r][c] = sum over i, j of w[i][j] x_in[r+i-3][c+j-3], an FP32
+ *            fused multiply-add chain from 0 in row-major (i, then j) order.
+ *            No reductions; cols % 4 == 0 and 16-byte aligned buffers.
+ *
  *  GEMM bodies: the loop runs over rows [lb, ub) of C with collapse 2 (all N
  *  columns); tensor-core bodies need K % 8 == 0 (EUNSUPPORTED otherwise).
  */
 typedef enum {
     UPIR_BODY_AXPY = 0, UPIR_BODY_IMOD = 1, UPIR_BODY_JACOBI5 = 2, UPIR_BODY_MATVEC = 3,
     UPIR_BODY_GEMM_F32 = 4, UPIR_BODY_GEMM_BF16 = 5, UPIR_BODY_GEMM_BF16X3 = 6,
-    UPIR_BODY_COVERAGE = 7, UPIR_BODY_SPLIT_BF16 = 8
+    UPIR_BODY_COVERAGE = 7, UPIR_BODY_SPLIT_BF16 = 8, UPIR_BODY_JACOBI5_TB = 9,
+    UPIR_BODY_FILTER7 = 10
 } upir_body;
 
 /* Value each iteration contributes to a reduction.

@@ -25,7 +25,8 @@ UPIR_SCHED_STATIC, UPIR_SCHED_DYNAMIC = 0, 1
 UPIR_RED_NONE, UPIR_RED_ADD, UPIR_RED_MUL, UPIR_RED_MAX, UPIR_RED_MIN = 0, 1, 2, 3, 4
 UPIR_F32, UPIR_I64 = 0, 1
 (UPIR_BODY_AXPY, UPIR_BODY_IMOD, UPIR_BODY_JACOBI5, UPIR_BODY_MATVEC, UPIR_BODY_GEMM_F32,
- UPIR_BODY_GEMM_BF16, UPIR_BODY_GEMM_BF16X3, UPIR_BODY_COVERAGE, UPIR_BODY_SPLIT_BF16) = range(9)
+ UPIR_BODY_GEMM_BF16, UPIR_BODY_GEMM_BF16X3, UPIR_BODY_COVERAGE, UPIR_BODY_SPLIT_BF16,
+ UPIR_BODY_JACOBI5_TB, UPIR_BODY_FILTER7) = range(11)
 UPIR_TERM_Y, UPIR_TERM_XY, UPIR_TERM_IMOD, UPIR_TERM_IV, UPIR_TERM_RESID = range(5)
 UPIR_HINT_VARIANT, UPIR_HINT_TILE_M, UPIR_HINT_TILE_N, UPIR_HINT_VEC, UPIR_HINT_STAGES = 1, 2, 3, 4, 5
 UPIR_SYNC_BARRIER, UPIR_SYNC_TASKWAIT = 0, 1

@@ -289,6 +289,16 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
+// The first 1024-byte aligned address at or after `raw` (dynamic shared
+// memory), formed by pointer arithmetic on the shared array rather than an
+// integer round trip, so that accesses through it stay shared-memory
+// instructions instead of generic ones.
+template <class T>
+__device__ __forceinline__ T* smem_align1k(unsigned char* raw) {
+    const uint32_t a = smem_u32(raw);
+    return reinterpret_cast<T*>(raw + ((1024u - (a & 1023u)) & 1023u));
+}
+
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
 }

@@ -13,46 +13,11 @@
 #include <cstring>
 
 #include "device_common.cuh"
+#include "tile_iter.cuh"
 
 namespace upir {
 
 namespace {
-
-// The sequence of tiles one team owns under the loop's schedule, produced on
-// demand by the single thread that issues the copies.
-struct TileIter {
-    int64_t next, end;  // current contiguous run [next, end)
-    int64_t chunk_j;    // static chunked: next chunk index
-    bool done;
-};
-
-__device__ __forceinline__ int64_t tile_iter_next(TileIter& it, const JacobiParams& p) {
-    for (;;) {
-        if (it.done) return -1;
-        if (it.next < it.end) return it.next++;
-        if (p.sched == UPIR_SCHED_DYNAMIC) {
-            const int64_t c = p.chunk > 0 ? p.chunk : 1;
-            const int64_t j = (int64_t)atomicAdd(p.sc.chunk_counter, 1ull);
-            if (j * c >= p.ntiles) {
-                it.done = true;
-                return -1;
-            }
-            it.next = j * c;
-            it.end = min(j * c + c, p.ntiles);
-        } else if (p.chunk > 0) {
-            if (it.chunk_j >= p.sk.nchunks) {
-                it.done = true;
-                return -1;
-            }
-            it.next = it.chunk_j * p.chunk;
-            it.end = min(it.next + p.chunk, p.ntiles);
-            it.chunk_j += gridDim.x;
-        } else {
-            it.done = true;  // the blocked run was set up front
-            return -1;
-        }
-    }
-}
 
 template <int S, int ROP>
 __global__ void __launch_bounds__(1024) jacobi_tma_kernel(const JacobiParams p,
@@ -64,7 +29,7 @@ __global__ void __launch_bounds__(1024) jacobi_tma_kernel(const JacobiParams p,
     const int TM = p.tile_m, TN = p.tile_n, SW = TN + 8;
     const int stage_floats = ((TM + 2) * SW + 255) / 256 * 256;  // 1 KB multiples
     // stage 0 starts on a 1024-byte boundary (the launch adds 1 KB of slack)
-    float* ring = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    float* ring = smem_align1k<float>(smem_raw);
     const int tpr = TN / 4;                    // threads per tile row (4 columns each)
     const int tx = threadIdx.x % tpr, ty = threadIdx.x / tpr;
     const int nty = blockDim.x / tpr;          // thread rows
@@ -73,12 +38,7 @@ __global__ void __launch_bounds__(1024) jacobi_tma_kernel(const JacobiParams p,
     const int cols = (int)p.cols, r_ub = (int)p.r_ub;
     float racc = ROP == UPIR_RED_MIN ? __int_as_float(0x7f800000) : -__int_as_float(0x7f800000);
 
-    TileIter it{0, 0, (int64_t)blockIdx.x, false};
-    if (p.sched == UPIR_SCHED_STATIC && p.chunk == 0) {
-        const int64_t w = blockIdx.x;
-        it.next = w * p.sk.base + min(w, p.sk.extra);
-        it.end = it.next + p.sk.base + (w < p.sk.extra ? 1 : 0);
-    }
+    TileIter it = tile_iter_begin(p);
     // producer side (one thread): next tile -> (row, column), then its copy
     auto issue_next = [&](int s) {
         const int64_t t = tile_iter_next(it, p);
@@ -170,18 +130,7 @@ __global__ void __launch_bounds__(1024) jacobi_tma_kernel(const JacobiParams p,
         const float b = block_fold(racc, ROP);
         if (threadIdx.x == 0) atomic_fold_minmax(p.rvar, b, ROP);
     }
-    if (p.sched == UPIR_SCHED_DYNAMIC) {
-        // the last team returns the tile counter to zero for the next launch
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            __threadfence();
-            last_team = atomicAdd(p.sc.ticket, 1u) == gridDim.x - 1;
-            if (last_team) {
-                *p.sc.ticket = 0;
-                *p.sc.chunk_counter = 0;
-            }
-        }
-    }
+    tile_iter_reset(p, &last_team);
     if (failed && threadIdx.x == 0) {
         // copies still in flight get a bounded chance to land before the
         // shared memory is released

@@ -122,7 +122,7 @@ upir_status plan_loop(upir_region r, const upir_loop_desc* d, LoopRec& lp) {
     ok(d->step != 0, UPIR_EINVAL, "step must be non-zero");
     ok(d->chunk >= 0, UPIR_EINVAL, "chunk must be >= 0");
     ok(d->sched == UPIR_SCHED_STATIC || d->sched == UPIR_SCHED_DYNAMIC, UPIR_EINVAL, "unknown schedule");
-    ok(d->body >= UPIR_BODY_AXPY && d->body <= UPIR_BODY_SPLIT_BF16, UPIR_EINVAL, "unknown body");
+    ok(d->body >= UPIR_BODY_AXPY && d->body <= UPIR_BODY_FILTER7, UPIR_EINVAL, "unknown body");
     ok(d->nbufs >= 0 && (d->nbufs == 0 || d->bufs), UPIR_EINVAL, "bad buffer list");
     ok(d->nscalars >= 0 && (d->nscalars == 0 || d->scalars), UPIR_EINVAL, "bad scalar list");
     ok(d->nreductions >= 0 && d->nreductions <= 2 && (d->nreductions == 0 || d->reductions),
@@ -353,6 +353,180 @@ upir_status plan_loop(upir_region r, const upir_loop_desc* d, LoopRec& lp) {
             lp.trip = ep.trip;
             break;
         }
+        case UPIR_BODY_JACOBI5_TB: {
+            ok(lp.bufs.size() == 2, UPIR_EINVAL, "JACOBI5_TB takes bufs u_in, u_out");
+            ok(lp.scalars.size() >= 3, UPIR_EINVAL, "JACOBI5_TB takes scalars rows, cols, sweeps");
+            ok(lp.collapse == 2, UPIR_EINVAL, "JACOBI5_TB is a collapse(2) loop");
+            if (ok.st) return ok.st;
+            const double rows = lp.scalars[0], cols = lp.scalars[1], sw = lp.scalars[2];
+            ok(is_int(rows) && is_int(cols) && rows >= 3 && cols >= 3 && rows < 2e9 && cols < 2e9,
+               UPIR_EINVAL, "JACOBI5_TB grid must be at least 3 x 3");
+            ok(is_int(sw) && sw >= 1 && sw <= 8, UPIR_EINVAL, "JACOBI5_TB sweeps must be an integer in [1, 8]");
+            if (ok.st) return ok.st;
+            const int64_t R = (int64_t)rows, C = (int64_t)cols;
+            const int T = (int)sw;
+            ok(lp.bufs[0] != lp.bufs[1], UPIR_EINVAL, "JACOBI5_TB needs distinct u_in and u_out");
+            ok(buf_floats(0) >= R * C && buf_floats(1) >= R * C, UPIR_EINVAL,
+               "JACOBI5_TB buffers smaller than the grid");
+            ok(lp.step == 1 && (lp.trip == 0 || (lp.lb >= 1 && lp.ub <= R - 1)), UPIR_EINVAL,
+               "JACOBI5_TB rows must be a unit-step range inside [1, rows-1)");
+            ok(!has_i, UPIR_EINVAL, "JACOBI5_TB has no int64 terms");
+            if (has_f) {
+                ok(rv.fterm == UPIR_TERM_RESID, UPIR_EINVAL, "JACOBI5_TB reductions take TERM_RESID");
+                ok(rv.fop == UPIR_RED_MAX || rv.fop == UPIR_RED_MIN, UPIR_EUNSUPPORTED,
+                   "JACOBI5_TB reduces with max or min");
+                const upir_reduction& red = lp.reds[0];
+                ok((size_t)(red.index + T) * 4 <= red.var->bytes, UPIR_EINVAL,
+                   "JACOBI5_TB needs `sweeps` reduction elements from the index on");
+            }
+            if (ok.st) return ok.st;
+            const float* uin = static_cast<const float*>(lp.bufs[0]->dev);
+            float* uout = static_cast<float*>(lp.bufs[1]->dev);
+            ok(C % 4 == 0 && (reinterpret_cast<uintptr_t>(uin) & 15) == 0 &&
+                   (reinterpret_cast<uintptr_t>(uout) & 15) == 0,
+               UPIR_EUNSUPPORTED, "JACOBI5_TB needs cols % 4 == 0 and 16-byte aligned buffers");
+            ok(U0 == 0 || (U0 % 32 == 0 && U0 <= kJacobiTBUnits), UPIR_EUNSUPPORTED,
+               "JACOBI5_TB runs with num_units a multiple of 32 up to 1024 (or 0)");
+            if (ok.st) return ok.st;
+            lp.kind = LK_JACOBI_TB;
+            lp.units = U0 ? U0 : kJacobiTBUnits;
+            JacobiTBParams& tp = lp.tb;
+            memset(&tp, 0, sizeof(tp));
+            // halo: T rows; T columns rounded up to whole 16-byte groups (the
+            // copy's first column must be 16-byte aligned)
+            const int hc = (T + 3) / 4 * 4;
+            // a box row is 32 groups of 4 columns, one per lane of a warp
+            ok(lp.tile_n == 0 || lp.tile_n == 128 - 2 * hc, UPIR_EINVAL,
+               "JACOBI5_TB tiles are 128 - 2 x column halo (4 or 8) columns wide");
+            lp.tile_n = 128 - 2 * hc;
+            // three planes (two copies in flight, one for the ping-pong)
+            const int64_t plane_rows = (int64_t)(kStencilSmemBudget - 1024) / 3 / 4 / (lp.tile_n + 2 * hc);
+            const int tm_max = (int)std::min<int64_t>(128, plane_rows - 2 * T) / 8 * 8;
+            lp.tile_m = lp.tile_m ? lp.tile_m : tm_max;
+            ok(lp.tile_m >= 1 && jacobi_tb_smem_bytes(lp.tile_m, lp.tile_n, T, hc) <= kStencilSmemBudget &&
+                   lp.tile_m + 2 * T <= 256 && lp.tile_n + 2 * hc <= 256,
+               UPIR_EINVAL, "JACOBI5_TB tile too large for shared memory");
+            if (ok.st) return ok.st;
+            lp.smem = jacobi_tb_smem_bytes(lp.tile_m, lp.tile_n, T, hc);
+            tp.uin = uin;
+            tp.uout = uout;
+            tp.rows = R;
+            tp.cols = C;
+            tp.r_lb = lp.lb;
+            tp.r_ub = lp.lb + lp.trip;
+            tp.tile_m = lp.tile_m;
+            tp.tile_n = lp.tile_n;
+            tp.sweeps = T;
+            tp.halo_c = hc;
+            tp.tiles_r = ceil_div(lp.trip, lp.tile_m);
+            tp.tiles_c = ceil_div(C, lp.tile_n);
+            tp.ntiles = tp.tiles_r * tp.tiles_c;
+            tp.chunk = lp.chunk;
+            tp.sched = lp.sched;
+            tp.rvar = rv.fvar;
+            tp.rop = rv.fop == UPIR_RED_MIN ? UPIR_RED_MIN : UPIR_RED_MAX;
+            tp.spin_limit = ctx->spin_limit;
+            tp.err_word = ctx->err_word;
+            tp.wait_prior = wait_prior;
+            if (lp.trip) {
+                upir_status st = encode_tmap_2d(ctx, &lp.tmap[0], uin, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4,
+                                                (uint64_t)C, (uint64_t)R, (uint32_t)(lp.tile_n + 2 * hc),
+                                                (uint32_t)(lp.tile_m + 2 * T), 0);
+                if (st != UPIR_OK) return st;
+            }
+            // one persistent team per SM, tiles balanced to within one
+            const int64_t c = lp.chunk > 0 ? lp.chunk : 1;
+            if (T0) lp.teams = T0;
+            else if (lp.sched == UPIR_SCHED_STATIC && lp.chunk == 0) {
+                const int64_t per = std::max<int64_t>(1, ceil_div(tp.ntiles, kNumSMs));
+                lp.teams = (int)std::max<int64_t>(1, ceil_div(tp.ntiles, per));
+            } else {
+                lp.teams = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(tp.ntiles, c), kNumSMs));
+            }
+            tp.sk = make_sched_const(tp.ntiles, lp.chunk, lp.teams);
+            if (lp.sched == UPIR_SCHED_DYNAMIC) {
+                upir_status st = alloc_scratch(ctx, lp, 0, 0, &tp.sc);
+                if (st != UPIR_OK) return st;
+            }
+            lp.skip = lp.trip == 0;
+            return UPIR_OK;
+        }
+        case UPIR_BODY_FILTER7: {
+            ok(lp.bufs.size() == 2, UPIR_EINVAL, "FILTER7 takes bufs x_in, x_out");
+            ok(lp.scalars.size() >= 51, UPIR_EINVAL, "FILTER7 takes scalars rows, cols and 49 weights");
+            ok(lp.collapse == 2, UPIR_EINVAL, "FILTER7 is a collapse(2) loop");
+            ok(!has_red, UPIR_EINVAL, "FILTER7 takes no reduction clause");
+            if (ok.st) return ok.st;
+            const double rows = lp.scalars[0], cols = lp.scalars[1];
+            ok(is_int(rows) && is_int(cols) && rows >= 7 && cols >= 7 && rows < 2e9 && cols < 2e9,
+               UPIR_EINVAL, "FILTER7 grid must be at least 7 x 7");
+            if (ok.st) return ok.st;
+            const int64_t R = (int64_t)rows, C = (int64_t)cols;
+            ok(lp.bufs[0] != lp.bufs[1], UPIR_EINVAL, "FILTER7 needs distinct x_in and x_out");
+            ok(buf_floats(0) >= R * C && buf_floats(1) >= R * C, UPIR_EINVAL, "FILTER7 buffers smaller than the grid");
+            ok(lp.step == 1 && (lp.trip == 0 || (lp.lb >= 3 && lp.ub <= R - 3)), UPIR_EINVAL,
+               "FILTER7 rows must be a unit-step range inside [3, rows-3)");
+            const float* xin = static_cast<const float*>(lp.bufs[0]->dev);
+            float* xout = static_cast<float*>(lp.bufs[1]->dev);
+            ok(C % 4 == 0 && (reinterpret_cast<uintptr_t>(xin) & 15) == 0 &&
+                   (reinterpret_cast<uintptr_t>(xout) & 15) == 0,
+               UPIR_EUNSUPPORTED, "FILTER7 needs cols % 4 == 0 and 16-byte aligned buffers");
+            ok(U0 == 0 || U0 == kFilter7Units, UPIR_EUNSUPPORTED, "FILTER7 runs with num_units 256 (or 0)");
+            if (ok.st) return ok.st;
+            lp.kind = LK_FILTER7;
+            lp.units = kFilter7Units;
+            Filter7Params& fp = lp.fp;
+            memset(&fp, 0, sizeof(fp));
+            lp.tile_m = lp.tile_m ? lp.tile_m : 32;
+            lp.tile_n = lp.tile_n ? lp.tile_n : 128;
+            ok(lp.tile_n / 4 <= kFilter7Units && kFilter7Units % (lp.tile_n / 4) == 0, UPIR_EINVAL,
+               "FILTER7 tile_n / 4 must divide 256");
+            ok(lp.tile_m % 4 == 0, UPIR_EINVAL, "FILTER7 tile_m must be a multiple of 4");
+            ok(lp.tile_m + 6 <= 256 && lp.tile_n + 8 <= 256 && filter7_smem_bytes(lp.tile_m, lp.tile_n) <= kStencilSmemBudget,
+               UPIR_EINVAL, "FILTER7 tile too large");
+            if (ok.st) return ok.st;
+            lp.smem = filter7_smem_bytes(lp.tile_m, lp.tile_n);
+            fp.xin = xin;
+            fp.xout = xout;
+            fp.rows = R;
+            fp.cols = C;
+            fp.r_lb = lp.lb;
+            fp.r_ub = lp.lb + lp.trip;
+            fp.tile_m = lp.tile_m;
+            fp.tile_n = lp.tile_n;
+            fp.tiles_r = ceil_div(lp.trip, lp.tile_m);
+            fp.tiles_c = ceil_div(C, lp.tile_n);
+            fp.ntiles = fp.tiles_r * fp.tiles_c;
+            fp.chunk = lp.chunk;
+            fp.sched = lp.sched;
+            fp.spin_limit = ctx->spin_limit;
+            fp.err_word = ctx->err_word;
+            fp.wait_prior = wait_prior;
+            for (int k = 0; k < 49; ++k) fp.w[k] = (float)lp.scalars[2 + k];
+            if (lp.trip) {
+                upir_status st = encode_tmap_2d(ctx, &lp.tmap[0], xin, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4,
+                                                (uint64_t)C, (uint64_t)R, (uint32_t)(lp.tile_n + 8),
+                                                (uint32_t)(lp.tile_m + 6), 0);
+                if (st != UPIR_OK) return st;
+            }
+            const int per_sm = std::max(1, filter7_max_teams_per_sm(lp.tile_m, lp.tile_n));
+            const int64_t slots = (int64_t)kNumSMs * per_sm;
+            const int64_t c = lp.chunk > 0 ? lp.chunk : 1;
+            if (T0) lp.teams = T0;
+            else if (lp.sched == UPIR_SCHED_STATIC && lp.chunk == 0) {
+                const int64_t per = std::max<int64_t>(1, ceil_div(fp.ntiles, slots));
+                lp.teams = (int)std::max<int64_t>(1, ceil_div(fp.ntiles, per));
+            } else {
+                lp.teams = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(fp.ntiles, c), slots));
+            }
+            fp.sk = make_sched_const(fp.ntiles, lp.chunk, lp.teams);
+            if (lp.sched == UPIR_SCHED_DYNAMIC) {
+                upir_status st = alloc_scratch(ctx, lp, 0, 0, &fp.sc);
+                if (st != UPIR_OK) return st;
+            }
+            lp.skip = lp.trip == 0;
+            return UPIR_OK;
+        }
         case UPIR_BODY_MATVEC: {
             ok(lp.bufs.size() == 3, UPIR_EINVAL, "MATVEC takes bufs A, x, y");
             ok(lp.scalars.size() >= 2, UPIR_EINVAL, "MATVEC takes scalars rows, cols");
@@ -539,6 +713,8 @@ cudaError_t launch_loop(upir_ctx ctx, LoopRec& lp, cudaStream_t s) {
         case LK_GEMM_F32: return launch_gemm_f32(lp.teams, lp.units, lp.gp, s);
         case LK_SPLIT: return launch_split_bf16(lp.teams, lp.units, lp.sp, s);
         case LK_GEMM_TC: return launch_gemm_tc_loop(ctx, lp, s);
+        case LK_JACOBI_TB: return launch_jacobi_tb(lp.teams, lp.units, lp.tb, &lp.tmap[0], s);
+        case LK_FILTER7: return launch_filter7(lp.teams, lp.fp, &lp.tmap[0], s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -23,7 +23,8 @@ struct upir_buf_s {
 namespace upir {
 
 enum LaunchKind {
-    LK_ELEM = 0, LK_JACOBI_TMA = 1, LK_MATVEC = 2, LK_GEMM_F32 = 3, LK_SPLIT = 4, LK_GEMM_TC = 5
+    LK_ELEM = 0, LK_JACOBI_TMA = 1, LK_MATVEC = 2, LK_GEMM_F32 = 3, LK_SPLIT = 4, LK_GEMM_TC = 5,
+    LK_JACOBI_TB = 6, LK_FILTER7 = 7
 };
 
 // A recorded, validated and planned loop.
@@ -48,10 +49,12 @@ struct LoopRec {
     size_t smem = 0;
     ElemParams ep{};
     JacobiParams jp{};
+    JacobiTBParams tb{};
+    Filter7Params fp{};
     MatvecParams mp{};
     GemmParams gp{};
     SplitParams sp{};
-    alignas(64) CUtensorMap tmap[6];
+    CUtensorMap tmap[6];  // the type carries the alignment TMA needs
     alignas(16) unsigned char tc_params[256];  // tensor-core GEMM parameters
 };
 

@@ -91,6 +91,44 @@ struct JacobiParams {
     Scratch sc;
 };
 
+// Time-blocked Jacobi (JACOBI5_TB): `sweeps` sweeps per tile visit, tiles of
+// tile_m x tile_n points with a halo of `sweeps` rows and halo_c columns.
+struct JacobiTBParams {
+    const float* uin;
+    float* uout;
+    int64_t rows, cols;
+    int64_t r_lb, r_ub;
+    int tile_m, tile_n, sweeps, halo_c;
+    int64_t tiles_r, tiles_c, ntiles;
+    int64_t chunk;
+    int sched;
+    float* rvar;  // first of `sweeps` reduction variables, or nullptr
+    int rop;
+    long long spin_limit;
+    int* err_word;
+    SchedConst sk;
+    int wait_prior;
+    Scratch sc;
+};
+
+// The 7 x 7 filter (FILTER7): tiles of tile_m x tile_n outputs.
+struct Filter7Params {
+    const float* xin;
+    float* xout;
+    int64_t rows, cols;
+    int64_t r_lb, r_ub;
+    int tile_m, tile_n;
+    int64_t tiles_r, tiles_c, ntiles;
+    int64_t chunk;
+    int sched;
+    long long spin_limit;
+    int* err_word;
+    SchedConst sk;
+    int wait_prior;
+    Scratch sc;
+    float w[49];  // weights, row-major over the window
+};
+
 struct MatvecParams {
     const float* A;
     const float* x;
@@ -175,6 +213,14 @@ int64_t finalize_groups(int64_t nslots);
 cudaError_t launch_jacobi_tma(int teams, int units, const JacobiParams& p, const void* tmap,
                               cudaStream_t s);
 size_t jacobi_tma_smem_bytes(int tile_m, int tile_n, int stages);
+constexpr int kJacobiTBUnits = 1024, kFilter7Units = 256, kFilter7Stages = 3;
+constexpr size_t kStencilSmemBudget = 222 * 1024;  // dynamic shared memory of the stencil kernels
+size_t jacobi_tb_plane_floats(int tile_m, int tile_n, int sweeps, int halo_c);
+size_t jacobi_tb_smem_bytes(int tile_m, int tile_n, int sweeps, int halo_c);
+cudaError_t launch_jacobi_tb(int teams, int units, const JacobiTBParams& p, const void* tmap, cudaStream_t s);
+size_t filter7_smem_bytes(int tile_m, int tile_n);
+int filter7_max_teams_per_sm(int tile_m, int tile_n);
+cudaError_t launch_filter7(int teams, const Filter7Params& p, const void* tmap, cudaStream_t s);
 int jacobi_tma_max_teams_per_sm(int units, int tile_m, int tile_n, int stages);
 cudaError_t launch_matvec(int teams, int units, const MatvecParams& p, cudaStream_t s);
 cudaError_t launch_gemm_f32(int teams, int units, const GemmParams& p, cudaStream_t s);
