@@ -13,7 +13,7 @@
 //    multiply-adds in row-major tap order.  Each thread streams the input rows
 //    of its 4-column, 4-row output block through registers, so every input
 //    row is read from shared memory once per block and the weights stay in
-//    the kernel parameters.
+//    the kernel parameters.  Two ring stages keep four teams per SM.
 //
 // Both kernels are persistent teams over the tile loop with TMA copies of the
 // halo boxes into a shared-memory ring; every mbarrier wait is bounded.

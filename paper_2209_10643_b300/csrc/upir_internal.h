@@ -213,7 +213,7 @@ int64_t finalize_groups(int64_t nslots);
 cudaError_t launch_jacobi_tma(int teams, int units, const JacobiParams& p, const void* tmap,
                               cudaStream_t s);
 size_t jacobi_tma_smem_bytes(int tile_m, int tile_n, int stages);
-constexpr int kJacobiTBUnits = 1024, kFilter7Units = 256, kFilter7Stages = 3;
+constexpr int kJacobiTBUnits = 1024, kFilter7Units = 256, kFilter7Stages = 2;
 constexpr size_t kStencilSmemBudget = 222 * 1024;  // dynamic shared memory of the stencil kernels
 size_t jacobi_tb_plane_floats(int tile_m, int tile_n, int sweeps, int halo_c);
 size_t jacobi_tb_smem_bytes(int tile_m, int tile_n, int sweeps, int halo_c);
