@@ -121,7 +121,7 @@ def induction_value(lb: int, step: int, k: int) -> int:
 #     fixed.
 # ----------------------------------------------------------------------------
 
-SCHED_STATIC, SCHED_DYNAMIC = 0, 1
+SCHED_STATIC, SCHED_DYNAMIC, SCHED_GUIDED, SCHED_RUNTIME, SCHED_AUTO, SCHED_TASKLOOP = range(6)
 
 
 def static_owner_map(trip: int, workers: int, chunk: int) -> np.ndarray:
@@ -154,19 +154,77 @@ def dynamic_chunks(trip: int, chunk: int) -> list[tuple[int, int]]:
     return [(s, min(s + c, trip)) for s in range(0, trip, c)]
 
 
-def check_dynamic_assignment(trip: int, chunk: int, owner: np.ndarray,
+def guided_chunks(trip: int, workers: int, chunk: int) -> list[tuple[int, int]]:
+    """Chunk boundaries of ``schedule(guided, c)`` (§3.2 lists guided among
+    the schedule policies without defining it).  Reading, after OpenMP: each
+    chunk handed out holds max(c, ceil(R / W)) iterations, R being the
+    iterations not yet handed out and W the workers (c = 0 means 1; the last
+    chunk may be shorter); chunks go out in increasing iteration order to
+    whichever worker asks next."""
+    if workers <= 0:
+        raise ValueError("need at least one worker")
+    c = chunk if chunk > 0 else 1
+    out, s = [], 0
+    while s < trip:
+        e = min(s + max(c, -(-(trip - s) // workers)), trip)
+        out.append((s, e))
+        s = e
+    return out
+
+
+def taskloop_chunks(trip: int, grainsize: int = 0, num_tasks: int = 0) -> list[tuple[int, int]]:
+    """Tasks of ``loop_parallel taskloop(grainsize, num_tasks)`` (§3.2: the two
+    fields control the granularity or the number of tasks).  Reading, after
+    OpenMP: num_tasks(n) makes min(n, trip) tasks; grainsize(g) makes
+    max(1, floor(trip / g)) tasks, so each holds between g and 2g - 1
+    iterations (or all of them when trip < g); with both fields the smaller
+    count wins.  The iterations are split into that many contiguous tasks, the
+    first (trip mod n) one iteration longer; tasks run in any order on any
+    worker, each exactly once."""
+    if trip == 0:
+        return []
+    counts = []
+    if num_tasks > 0:
+        counts.append(min(num_tasks, trip))
+    if grainsize > 0:
+        counts.append(max(1, trip // grainsize))
+    if not counts:
+        raise ValueError("taskloop needs grainsize or num_tasks")
+    n = min(counts)
+    base, extra = divmod(trip, n)
+    out, s = [], 0
+    for t in range(n):
+        e = s + base + (1 if t < extra else 0)
+        out.append((s, e))
+        s = e
+    return out
+
+
+def check_chunked_assignment(trip: int, chunks: list[tuple[int, int]], owner: np.ndarray,
                              count: np.ndarray, workers: int) -> bool:
-    """True when (owner, count) is a valid dynamic-schedule execution:
+    """True when (owner, count) is a valid execution of a schedule that hands
+    out the given chunks to whichever worker asks: the chunks tile [0, trip),
     every iteration ran exactly once and each chunk ran on a single worker."""
     if owner.shape != (trip,) or count.shape != (trip,):
         return False
     if trip and (count.min() != 1 or count.max() != 1):
         return False
-    for s, e in dynamic_chunks(trip, chunk):
+    s0 = 0
+    for s, e in chunks:
+        if s != s0 or e <= s:
+            return False
+        s0 = e
         w = owner[s]
         if w < 0 or w >= workers or np.any(owner[s:e] != w):
             return False
-    return True
+    return s0 == trip
+
+
+def check_dynamic_assignment(trip: int, chunk: int, owner: np.ndarray,
+                             count: np.ndarray, workers: int) -> bool:
+    """True when (owner, count) is a valid dynamic-schedule execution:
+    every iteration ran exactly once and each chunk ran on a single worker."""
+    return check_chunked_assignment(trip, dynamic_chunks(trip, chunk), owner, count, workers)
 
 
 # ----------------------------------------------------------------------------

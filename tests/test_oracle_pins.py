@@ -564,3 +564,63 @@ def test_region_interpreter_time_blocked_loop_reduces_per_sweep():
     r = dev.array(res)
     assert r[0] == -np.inf and r[5] == -np.inf
     assert np.array_equal(r[1:5], np.array([t.max() for t in terms], np.float32))
+
+
+# --- guided schedule and taskloop -------------------------------------------------
+
+def test_guided_and_taskloop_hand_tables():
+    g = gold("guided_taskloop_tables.json")
+    for c in g["guided"]:
+        ch = O.guided_chunks(c["trip"], c["workers"], c["chunk"])
+        assert [e - s for s, e in ch] == c["sizes"], c
+    for c in g["taskloop"]:
+        ch = O.taskloop_chunks(c["trip"], c["grainsize"], c["num_tasks"])
+        assert [e - s for s, e in ch] == c["sizes"], c
+
+
+def test_guided_invariants_brute_force():
+    for trip in range(0, 80):
+        for workers in range(1, 7):
+            for chunk in range(0, 6):
+                ch = O.guided_chunks(trip, workers, chunk)
+                sizes = [e - s for s, e in ch]
+                assert sum(sizes) == trip and all(z > 0 for z in sizes)
+                assert all(a >= b for a, b in zip(sizes, sizes[1:-1]))  # non-increasing but the last
+                s = 0
+                for a, b in ch:  # each chunk: max(c, ceil(remaining / W)), capped by what remains
+                    assert a == s and b - a == min(trip - a, max(max(chunk, 1), -(-(trip - a) // workers)))
+                    s = b
+
+
+def test_taskloop_invariants_brute_force():
+    for trip in range(0, 60):
+        for gs in range(0, 8):
+            for nt in range(0, 8):
+                if gs == 0 and nt == 0:
+                    continue
+                ch = O.taskloop_chunks(trip, gs, nt)
+                sizes = [e - s for s, e in ch]
+                assert sum(sizes) == trip
+                if trip == 0:
+                    continue
+                assert max(sizes) - min(sizes) <= 1
+                if nt:
+                    assert len(sizes) <= nt
+                if gs and not nt:
+                    assert min(sizes) >= min(gs, trip) and (trip < gs or max(sizes) < 2 * gs)
+
+
+def test_chunked_assignment_checker_catches_violations():
+    ch = O.guided_chunks(20, 3, 0)
+    owner = np.zeros(20, np.int64)
+    count = np.ones(20, np.int64)
+    for k, (s, e) in enumerate(ch):
+        owner[s:e] = k % 3
+    assert O.check_chunked_assignment(20, ch, owner, count, 3)
+    bad = owner.copy()
+    bad[ch[0][0]] = (bad[ch[0][0]] + 1) % 3          # a chunk split over two workers
+    assert not O.check_chunked_assignment(20, ch, bad, count, 3)
+    twice = count.copy()
+    twice[5] = 2                                        # an iteration run twice
+    assert not O.check_chunked_assignment(20, ch, owner, twice, 3)
+    assert not O.check_chunked_assignment(20, ch[:-1], owner, count, 3)   # chunks do not tile the range
