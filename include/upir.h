@@ -134,7 +134,32 @@ upir_status upir_spmd_region(upir_ctx ctx, int32_t num_teams, int32_t num_units,
 
 /* --------------------------------------------------------- worksharing loop -- */
 
-typedef enum { UPIR_SCHED_STATIC = 0, UPIR_SCHED_DYNAMIC = 1 } upir_sched; /* §3.2 subset */
+/* Schedule policies of §3.2 (worksharing schedule static | dynamic | guided |
+ * runtime | auto, and the taskloop parallelization).  W = the loop's workers.
+ *  STATIC    see upir_loop_desc.
+ *  DYNAMIC   chunks of `chunk` iterations (0 means 1), in increasing order, to
+ *            whichever worker asks next.
+ *  GUIDED    like DYNAMIC, but each chunk holds max(chunk, ceil(R / W))
+ *            iterations, R being those not yet handed out (chunk 0 means 1).
+ *  RUNTIME   the context's run schedule (upir_ctx_set_run_schedule; default
+ *            STATIC with chunk 0, or the UPIR_SCHEDULE environment variable
+ *            "static|dynamic|guided[,chunk]" read by upir_init).
+ *  AUTO      the runtime chooses: with a cost model installed
+ *            (upir_ctx_set_cost_model) the candidate schedule and units per
+ *            team it predicts fastest (AXPY, JACOBI5 and MATVEC bodies; the
+ *            others take STATIC), else STATIC with the planner's geometry.
+ *  TASKLOOP  the iterations are cut into tasks (hints GRAINSIZE g: max(1,
+ *            trip / g) tasks; NUM_TASKS n: min(n, trip) tasks; with both the
+ *            smaller count; with neither 8 tasks per SM, 1184), contiguous,
+ *            the first (trip mod tasks) one iteration longer, which the
+ *            workers claim dynamically.  chunk must be 0.
+ * Tiled bodies (tiled JACOBI5, JACOBI5_TB, FILTER7, GEMM_F32) schedule their
+ * tiles: chunks, tasks and W count tiles and teams there.  The tensor-core
+ * GEMM takes STATIC (and RUNTIME / AUTO resolving to it) only. */
+typedef enum {
+    UPIR_SCHED_STATIC = 0, UPIR_SCHED_DYNAMIC = 1, UPIR_SCHED_GUIDED = 2, UPIR_SCHED_RUNTIME = 3,
+    UPIR_SCHED_AUTO = 4, UPIR_SCHED_TASKLOOP = 5
+} upir_sched;
 
 typedef enum {
     UPIR_RED_NONE = 0, UPIR_RED_ADD = 1, UPIR_RED_MUL = 2, UPIR_RED_MAX = 3, UPIR_RED_MIN = 4
@@ -227,7 +252,9 @@ typedef enum {
     UPIR_HINT_TILE_M    = 2, /* tile rows (JACOBI5 tiled variant, GEMM)                       */
     UPIR_HINT_TILE_N    = 3, /* tile cols                                                     */
     UPIR_HINT_VEC       = 4, /* iterations per worker the planner aims for (1, 4, 8 or 16)    */
-    UPIR_HINT_STAGES    = 5  /* shared-memory pipeline depth of the tiled JACOBI5 (1..4)      */
+    UPIR_HINT_STAGES    = 5, /* shared-memory pipeline depth of the tiled JACOBI5 (1..4)      */
+    UPIR_HINT_GRAINSIZE = 6, /* taskloop grainsize (>= 1; schedule TASKLOOP only)             */
+    UPIR_HINT_NUM_TASKS = 7  /* taskloop num_tasks (>= 1; schedule TASKLOOP only)             */
 } upir_hint_key;
 
 /* The canonical loop with its worksharing parallelization (§3.2).
@@ -334,6 +361,13 @@ upir_status upir_ctx_timings(upir_ctx ctx, float* ms, int32_t* body, int32_t cap
 
 /* Launch geometry the planner chose for loop `loop_index` of a region (after
  * upir_loop): teams (grid) and units (block) of its main kernel. */
+/* Schedule the planner settled on for loop `loop_index` (RUNTIME and AUTO
+ * resolved): *sched (STATIC, DYNAMIC, GUIDED or TASKLOOP), *chunk, and
+ * *nchunks, the number of chunks or tasks handed out dynamically (0 for
+ * STATIC).  Any output pointer may be NULL. */
+upir_status upir_region_loop_schedule(upir_region region, int32_t loop_index, int32_t* sched,
+                                      int64_t* chunk, int64_t* nchunks);
+
 upir_status upir_region_loop_geometry(upir_region region, int32_t loop_index,
                                       int32_t* teams, int32_t* units);
 
@@ -347,6 +381,44 @@ upir_status upir_selftest_bounded_wait(upir_ctx ctx, int64_t spin_limit);
 /* Spin budget (polls) of every bounded device-side wait; default 2^26, also
  * settable with the environment variable UPIR_SPIN_LIMIT. */
 upir_status upir_ctx_set_spin_limit(upir_ctx ctx, int64_t spin_limit);
+
+/* The run schedule that loops with UPIR_SCHED_RUNTIME take when they are
+ * recorded: sched STATIC, DYNAMIC or GUIDED with chunk >= 0.  EINVAL
+ * otherwise. */
+upir_status upir_ctx_set_run_schedule(upir_ctx ctx, int32_t sched, int64_t chunk);
+
+/* Install the learned cost model that UPIR_SCHED_AUTO consults when a loop is
+ * recorded: `params` are the UPIR_MLP_NPARAM FP32 parameters of the
+ * 12 -> 64 -> 64 -> 1 MLP (layout of upir_mlp_forward), `feat_mean` and
+ * `feat_std` the 12 feature means and standard deviations the inputs are
+ * standardised with (std <= 0 counts as 1).  All host pointers, copied.  The
+ * features of a candidate are: body one-hot (AXPY, JACOBI5, MATVEC, GEMM),
+ * log2 trip (JACOBI5: interior points), bytes and flops per iteration (AXPY
+ * 12, 4; JACOBI5 8, 6; MATVEC 4 cols, 2 cols), schedule one-hot (static,
+ * dynamic), log2(chunk + 1), log2 units, log2 teams (0: planner-sized).  The
+ * prediction uses bfloat16-rounded weights and FP32 arithmetic on the host.
+ * params NULL removes the model. */
+upir_status upir_ctx_set_cost_model(upir_ctx ctx, const float* params, const float* feat_mean,
+                                    const float* feat_std);
+
+/* Host-only helpers of the auto schedule (no GPU needed).
+ * upir_auto_candidates: the candidate (sched, chunk, units) triples the cost
+ *   model ranks for a body (AXPY, JACOBI5, MATVEC; none for the others);
+ *   *count gets their number, at most `cap` are written (arrays may be NULL).
+ * upir_auto_features: the 12 features of one candidate; trip is the loop's
+ *   trip count (rows for JACOBI5 and MATVEC), cols the grid / matrix width.
+ * upir_auto_pick: the candidate the model (params, feat_mean, feat_std as for
+ *   upir_ctx_set_cost_model; params NULL: none) predicts fastest, restricted
+ *   to `units` when non-zero; *units_out is its units (0 when fixed or when no
+ *   candidate applies, the schedule then being STATIC with chunk 0).
+ * EINVAL for bad pointers or sizes. */
+upir_status upir_auto_candidates(int32_t body, int32_t* sched, int64_t* chunk, int32_t* units, int32_t cap,
+                                 int32_t* count);
+upir_status upir_auto_features(int32_t body, int64_t trip, int64_t cols, int32_t sched, int64_t chunk,
+                               int32_t units, int32_t teams, float* out);
+upir_status upir_auto_pick(const float* params, const float* feat_mean, const float* feat_std, int32_t body,
+                           int64_t trip, int64_t cols, int32_t units, int32_t teams, int32_t* sched,
+                           int64_t* chunk, int32_t* units_out);
 
 /* ------------------------------------------- allocation-free AXPY variant -- */
 /* The paper has no counterpart to this call; it serves callers that cannot

@@ -21,14 +21,16 @@ lib = C.CDLL(LIB_PATH)
 UPIR_OK, UPIR_EINVAL, UPIR_ENOTMAPPED, UPIR_EBUSY, UPIR_ENOMEM, UPIR_ECUDA, \
     UPIR_ETIMEDOUT, UPIR_EUNSUPPORTED = 0, -1, -2, -3, -4, -5, -6, -7
 UPIR_MAP_TO, UPIR_MAP_FROM, UPIR_MAP_TOFROM, UPIR_MAP_ALLOC = 0, 1, 2, 3
-UPIR_SCHED_STATIC, UPIR_SCHED_DYNAMIC = 0, 1
+(UPIR_SCHED_STATIC, UPIR_SCHED_DYNAMIC, UPIR_SCHED_GUIDED, UPIR_SCHED_RUNTIME, UPIR_SCHED_AUTO,
+ UPIR_SCHED_TASKLOOP) = range(6)
 UPIR_RED_NONE, UPIR_RED_ADD, UPIR_RED_MUL, UPIR_RED_MAX, UPIR_RED_MIN = 0, 1, 2, 3, 4
 UPIR_F32, UPIR_I64 = 0, 1
 (UPIR_BODY_AXPY, UPIR_BODY_IMOD, UPIR_BODY_JACOBI5, UPIR_BODY_MATVEC, UPIR_BODY_GEMM_F32,
  UPIR_BODY_GEMM_BF16, UPIR_BODY_GEMM_BF16X3, UPIR_BODY_COVERAGE, UPIR_BODY_SPLIT_BF16,
  UPIR_BODY_JACOBI5_TB, UPIR_BODY_FILTER7) = range(11)
 UPIR_TERM_Y, UPIR_TERM_XY, UPIR_TERM_IMOD, UPIR_TERM_IV, UPIR_TERM_RESID = range(5)
-UPIR_HINT_VARIANT, UPIR_HINT_TILE_M, UPIR_HINT_TILE_N, UPIR_HINT_VEC, UPIR_HINT_STAGES = 1, 2, 3, 4, 5
+(UPIR_HINT_VARIANT, UPIR_HINT_TILE_M, UPIR_HINT_TILE_N, UPIR_HINT_VEC, UPIR_HINT_STAGES, UPIR_HINT_GRAINSIZE,
+ UPIR_HINT_NUM_TASKS) = range(1, 8)
 UPIR_SYNC_BARRIER, UPIR_SYNC_TASKWAIT = 0, 1
 UPIR_SUBMIT_GRAPH = 1
 UPIR_BATCH_LAUNCHES, UPIR_BATCH_GRAPH, UPIR_BATCH_PERSISTENT = 0, 1, 2
@@ -87,6 +89,12 @@ _SIGS = {
     "upir_ctx_set_timing": (_i32, [_vp, _i32]),
     "upir_ctx_timings": (_i32, [_vp, _P(C.c_float), _P(_i32), _i32, _P(_i32)]),
     "upir_region_loop_geometry": (_i32, [_vp, _i32, _P(_i32), _P(_i32)]),
+    "upir_region_loop_schedule": (_i32, [_vp, _i32, _P(_i32), _P(_i64), _P(_i64)]),
+    "upir_ctx_set_run_schedule": (_i32, [_vp, _i32, _i64]),
+    "upir_ctx_set_cost_model": (_i32, [_vp, _vp, _vp, _vp]),
+    "upir_auto_candidates": (_i32, [_i32, _P(_i32), _P(_i64), _P(_i32), _i32, _P(_i32)]),
+    "upir_auto_features": (_i32, [_i32, _i64, _i64, _i32, _i64, _i32, _i32, _P(C.c_float)]),
+    "upir_auto_pick": (_i32, [_vp, _vp, _vp, _i32, _i64, _i64, _i32, _i32, _P(_i32), _P(_i64), _P(_i32)]),
     "upir_selftest_bounded_wait": (_i32, [_vp, _i64]),
     "upir_ctx_set_spin_limit": (_i32, [_vp, _i64]),
     "upir_axpy_reduce_noalloc": (_i32, [_vp, _vp, _i64, C.c_float, _i64, _i64, _vp, _vp, _vp]),
@@ -254,6 +262,64 @@ def upir_region_loop_geometry(region: int, index: int) -> tuple[int, int]:
     if st != UPIR_OK:
         raise UpirError(st, "upir_region_loop_geometry")
     return t.value, u.value
+
+
+def upir_region_loop_schedule(region: int, index: int) -> tuple[int, int, int]:
+    """(sched, chunk, nchunks) the planner settled on for a loop."""
+    sc, ch, n = C.c_int32(), C.c_int64(), C.c_int64()
+    st = lib.upir_region_loop_schedule(region, index, C.byref(sc), C.byref(ch), C.byref(n))
+    if st != UPIR_OK:
+        raise UpirError(st, "upir_region_loop_schedule")
+    return sc.value, ch.value, n.value
+
+
+def upir_ctx_set_run_schedule(ctx: int, sched: int, chunk: int = 0) -> None:
+    _chk(ctx, lib.upir_ctx_set_run_schedule(ctx, sched, chunk), "upir_ctx_set_run_schedule")
+
+
+def _f32(a):
+    import numpy as np
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float32).ravel())
+
+
+def upir_ctx_set_cost_model(ctx: int, params, feat_mean=None, feat_std=None) -> None:
+    """Install (or with params None remove) the cost model of schedule(auto)."""
+    if params is None:
+        _chk(ctx, lib.upir_ctx_set_cost_model(ctx, None, None, None), "upir_ctx_set_cost_model")
+        return
+    p, m, sd = _f32(params), _f32(feat_mean), _f32(feat_std)
+    if p.size != UPIR_MLP_NPARAM or m.size != UPIR_MLP_IN or sd.size != UPIR_MLP_IN:
+        raise ValueError("cost model needs UPIR_MLP_NPARAM parameters and 12 means / deviations")
+    _chk(ctx, lib.upir_ctx_set_cost_model(ctx, p.ctypes.data, m.ctypes.data, sd.ctypes.data),
+         "upir_ctx_set_cost_model")
+
+
+def upir_auto_candidates(body: int) -> list[tuple[int, int, int]]:
+    n = C.c_int32()
+    _chk(None, lib.upir_auto_candidates(body, None, None, None, 0, C.byref(n)), "upir_auto_candidates")
+    sc, ch, un = (C.c_int32 * n.value)(), (C.c_int64 * n.value)(), (C.c_int32 * n.value)()
+    _chk(None, lib.upir_auto_candidates(body, sc, ch, un, n.value, C.byref(n)), "upir_auto_candidates")
+    return [(sc[i], ch[i], un[i]) for i in range(n.value)]
+
+
+def upir_auto_features(body: int, trip: int, cols: int, sched: int, chunk: int, units: int, teams: int):
+    out = (C.c_float * UPIR_MLP_IN)()
+    _chk(None, lib.upir_auto_features(body, trip, cols, sched, chunk, units, teams, out), "upir_auto_features")
+    return list(out)
+
+
+def upir_auto_pick(params, feat_mean, feat_std, body: int, trip: int, cols: int = 0, units: int = 0,
+                   teams: int = 0) -> tuple[int, int, int]:
+    """(sched, chunk, units) the model picks (host computation, no GPU)."""
+    sc, ch, un = C.c_int32(), C.c_int64(), C.c_int32()
+    if params is None:
+        args = (None, None, None)
+    else:
+        p, m, sd = _f32(params), _f32(feat_mean), _f32(feat_std)
+        args = (p.ctypes.data, m.ctypes.data, sd.ctypes.data)
+    _chk(None, lib.upir_auto_pick(*args, body, trip, cols, units, teams, C.byref(sc), C.byref(ch), C.byref(un)),
+         "upir_auto_pick")
+    return sc.value, ch.value, un.value
 
 
 def upir_selftest_bounded_wait(ctx: int, spin_limit: int) -> None:

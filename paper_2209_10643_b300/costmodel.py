@@ -38,28 +38,14 @@ def features(op: int, trip: int, bytes_per_iter: float, flops_per_iter: float, s
     return f
 
 
+_OP_BODY = {OP_AXPY: U.UPIR_BODY_AXPY, OP_JACOBI: U.UPIR_BODY_JACOBI5, OP_MATVEC: U.UPIR_BODY_MATVEC,
+            OP_GEMM: U.UPIR_BODY_GEMM_F32}
+
+
 def candidates(op: int) -> list[dict]:
-    """Candidate schedules per loop kind (teams = 0: the planner sizes the grid)."""
-    out = []
-    if op == OP_AXPY:
-        for units in (128, 256, 512, 1024):
-            for chunk in (0, 4, 64, 1024):
-                out.append(dict(sched=U.UPIR_SCHED_STATIC, chunk=chunk, units=units, teams=0))
-            for chunk in (256, 4096, 65536):
-                out.append(dict(sched=U.UPIR_SCHED_DYNAMIC, chunk=chunk, units=units, teams=0))
-    elif op == OP_JACOBI:
-        for units in (128, 256, 512):
-            for chunk in (0, 1, 4):
-                out.append(dict(sched=U.UPIR_SCHED_STATIC, chunk=chunk, units=units, teams=0))
-            for chunk in (1, 4):
-                out.append(dict(sched=U.UPIR_SCHED_DYNAMIC, chunk=chunk, units=units, teams=0))
-    else:
-        for units in (128, 256, 512, 1024):
-            for chunk in (0, 1, 8):
-                out.append(dict(sched=U.UPIR_SCHED_STATIC, chunk=chunk, units=units, teams=0))
-            for chunk in (1, 8):
-                out.append(dict(sched=U.UPIR_SCHED_DYNAMIC, chunk=chunk, units=units, teams=0))
-    return out
+    """Candidate schedules per loop kind (teams = 0: the planner sizes the
+    grid), the same list the runtime's schedule(auto) ranks."""
+    return [dict(sched=sc, chunk=ch, units=un, teams=0) for sc, ch, un in U.upir_auto_candidates(_OP_BODY[op])]
 
 
 def heuristic(op: int, trip: int) -> dict:
@@ -278,6 +264,14 @@ class GpuMLP:
             if (ep + 1) % log_every == 0 or ep == epochs - 1:
                 losses.append(self.full_loss(x, t))
         return losses
+
+
+def install(ctx: int, model: "GpuMLP", mean: np.ndarray, std: np.ndarray) -> None:
+    """Make a trained model the one the context's schedule(auto) consults."""
+    p = model.params()
+    flat = np.concatenate([p[k].astype(np.float32).ravel() for k in ("W1", "b1", "W2", "b2", "W3", "b3")])
+    U.upir_ctx_set_cost_model(ctx, flat, np.asarray(mean, np.float32),
+                              np.where(np.asarray(std) > 0, std, 1.0).astype(np.float32))
 
 
 def standardize(f: np.ndarray, mean=None, std=None):

@@ -215,6 +215,24 @@ __device__ __forceinline__ float block_fold(float v, int op) {
     return v;  // valid in thread 0
 }
 
+// Dynamically handed-out chunk j of a loop over n logical units: [b, e) of
+// fixed size c (0 means 1), or from the planner's table of chunk starts
+// (guided schedules, taskloops).  False once j is past the last chunk.
+__device__ __forceinline__ bool dyn_chunk(const Scratch& sc, int64_t c, int64_t n, int64_t j, int64_t& b,
+                                          int64_t& e) {
+    if (sc.chunk_starts) {
+        if (j >= sc.nchunks_tab) return false;
+        b = sc.chunk_starts[j];
+        e = sc.chunk_starts[j + 1];
+        return true;
+    }
+    const int64_t cc = c > 0 ? c : 1;
+    if (j >= (n + cc - 1) / cc) return false;
+    b = j * cc;
+    e = min(b + cc, n);
+    return true;
+}
+
 // Warp-aggregated claim of the next dynamic chunk: the active lanes take
 // consecutive tickets with one atomic.
 __device__ __forceinline__ unsigned long long claim_chunk(unsigned long long* counter) {

@@ -156,12 +156,12 @@ __global__ void __launch_bounds__(1024, 1) elem_kernel(const ElemParams p) {
             if (threadIdx.x == 0) p.sc.partials[blockIdx.x] = bp;
         }
     } else {
-        const int64_t c = p.chunk > 0 ? p.chunk : 1;
         for (;;) {
             const int64_t k = (int64_t)claim_chunk(p.sc.chunk_counter);
-            if (k >= p.nchunks) break;
+            int64_t k0, k1;
+            if (!dyn_chunk(p.sc, p.chunk, p.trip, k, k0, k1)) break;
             Terms t{facc_identity(FOP), iacc_identity(IOP), 0};
-            body_range<BODY, FOP, IOP>(p, t, k * c, min(k * c + c, p.trip), w);
+            body_range<BODY, FOP, IOP>(p, t, k0, k1, w);
             if (HR) p.sc.partials[k] = make_partial(t.f, t.i);
         }
     }

@@ -93,15 +93,14 @@ __global__ void __launch_bounds__(256) gemm_f32_kernel(const GemmParams p) {
 
     if (p.sched == UPIR_SCHED_DYNAMIC) {
         __shared__ int64_t next;
-        const int64_t c = p.chunk > 0 ? p.chunk : 1;
-        const int64_t nchunks = (ntiles + c - 1) / c;
         for (;;) {
             if (t == 0) next = (int64_t)atomicAdd(p.sc.chunk_counter, 1ull);
             __syncthreads();
             const int64_t j = next;
             __syncthreads();
-            if (j >= nchunks) break;
-            for (int64_t tile = j * c; tile < min(j * c + c, ntiles); ++tile) do_tile(tile);
+            int64_t t0, t1;
+            if (!dyn_chunk(p.sc, p.chunk, ntiles, j, t0, t1)) break;
+            for (int64_t tile = t0; tile < t1; ++tile) do_tile(tile);
         }
         __shared__ int last;
         __syncthreads();

@@ -26,14 +26,13 @@ __global__ void __launch_bounds__(1024) matvec_kernel(const MatvecParams p) {
         }
     };
     if (p.sched == UPIR_SCHED_DYNAMIC) {
-        const int64_t c = p.chunk > 0 ? p.chunk : 1;
-        const int64_t nchunks = (p.trip + c - 1) / c;
         for (;;) {
             unsigned long long j = 0;
             if (lane == 0) j = atomicAdd(p.sc.chunk_counter, 1ull);
             j = __shfl_sync(0xffffffffu, j, 0);
-            if ((int64_t)j >= nchunks) break;
-            rows((int64_t)j * c, min((int64_t)j * c + c, p.trip));
+            int64_t k0, k1;
+            if (!dyn_chunk(p.sc, p.chunk, p.trip, (int64_t)j, k0, k1)) break;
+            rows(k0, k1);
         }
         __shared__ int last;
         __syncthreads();

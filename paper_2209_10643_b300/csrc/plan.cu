@@ -37,11 +37,13 @@ struct Check {
 };
 
 // Device scratch: [chunk counter u64][ticket u32][pad][group tickets u32 x G]
-// [group partials x G][partials x S], zeroed once.
+// [group partials x G][partials x S][chunk starts i64 x (chunks + 1)], zeroed
+// once, then the loop's chunk table (guided schedules, taskloops) copied in.
 upir_status alloc_scratch(upir_ctx ctx, LoopRec& lp, int64_t ngroups, int64_t nslots, Scratch* sc) {
     const size_t head = 16;
     const size_t gt = ((size_t)ngroups * 4 + 15) / 16 * 16;
-    const size_t bytes = head + gt + (size_t)ngroups * sizeof(Partial) + (size_t)nslots * sizeof(Partial);
+    const size_t tab_off = head + gt + (size_t)ngroups * sizeof(Partial) + (size_t)nslots * sizeof(Partial);
+    const size_t bytes = tab_off + lp.chunk_table.size() * sizeof(int64_t);
     char* p = static_cast<char*>(dev_alloc(ctx, bytes));
     if (!p) return fail(ctx, UPIR_ENOMEM, "upir_loop: scratch allocation of %zu bytes failed", bytes);
     cudaError_t e = cudaMemsetAsync(p, 0, bytes, ctx->stream);
@@ -58,7 +60,69 @@ upir_status alloc_scratch(upir_ctx ctx, LoopRec& lp, int64_t ngroups, int64_t ns
     sc->group_tickets = reinterpret_cast<unsigned*>(p + head);
     sc->group_partials = reinterpret_cast<Partial*>(p + head + gt);
     sc->partials = sc->group_partials + ngroups;
+    sc->chunk_starts = nullptr;
+    sc->nchunks_tab = 0;
+    if (!lp.chunk_table.empty()) {
+        // the host table lives in the loop record, so the copy may stay in flight
+        e = cudaMemcpyAsync(p + tab_off, lp.chunk_table.data(), lp.chunk_table.size() * sizeof(int64_t),
+                            cudaMemcpyHostToDevice, ctx->stream);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "upir_loop: chunk table copy");
+        sc->chunk_starts = reinterpret_cast<const int64_t*>(p + tab_off);
+        sc->nchunks_tab = (int64_t)lp.chunk_table.size() - 1;
+    }
     return UPIR_OK;
+}
+
+bool is_dyn(int sched) {
+    return sched == UPIR_SCHED_DYNAMIC || sched == UPIR_SCHED_GUIDED || sched == UPIR_SCHED_TASKLOOP;
+}
+
+// Kernels know two ways of handing out work: static ranges, or chunks claimed
+// from a counter (of fixed size, or from the chunk table).
+int kernel_sched(int sched) { return is_dyn(sched) ? UPIR_SCHED_DYNAMIC : UPIR_SCHED_STATIC; }
+
+constexpr int64_t kDefaultTasks = 8 * kNumSMs;  // taskloop without grainsize / num_tasks
+
+int64_t taskloop_tasks(const LoopRec& lp, int64_t n) {
+    if (n <= 0) return 0;
+    int64_t t = -1;
+    if (lp.num_tasks > 0) t = std::min(lp.num_tasks, n);
+    if (lp.grainsize > 0) t = t < 0 ? std::max<int64_t>(1, n / lp.grainsize)
+                                    : std::min(t, std::max<int64_t>(1, n / lp.grainsize));
+    return t < 0 ? std::min(kDefaultTasks, n) : t;
+}
+
+// Number of chunks handed out dynamically over n units, for sizing the grid
+// (guided: an upper bound; the table is built once the workers are known).
+int64_t dyn_estimate(const LoopRec& lp, int64_t n) {
+    if (lp.sched == UPIR_SCHED_TASKLOOP) return taskloop_tasks(lp, n);
+    return ceil_div(n, lp.chunk > 0 ? lp.chunk : 1);
+}
+
+// The chunk table of a guided schedule or a taskloop over n units with W
+// workers (§3.2; see upir_sched); returns the number of chunks handed out
+// dynamically, also kept in lp.nchunks.
+int64_t build_chunk_table(LoopRec& lp, int64_t n, int64_t workers) {
+    lp.chunk_table.clear();
+    if (lp.sched == UPIR_SCHED_GUIDED) {
+        const int64_t c = lp.chunk > 0 ? lp.chunk : 1, W = std::max<int64_t>(workers, 1);
+        int64_t s = 0;
+        lp.chunk_table.push_back(0);
+        while (s < n) {
+            s += std::min(n - s, std::max(c, ceil_div(n - s, W)));
+            lp.chunk_table.push_back(s);
+        }
+    } else if (lp.sched == UPIR_SCHED_TASKLOOP) {
+        const int64_t t = taskloop_tasks(lp, n);
+        lp.chunk_table.push_back(0);
+        for (int64_t k = 0, s = 0; k < t; ++k) {
+            s += n / t + (k < n % t ? 1 : 0);
+            lp.chunk_table.push_back(s);
+        }
+    }
+    lp.nchunks = lp.chunk_table.empty() ? ceil_div(n, lp.chunk > 0 ? lp.chunk : 1)
+                                        : (int64_t)lp.chunk_table.size() - 1;
+    return lp.nchunks;
 }
 
 int default_teams_for_chunks(int64_t nchunks, int units) {
@@ -121,7 +185,7 @@ upir_status plan_loop(upir_region r, const upir_loop_desc* d, LoopRec& lp) {
     if (!ok(d != nullptr, UPIR_EINVAL, "descriptor is NULL")) return ok.st;
     ok(d->step != 0, UPIR_EINVAL, "step must be non-zero");
     ok(d->chunk >= 0, UPIR_EINVAL, "chunk must be >= 0");
-    ok(d->sched == UPIR_SCHED_STATIC || d->sched == UPIR_SCHED_DYNAMIC, UPIR_EINVAL, "unknown schedule");
+    ok(d->sched >= UPIR_SCHED_STATIC && d->sched <= UPIR_SCHED_TASKLOOP, UPIR_EINVAL, "unknown schedule");
     ok(d->body >= UPIR_BODY_AXPY && d->body <= UPIR_BODY_FILTER7, UPIR_EINVAL, "unknown body");
     ok(d->nbufs >= 0 && (d->nbufs == 0 || d->bufs), UPIR_EINVAL, "bad buffer list");
     ok(d->nscalars >= 0 && (d->nscalars == 0 || d->scalars), UPIR_EINVAL, "bad scalar list");
@@ -154,8 +218,30 @@ upir_status plan_loop(upir_region r, const upir_loop_desc* d, LoopRec& lp) {
         else if (k == UPIR_HINT_TILE_N) ok(v >= 4 && v <= 248 && v % 4 == 0, UPIR_EINVAL, "tile_n hint must be a multiple of 4 in [4, 248]"), lp.tile_n = (int)v;
         else if (k == UPIR_HINT_VEC) ok(v == 1 || v == 4 || v == 8 || v == 16, UPIR_EINVAL, "vec hint must be 1, 4, 8 or 16"), lp.vec = (int)v;
         else if (k == UPIR_HINT_STAGES) ok(v >= 1 && v <= 4, UPIR_EINVAL, "stages hint must be in [1, 4]"), lp.stages = (int)v;
+        else if (k == UPIR_HINT_GRAINSIZE) ok(v >= 1, UPIR_EINVAL, "grainsize hint must be >= 1"), lp.grainsize = v;
+        else if (k == UPIR_HINT_NUM_TASKS) ok(v >= 1, UPIR_EINVAL, "num_tasks hint must be >= 1"), lp.num_tasks = v;
         else ok(false, UPIR_EINVAL, "unknown hint key");
     }
+    if (ok.st) return ok.st;
+
+    // Schedule: RUNTIME takes the context's run schedule, AUTO the cost
+    // model's pick (§3.2 schedule policies; see upir_sched).
+    if (lp.sched == UPIR_SCHED_RUNTIME) {
+        lp.sched = ctx->run_sched;
+        lp.chunk = ctx->run_chunk;
+    }
+    int auto_units = 0;
+    if (lp.sched == UPIR_SCHED_AUTO) {
+        int s2 = UPIR_SCHED_STATIC;
+        int64_t c2 = 0;
+        auto_schedule(ctx, r, d, lp.trip, &s2, &c2, &auto_units);
+        lp.sched = s2;
+        lp.chunk = c2;
+    }
+    ok(lp.sched != UPIR_SCHED_TASKLOOP || lp.chunk == 0, UPIR_EINVAL,
+       "taskloop takes no chunk (GRAINSIZE / NUM_TASKS hints set its tasks)");
+    ok(lp.sched == UPIR_SCHED_TASKLOOP || (lp.grainsize == 0 && lp.num_tasks == 0), UPIR_EINVAL,
+       "GRAINSIZE / NUM_TASKS hints need the TASKLOOP schedule");
     if (ok.st) return ok.st;
 
     // Reductions: at most one FP32 and one int64 clause.
@@ -217,7 +303,7 @@ upir_status plan_loop(upir_region r, const upir_loop_desc* d, LoopRec& lp) {
     const int U0 = r->units, T0 = r->teams;
     // implicit barrier after the previous loop of the region unless it was nowait
     const int wait_prior = (r->loops.empty() || !r->loops.back()->nowait) ? 1 : 0;
-    lp.units = U0 ? U0 : 256;
+    lp.units = U0 ? U0 : (auto_units ? auto_units : 256);
     lp.kind = LK_ELEM;
     ElemParams& ep = lp.ep;
     memset(&ep, 0, sizeof(ep));
@@ -310,7 +396,7 @@ upir_status plan_loop(upir_region r, const upir_loop_desc* d, LoopRec& lp) {
                 jp.tiles_c = ceil_div(C, lp.tile_n);
                 jp.ntiles = jp.tiles_r * jp.tiles_c;
                 jp.chunk = lp.chunk;
-                jp.sched = lp.sched;
+                jp.sched = kernel_sched(lp.sched);
                 jp.rvar = rv.fvar;
                 jp.rop = rv.fop == UPIR_RED_MIN ? UPIR_RED_MIN : UPIR_RED_MAX;
                 jp.spin_limit = ctx->spin_limit;
@@ -326,16 +412,16 @@ upir_status plan_loop(upir_region r, const upir_loop_desc* d, LoopRec& lp) {
                 // every team gets the same number of tiles (to within one)
                 const int per_sm = std::max(1, jacobi_tma_max_teams_per_sm(lp.units, lp.tile_m, lp.tile_n, jp.stages));
                 const int64_t slots = (int64_t)kNumSMs * per_sm;
-                const int64_t c = lp.chunk > 0 ? lp.chunk : 1;
                 if (T0) lp.teams = T0;
                 else if (lp.sched == UPIR_SCHED_STATIC && lp.chunk == 0) {
                     const int64_t per = std::max<int64_t>(1, ceil_div(jp.ntiles, slots));
                     lp.teams = (int)std::max<int64_t>(1, ceil_div(jp.ntiles, per));
                 } else {
-                    lp.teams = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(jp.ntiles, c), slots));
+                    lp.teams = (int)std::max<int64_t>(1, std::min<int64_t>(dyn_estimate(lp, jp.ntiles), slots));
                 }
                 jp.sk = make_sched_const(jp.ntiles, lp.chunk, lp.teams);
-                if (lp.sched == UPIR_SCHED_DYNAMIC) {
+                if (is_dyn(lp.sched)) {
+                    build_chunk_table(lp, jp.ntiles, lp.teams);
                     upir_status st = alloc_scratch(ctx, lp, 0, 0, &jp.sc);
                     if (st != UPIR_OK) return st;
                 }
@@ -422,7 +508,7 @@ upir_status plan_loop(upir_region r, const upir_loop_desc* d, LoopRec& lp) {
             tp.tiles_c = ceil_div(C, lp.tile_n);
             tp.ntiles = tp.tiles_r * tp.tiles_c;
             tp.chunk = lp.chunk;
-            tp.sched = lp.sched;
+            tp.sched = kernel_sched(lp.sched);
             tp.rvar = rv.fvar;
             tp.rop = rv.fop == UPIR_RED_MIN ? UPIR_RED_MIN : UPIR_RED_MAX;
             tp.spin_limit = ctx->spin_limit;
@@ -435,16 +521,16 @@ upir_status plan_loop(upir_region r, const upir_loop_desc* d, LoopRec& lp) {
                 if (st != UPIR_OK) return st;
             }
             // one persistent team per SM, tiles balanced to within one
-            const int64_t c = lp.chunk > 0 ? lp.chunk : 1;
             if (T0) lp.teams = T0;
             else if (lp.sched == UPIR_SCHED_STATIC && lp.chunk == 0) {
                 const int64_t per = std::max<int64_t>(1, ceil_div(tp.ntiles, kNumSMs));
                 lp.teams = (int)std::max<int64_t>(1, ceil_div(tp.ntiles, per));
             } else {
-                lp.teams = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(tp.ntiles, c), kNumSMs));
+                lp.teams = (int)std::max<int64_t>(1, std::min<int64_t>(dyn_estimate(lp, tp.ntiles), kNumSMs));
             }
             tp.sk = make_sched_const(tp.ntiles, lp.chunk, lp.teams);
-            if (lp.sched == UPIR_SCHED_DYNAMIC) {
+            if (is_dyn(lp.sched)) {
+                build_chunk_table(lp, tp.ntiles, lp.teams);
                 upir_status st = alloc_scratch(ctx, lp, 0, 0, &tp.sc);
                 if (st != UPIR_OK) return st;
             }
@@ -498,7 +584,7 @@ upir_status plan_loop(upir_region r, const upir_loop_desc* d, LoopRec& lp) {
             fp.tiles_c = ceil_div(C, lp.tile_n);
             fp.ntiles = fp.tiles_r * fp.tiles_c;
             fp.chunk = lp.chunk;
-            fp.sched = lp.sched;
+            fp.sched = kernel_sched(lp.sched);
             fp.spin_limit = ctx->spin_limit;
             fp.err_word = ctx->err_word;
             fp.wait_prior = wait_prior;
@@ -511,16 +597,16 @@ upir_status plan_loop(upir_region r, const upir_loop_desc* d, LoopRec& lp) {
             }
             const int per_sm = std::max(1, filter7_max_teams_per_sm(lp.tile_m, lp.tile_n));
             const int64_t slots = (int64_t)kNumSMs * per_sm;
-            const int64_t c = lp.chunk > 0 ? lp.chunk : 1;
             if (T0) lp.teams = T0;
             else if (lp.sched == UPIR_SCHED_STATIC && lp.chunk == 0) {
                 const int64_t per = std::max<int64_t>(1, ceil_div(fp.ntiles, slots));
                 lp.teams = (int)std::max<int64_t>(1, ceil_div(fp.ntiles, per));
             } else {
-                lp.teams = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(fp.ntiles, c), slots));
+                lp.teams = (int)std::max<int64_t>(1, std::min<int64_t>(dyn_estimate(lp, fp.ntiles), slots));
             }
             fp.sk = make_sched_const(fp.ntiles, lp.chunk, lp.teams);
-            if (lp.sched == UPIR_SCHED_DYNAMIC) {
+            if (is_dyn(lp.sched)) {
+                build_chunk_table(lp, fp.ntiles, lp.teams);
                 upir_status st = alloc_scratch(ctx, lp, 0, 0, &fp.sc);
                 if (st != UPIR_OK) return st;
             }
@@ -554,7 +640,7 @@ upir_status plan_loop(upir_region r, const upir_loop_desc* d, LoopRec& lp) {
             mp.step = lp.step;
             mp.trip = lp.trip;
             mp.chunk = lp.chunk;
-            mp.sched = lp.sched;
+            mp.sched = kernel_sched(lp.sched);
             const int64_t wpb = lp.units / 32;
             const int64_t resident_warps = (int64_t)kNumSMs * (kResidentThreadsPerSM / 32);
             if (T0) lp.teams = T0;
@@ -562,13 +648,13 @@ upir_status plan_loop(upir_region r, const upir_loop_desc* d, LoopRec& lp) {
                 const int64_t per = std::max<int64_t>(1, ceil_div(lp.trip, resident_warps));
                 lp.teams = (int)std::max<int64_t>(1, ceil_div(ceil_div(lp.trip, per), wpb));
             } else {
-                const int64_t c = lp.chunk > 0 ? lp.chunk : 1;
-                lp.teams = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(ceil_div(lp.trip, c), wpb),
+                lp.teams = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(dyn_estimate(lp, lp.trip), wpb),
                                                                        resident_warps / wpb));
             }
             mp.sk = make_sched_const(lp.trip, lp.chunk, (int64_t)lp.teams * wpb);
             mp.wait_prior = wait_prior;
-            if (lp.sched == UPIR_SCHED_DYNAMIC) {
+            if (is_dyn(lp.sched)) {
+                build_chunk_table(lp, lp.trip, (int64_t)lp.teams * wpb);
                 upir_status st = alloc_scratch(ctx, lp, 0, 0, &mp.sc);
                 if (st != UPIR_OK) return st;
             }
@@ -610,16 +696,16 @@ upir_status plan_loop(upir_region r, const upir_loop_desc* d, LoopRec& lp) {
                 gp.row_lb = lp.lb;
                 gp.row_ub = lp.lb + lp.trip;
                 gp.chunk = lp.chunk;
-                gp.sched = lp.sched;
+                gp.sched = kernel_sched(lp.sched);
                 const int64_t ntiles = ceil_div(lp.trip, 128) * ceil_div(N, 128);
-                const int64_t c = lp.chunk > 0 ? lp.chunk : 1;
                 if (T0) lp.teams = T0;
                 else if (lp.sched == UPIR_SCHED_STATIC && lp.chunk == 0)
                     lp.teams = (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, 0x7fffffff));
                 else
-                    lp.teams = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(ntiles, c), kNumSMs * 2));
+                    lp.teams = (int)std::max<int64_t>(1, std::min<int64_t>(dyn_estimate(lp, ntiles), kNumSMs * 2));
                 gp.sk = make_sched_const(ntiles, lp.chunk, lp.teams);
-                if (lp.sched == UPIR_SCHED_DYNAMIC) {
+                if (is_dyn(lp.sched)) {
+                    build_chunk_table(lp, ntiles, lp.teams);
                     upir_status st = alloc_scratch(ctx, lp, 0, 0, &gp.sc);
                     if (st != UPIR_OK) return st;
                 }
@@ -675,7 +761,7 @@ upir_status plan_loop(upir_region r, const upir_loop_desc* d, LoopRec& lp) {
     const int64_t vdef = has_red ? 8 : 4;
     // reducing element loops run better in smaller teams (more, shorter-lived
     // blocks overlap their block-level reduction trees with other blocks' loads)
-    if (!U0 && has_red && lp.body == UPIR_BODY_AXPY) lp.units = 128;
+    if (!U0 && !auto_units && has_red && lp.body == UPIR_BODY_AXPY) lp.units = 128;
     const int U = lp.units;
     const int64_t V = (lp.body == UPIR_BODY_AXPY && lp.step == 1) ? (lp.vec ? lp.vec : vdef)
                       : (lp.body == UPIR_BODY_IMOD ? vdef : 1);
@@ -689,12 +775,13 @@ upir_status plan_loop(upir_region r, const upir_loop_desc* d, LoopRec& lp) {
             if (st != UPIR_OK) return st;
         }
     } else {
-        const int64_t c = lp.chunk > 0 ? lp.chunk : 1;
-        ep.nchunks = ceil_div(trip, c);
-        if (has_red && !ok(ep.nchunks <= (1ll << 27), UPIR_EUNSUPPORTED,
+        // dynamic, guided or taskloop: chunks claimed from a counter
+        const int64_t est = dyn_estimate(lp, trip);
+        if (has_red && !ok(est <= (1ll << 27), UPIR_EUNSUPPORTED,
                            "dynamic reductions need at most 2^27 chunks (raise the chunk)"))
             return ok.st;
-        lp.teams = T0 ? T0 : default_teams_for_chunks(ep.nchunks, U);
+        lp.teams = T0 ? T0 : default_teams_for_chunks(est, U);
+        ep.nchunks = build_chunk_table(lp, trip, (int64_t)lp.teams * U);
         const int64_t nslots = has_red ? ep.nchunks : 0;
         upir_status st = alloc_scratch(ctx, lp, finalize_groups(nslots), nslots, &ep.sc);
         if (st != UPIR_OK) return st;
@@ -706,7 +793,7 @@ upir_status plan_loop(upir_region r, const upir_loop_desc* d, LoopRec& lp) {
 cudaError_t launch_loop(upir_ctx ctx, LoopRec& lp, cudaStream_t s) {
     switch (lp.kind) {
         case LK_ELEM:
-            return launch_elem(lp.body, lp.sched == UPIR_SCHED_DYNAMIC, lp.ep.rv.fvar ? lp.ep.rv.fop : 0,
+            return launch_elem(lp.body, is_dyn(lp.sched), lp.ep.rv.fvar ? lp.ep.rv.fop : 0,
                                lp.ep.rv.ivar ? lp.ep.rv.iop : 0, lp.teams, lp.units, lp.ep, s);
         case LK_JACOBI_TMA: return launch_jacobi_tma(lp.teams, lp.units, lp.jp, &lp.tmap[0], s);
         case LK_MATVEC: return launch_matvec(lp.teams, lp.units, lp.mp, s);

@@ -106,6 +106,19 @@ extern "C" upir_status upir_init(upir_ctx* out, int32_t device, void* cuda_strea
     }
     const char* env = getenv("UPIR_SPIN_LIMIT");
     if (env && atoll(env) > 0) c->spin_limit = atoll(env);
+    // run schedule of UPIR_SCHED_RUNTIME loops: "static|dynamic|guided[,chunk]"
+    if (const char* rs = getenv("UPIR_SCHEDULE")) {
+        const std::string v(rs);
+        const size_t comma = v.find(',');
+        const std::string kind = v.substr(0, comma);
+        const long long ch = comma == std::string::npos ? 0 : atoll(v.c_str() + comma + 1);
+        const int k = kind == "static" ? UPIR_SCHED_STATIC : kind == "dynamic" ? UPIR_SCHED_DYNAMIC
+                      : kind == "guided" ? UPIR_SCHED_GUIDED : -1;
+        if (k >= 0 && ch >= 0) {
+            c->run_sched = k;
+            c->run_chunk = ch;
+        }
+    }
     c->err_word = static_cast<int*>(dev_alloc(c.get(), 256));
     if (!c->err_word) {
         if (c->own_stream) cudaStreamDestroy(c->stream);
@@ -339,6 +352,26 @@ extern "C" upir_status upir_sync(upir_region r, int32_t kind) {
     }
     if (kind == UPIR_SYNC_TASKWAIT) return upir_ctx_wait(r->ctx);
     return fail(r->ctx, UPIR_EINVAL, "upir_sync: unknown kind %d", kind);
+}
+
+extern "C" upir_status upir_region_loop_schedule(upir_region r, int32_t i, int32_t* sched, int64_t* chunk,
+                                                 int64_t* nchunks) {
+    if (!r) return UPIR_EINVAL;
+    if (i < 0 || i >= (int32_t)r->loops.size()) return fail(r->ctx, UPIR_EINVAL, "loop index out of range");
+    const LoopRec& lp = *r->loops[i];
+    if (sched) *sched = lp.sched;
+    if (chunk) *chunk = lp.chunk;
+    if (nchunks) *nchunks = lp.sched == UPIR_SCHED_STATIC ? 0 : lp.nchunks;
+    return UPIR_OK;
+}
+
+extern "C" upir_status upir_ctx_set_run_schedule(upir_ctx ctx, int32_t sched, int64_t chunk) {
+    if (!ctx) return UPIR_EINVAL;
+    if ((sched != UPIR_SCHED_STATIC && sched != UPIR_SCHED_DYNAMIC && sched != UPIR_SCHED_GUIDED) || chunk < 0)
+        return fail(ctx, UPIR_EINVAL, "upir_ctx_set_run_schedule: STATIC, DYNAMIC or GUIDED with chunk >= 0");
+    ctx->run_sched = sched;
+    ctx->run_chunk = chunk;
+    return UPIR_OK;
 }
 
 extern "C" upir_status upir_region_loop_geometry(upir_region r, int32_t i, int32_t* teams,

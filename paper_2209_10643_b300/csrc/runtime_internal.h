@@ -35,6 +35,10 @@ struct LoopRec {
     std::vector<double> scalars;
     std::vector<upir_reduction> reds;
     int variant = 0, tile_m = 0, tile_n = 0, vec = 0, stages = 0;  // 0: planner default
+    int64_t grainsize = 0, num_tasks = 0;  // taskloop hints
+    // guided / taskloop chunk starts (host copy; the device copy is in scratch)
+    std::vector<int64_t> chunk_table;
+    int64_t nchunks = 0;  // chunks or tasks handed out dynamically (0: static)
     int teams = 0, units = 0;
     int kind = LK_ELEM;
     bool skip = false;       // zero-trip loop: nothing to launch
@@ -89,6 +93,9 @@ struct upir_ctx_s {
     std::vector<cudaEvent_t> event_pool;
     void* mlp_scratch = nullptr;      // per-team gradient partials of the cost model
     size_t mlp_scratch_bytes = 0;
+    int run_sched = UPIR_SCHED_STATIC;  // what UPIR_SCHED_RUNTIME loops take
+    int64_t run_chunk = 0;
+    std::vector<float> cm_params, cm_mean, cm_std;  // cost model for UPIR_SCHED_AUTO (empty: none)
 };
 
 namespace upir {
@@ -99,6 +106,9 @@ void* dev_alloc(upir_ctx ctx, size_t bytes);
 void dev_free(upir_ctx ctx, void* p, size_t bytes);
 
 upir_status plan_loop(upir_region r, const upir_loop_desc* d, LoopRec& lp);
+// schedule(auto): the cost model's schedule, chunk and units for a loop
+void auto_schedule(upir_ctx ctx, upir_region r, const upir_loop_desc* d, int64_t trip, int* sched, int64_t* chunk,
+                   int* units_out);
 void release_loop(upir_ctx ctx, LoopRec& lp);
 cudaError_t launch_loop(upir_ctx ctx, LoopRec& lp, cudaStream_t s);
 upir_status launch_region_loops(upir_region r, bool timed);

@@ -32,14 +32,11 @@ __device__ __forceinline__ int64_t tile_iter_next(TileIter& it, const P& p) {
         if (it.done) return -1;
         if (it.next < it.end) return it.next++;
         if (p.sched == UPIR_SCHED_DYNAMIC) {
-            const int64_t c = p.chunk > 0 ? p.chunk : 1;
             const int64_t j = (int64_t)atomicAdd(p.sc.chunk_counter, 1ull);
-            if (j * c >= p.ntiles) {
+            if (!dyn_chunk(p.sc, p.chunk, p.ntiles, j, it.next, it.end)) {
                 it.done = true;
                 return -1;
             }
-            it.next = j * c;
-            it.end = min(j * c + c, p.ntiles);
         } else if (p.chunk > 0) {
             if (it.chunk_j >= p.sk.nchunks) {
                 it.done = true;

@@ -50,6 +50,10 @@ struct Scratch {
     unsigned* group_tickets;
     Partial* group_partials;
     Partial* partials;
+    // guided schedules and taskloops: the starts of the nchunks_tab chunks
+    // (and the end of the last), else nullptr for chunks of a fixed size
+    const int64_t* chunk_starts;
+    int64_t nchunks_tab;
 };
 
 // Element-granular loop bodies (AXPY, IMOD, COVERAGE, per-point JACOBI5).
