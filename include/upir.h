@@ -59,6 +59,7 @@ typedef struct upir_ctx_s*    upir_ctx;
 typedef struct upir_buf_s*    upir_buf;
 typedef struct upir_region_s* upir_region;
 typedef struct upir_batch_s*  upir_batch;
+typedef struct upir_event_s*  upir_event;
 
 /* Device allocator callback.  alloc returns device memory of at least `bytes`
  * bytes, 256-byte aligned, usable in stream order on `stream`, or NULL.
@@ -121,6 +122,47 @@ upir_status upir_data_unmap(upir_ctx ctx, upir_buf buf);
 
 /* Device address and size of a mapped buffer. */
 upir_status upir_buf_device_ptr(upir_buf buf, void** device_ptr, size_t* bytes);
+
+/* ----------------------------------------------- asynchronous data movement --
+ * §4 leaves data movement to the runtime "for the purpose of achieving maximum
+ * overlapping and pipelining of computation and data movement".  These calls
+ * put the copies on the context's copy stream, ordered after the work already
+ * submitted, and return at once; a later submission that uses the buffer
+ * waits (on the device) for the copy.  Overlap with computation needs
+ * page-locked host memory (pageable memory still works, without overlap).
+ *
+ * Host->device and device->host copies use separate streams, so both copy
+ * directions and the computation can overlap; one buffer's copies stay in
+ * the order they were issued.
+ * upir_data_map_async: like upir_data_map; TO/TOFROM copy host->device
+ *   asynchronously (the host memory must stay unchanged until the copy is
+ *   done: upir_buf_wait or a later submission that uses the buffer).
+ * upir_data_update_async: like upir_data_update; FROM copies device->host
+ *   asynchronously: read the host memory only after upir_buf_wait.
+ * upir_buf_wait: the host waits for the buffer's pending copy (if any).
+ * upir_data_unmap and upir_ctx_wait also wait for pending copies.
+ * Errors as for the synchronous calls. */
+upir_status upir_data_map_async(upir_ctx ctx, void* host, size_t bytes, int32_t kind, upir_buf* out);
+upir_status upir_data_update_async(upir_ctx ctx, upir_buf buf, int32_t direction);
+upir_status upir_buf_wait(upir_ctx ctx, upir_buf buf);
+
+/* ------------------------------------------------------ two-step sync steps --
+ * §5: a sync is an arrive-compute step (a unit reaches the sync point and its
+ * part of the work is issued) and a wait-release step (it waits for everyone
+ * and is released); the asynchronous form splits them so that work can go
+ * between.  Here the work is what a context has submitted:
+ * upir_ctx_arrive: arrive-compute; *out marks everything submitted to the
+ *   context so far (an event on its stream).
+ * upir_event_query: UPIR_OK when that work has completed, UPIR_EBUSY if not.
+ * upir_event_wait: wait-release on the host (blocks until completion).
+ * upir_ctx_wait_event: wait-release on the device: work later submitted to
+ *   `ctx` starts after the event's work (also across contexts on one device).
+ * upir_event_destroy: release the event (after waits that use it). */
+upir_status upir_ctx_arrive(upir_ctx ctx, upir_event* out);
+upir_status upir_event_query(upir_event ev);
+upir_status upir_event_wait(upir_event ev);
+upir_status upir_ctx_wait_event(upir_ctx ctx, upir_event ev);
+upir_status upir_event_destroy(upir_event ev);
 
 /* ------------------------------------------------------------- SPMD region -- */
 /* §3.1: an SPMD region runs num_teams teams of num_units units each.  Here a

@@ -90,6 +90,14 @@ _SIGS = {
     "upir_ctx_timings": (_i32, [_vp, _P(C.c_float), _P(_i32), _i32, _P(_i32)]),
     "upir_region_loop_geometry": (_i32, [_vp, _i32, _P(_i32), _P(_i32)]),
     "upir_region_loop_schedule": (_i32, [_vp, _i32, _P(_i32), _P(_i64), _P(_i64)]),
+    "upir_data_map_async": (_i32, [_vp, _vp, _sz, _i32, _P(_vp)]),
+    "upir_data_update_async": (_i32, [_vp, _vp, _i32]),
+    "upir_buf_wait": (_i32, [_vp, _vp]),
+    "upir_ctx_arrive": (_i32, [_vp, _P(_vp)]),
+    "upir_event_query": (_i32, [_vp]),
+    "upir_event_wait": (_i32, [_vp]),
+    "upir_ctx_wait_event": (_i32, [_vp, _vp]),
+    "upir_event_destroy": (_i32, [_vp]),
     "upir_ctx_set_run_schedule": (_i32, [_vp, _i32, _i64]),
     "upir_ctx_set_cost_model": (_i32, [_vp, _vp, _vp, _vp]),
     "upir_auto_candidates": (_i32, [_i32, _P(_i32), _P(_i64), _P(_i32), _i32, _P(_i32)]),
@@ -262,6 +270,50 @@ def upir_region_loop_geometry(region: int, index: int) -> tuple[int, int]:
     if st != UPIR_OK:
         raise UpirError(st, "upir_region_loop_geometry")
     return t.value, u.value
+
+
+def upir_data_map_async(ctx: int, host_ptr: int, nbytes: int, kind: int) -> int:
+    h = C.c_void_p()
+    _chk(ctx, lib.upir_data_map_async(ctx, host_ptr, nbytes, kind, C.byref(h)), "upir_data_map_async")
+    return h.value
+
+
+def upir_data_update_async(ctx: int, buf: int, direction: int) -> None:
+    _chk(ctx, lib.upir_data_update_async(ctx, buf, direction), "upir_data_update_async")
+
+
+def upir_buf_wait(ctx: int, buf: int) -> None:
+    _chk(ctx, lib.upir_buf_wait(ctx, buf), "upir_buf_wait")
+
+
+def upir_ctx_arrive(ctx: int) -> int:
+    h = C.c_void_p()
+    _chk(ctx, lib.upir_ctx_arrive(ctx, C.byref(h)), "upir_ctx_arrive")
+    return h.value
+
+
+def upir_event_query(ev: int) -> bool:
+    """True when the event's work has completed."""
+    st = lib.upir_event_query(ev)
+    if st not in (UPIR_OK, UPIR_EBUSY):
+        raise UpirError(st, "upir_event_query")
+    return st == UPIR_OK
+
+
+def upir_event_wait(ev: int) -> None:
+    st = lib.upir_event_wait(ev)
+    if st != UPIR_OK:
+        raise UpirError(st, "upir_event_wait")
+
+
+def upir_ctx_wait_event(ctx: int, ev: int) -> None:
+    _chk(ctx, lib.upir_ctx_wait_event(ctx, ev), "upir_ctx_wait_event")
+
+
+def upir_event_destroy(ev: int) -> None:
+    st = lib.upir_event_destroy(ev)
+    if st != UPIR_OK:
+        raise UpirError(st, "upir_event_destroy")
 
 
 def upir_region_loop_schedule(region: int, index: int) -> tuple[int, int, int]:

@@ -242,6 +242,8 @@ extern "C" upir_status upir_batch_create(upir_ctx ctx, const upir_region* region
 extern "C" upir_status upir_batch_submit(upir_batch b) {
     if (!b) return UPIR_EINVAL;
     upir_ctx ctx = b->ctx;
+    for (upir_region r : b->regions)
+        if (upir_status st = wait_region_buffers(r)) return st;
     if (b->mode == UPIR_BATCH_LAUNCHES) {
         for (upir_region r : b->regions) {
             upir_status st = launch_region_loops(r, ctx->timing);

@@ -136,6 +136,8 @@ extern "C" upir_status upir_finalize(upir_ctx ctx) {
     if (!ctx) return UPIR_OK;
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->stream);
+    if (ctx->copy_stream) cudaStreamSynchronize(ctx->copy_stream);
+    if (ctx->d2h_stream) cudaStreamSynchronize(ctx->d2h_stream);
     cudaGetLastError();
     for (upir_batch b : std::vector<upir_batch>(ctx->batches.begin(), ctx->batches.end()))
         destroy_batch(b);
@@ -143,6 +145,7 @@ extern "C" upir_status upir_finalize(upir_ctx ctx) {
         destroy_region(r);
     for (upir_buf b : ctx->all_bufs) {
         if (b->live && !b->wrapped) dev_free(ctx, b->dev, b->bytes);
+        if (b->ready) cudaEventDestroy(b->ready);
         delete b;
     }
     ctx->all_bufs.clear();
@@ -155,6 +158,8 @@ extern "C" upir_status upir_finalize(upir_ctx ctx) {
     dev_free(ctx, ctx->err_word, 256);
     cudaStreamSynchronize(ctx->stream);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+    if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
+    if (ctx->d2h_stream) cudaStreamDestroy(ctx->d2h_stream);
     cudaGetLastError();
     delete ctx;
     return UPIR_OK;
@@ -162,7 +167,9 @@ extern "C" upir_status upir_finalize(upir_ctx ctx) {
 
 extern "C" upir_status upir_ctx_wait(upir_ctx ctx) {
     if (!ctx) return UPIR_EINVAL;
-    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    cudaError_t e = ctx->copy_stream ? cudaStreamSynchronize(ctx->copy_stream) : cudaSuccess;
+    if (e == cudaSuccess && ctx->d2h_stream) e = cudaStreamSynchronize(ctx->d2h_stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamSynchronize");
     int word = 0;
     e = cudaMemcpyAsync(&word, ctx->err_word, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
@@ -266,11 +273,19 @@ extern "C" upir_status upir_data_unmap(upir_ctx ctx, upir_buf b) {
     if (b->refs > 0)
         return fail(ctx, UPIR_EBUSY, "upir_data_unmap: %d live region loop(s) use this buffer", b->refs);
     cudaError_t e = cudaSuccess;
+    if (b->ready) {
+        // a pending asynchronous copy finishes first (and the compute stream
+        // is ordered after it, for the copy back below)
+        e = cudaStreamWaitEvent(ctx->stream, b->ready, 0);
+        b->pending = false;
+    }
     if (!b->wrapped && b->bytes > 0 && (b->kind == UPIR_MAP_FROM || b->kind == UPIR_MAP_TOFROM))
         e = cudaMemcpyAsync(b->host, b->dev, b->bytes, cudaMemcpyDeviceToHost, ctx->stream);
     cudaError_t e2 = cudaStreamSynchronize(ctx->stream);
     if (e == cudaSuccess) e = e2;
     if (!b->wrapped) dev_free(ctx, b->dev, b->bytes);
+    if (b->ready) cudaEventDestroy(b->ready);
+    b->ready = nullptr;
     b->live = false;
     b->dev = nullptr;
     if (e != cudaSuccess) return cuda_fail(ctx, e, "upir_data_unmap: device->host copy");
@@ -281,6 +296,173 @@ extern "C" upir_status upir_buf_device_ptr(upir_buf b, void** device_ptr, size_t
     if (!b || !b->live) return UPIR_ENOTMAPPED;
     if (device_ptr) *device_ptr = b->dev;
     if (bytes) *bytes = b->bytes;
+    return UPIR_OK;
+}
+
+// ----------------------------------------------- asynchronous data movement --
+
+namespace {
+
+// The copy stream of one direction, created on first use, ordered after the
+// buffer's previous copy and, with after_compute, after the work already
+// submitted to the context.
+upir_status copy_stream_for(upir_ctx ctx, upir_buf b, bool to_device, bool after_compute, cudaStream_t* out) {
+    cudaStream_t& cs = to_device ? ctx->copy_stream : ctx->d2h_stream;
+    if (!cs && cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess)
+        return cuda_fail(ctx, cudaGetLastError(), "creating a copy stream");
+    cudaError_t e = cudaSuccess;
+    if (after_compute) {
+        cudaEvent_t ev;
+        e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventRecord(ev, ctx->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ev, 0);
+        cudaEventDestroy(ev);  // released once the wait has consumed it
+    }
+    if (e == cudaSuccess && b->ready) e = cudaStreamWaitEvent(cs, b->ready, 0);
+    *out = cs;
+    return e == cudaSuccess ? UPIR_OK : cuda_fail(ctx, e, "ordering a copy stream");
+}
+
+// Record the end of a buffer's copy on the stream that carried it.
+upir_status mark_pending(upir_ctx ctx, upir_buf b, cudaStream_t cs) {
+    cudaError_t e = cudaSuccess;
+    if (!b->ready) e = cudaEventCreateWithFlags(&b->ready, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(b->ready, cs);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "recording a copy event");
+    b->pending = true;
+    return UPIR_OK;
+}
+
+}  // namespace
+
+upir_status upir::wait_region_buffers(upir_region r) {
+    upir_ctx ctx = r->ctx;
+    for (auto& lp : r->loops) {
+        auto wait = [&](upir_buf b) -> cudaError_t {
+            if (!b->pending) return cudaSuccess;
+            b->pending = false;
+            return cudaStreamWaitEvent(ctx->stream, b->ready, 0);
+        };
+        for (upir_buf b : lp->bufs)
+            if (cudaError_t e = wait(b)) return cuda_fail(ctx, e, "waiting for a buffer's copy");
+        for (auto& red : lp->reds)
+            if (cudaError_t e = wait(red.var)) return cuda_fail(ctx, e, "waiting for a buffer's copy");
+    }
+    return UPIR_OK;
+}
+
+extern "C" upir_status upir_data_map_async(upir_ctx ctx, void* host, size_t bytes, int32_t kind,
+                                           upir_buf* out) {
+    if (!ctx) return UPIR_EINVAL;
+    if (!out) return fail(ctx, UPIR_EINVAL, "upir_data_map_async: out is NULL");
+    *out = nullptr;
+    if (kind < UPIR_MAP_TO || kind > UPIR_MAP_ALLOC)
+        return fail(ctx, UPIR_EINVAL, "upir_data_map_async: unknown map kind %d", kind);
+    if (!host && bytes > 0 && kind != UPIR_MAP_ALLOC)
+        return fail(ctx, UPIR_EINVAL, "upir_data_map_async: NULL host pointer for a copied mapping");
+    void* dev = dev_alloc(ctx, bytes);
+    if (bytes > 0 && !dev) return fail(ctx, UPIR_ENOMEM, "upir_data_map_async: allocation of %zu bytes failed", bytes);
+    upir_buf b = new upir_buf_s();
+    b->ctx = ctx;
+    b->host = host;
+    b->dev = dev;
+    b->bytes = bytes;
+    b->kind = kind;
+    ctx->all_bufs.insert(b);
+    if (bytes > 0 && (kind == UPIR_MAP_TO || kind == UPIR_MAP_TOFROM)) {
+        // A fresh buffer: the copy need not wait for earlier work, only for
+        // a caller allocator's stream-ordered allocation on the context stream
+        // (cudaMalloc's memory is usable at once); then it runs beside the
+        // computation.
+        cudaStream_t cs = nullptr;
+        upir_status st = copy_stream_for(ctx, b, true, ctx->alloc.alloc != nullptr, &cs);
+        cudaError_t e = st == UPIR_OK ? cudaMemcpyAsync(dev, host, bytes, cudaMemcpyHostToDevice, cs)
+                                      : cudaErrorUnknown;
+        if (st == UPIR_OK && e != cudaSuccess) st = cuda_fail(ctx, e, "upir_data_map_async: host->device copy");
+        if (st == UPIR_OK) st = mark_pending(ctx, b, cs);
+        if (st != UPIR_OK) {
+            if (ctx->copy_stream) cudaStreamSynchronize(ctx->copy_stream);
+            dev_free(ctx, dev, bytes);
+            if (b->ready) cudaEventDestroy(b->ready);
+            ctx->all_bufs.erase(b);
+            delete b;
+            return st;
+        }
+    }
+    *out = b;
+    return UPIR_OK;
+}
+
+extern "C" upir_status upir_data_update_async(upir_ctx ctx, upir_buf b, int32_t direction) {
+    if (!ctx) return UPIR_EINVAL;
+    if (!buf_ok(ctx, b)) return fail(ctx, UPIR_ENOTMAPPED, "upir_data_update_async: buffer not mapped");
+    if (b->wrapped || !b->host) return fail(ctx, UPIR_EINVAL, "upir_data_update_async: no host copy");
+    if (direction != UPIR_MAP_TO && direction != UPIR_MAP_FROM)
+        return fail(ctx, UPIR_EINVAL, "upir_data_update_async: direction must be TO or FROM");
+    if (b->bytes == 0) return UPIR_OK;
+    // after the work submitted so far (which may read or write the buffer)
+    // and after the buffer's previous copy (the copy stream is in order)
+    cudaStream_t cs = nullptr;
+    upir_status st = copy_stream_for(ctx, b, direction == UPIR_MAP_TO, true, &cs);
+    if (st != UPIR_OK) return st;
+    cudaError_t e = direction == UPIR_MAP_TO
+                        ? cudaMemcpyAsync(b->dev, b->host, b->bytes, cudaMemcpyHostToDevice, cs)
+                        : cudaMemcpyAsync(b->host, b->dev, b->bytes, cudaMemcpyDeviceToHost, cs);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "upir_data_update_async");
+    return mark_pending(ctx, b, cs);
+}
+
+extern "C" upir_status upir_buf_wait(upir_ctx ctx, upir_buf b) {
+    if (!ctx) return UPIR_EINVAL;
+    if (!buf_ok(ctx, b)) return fail(ctx, UPIR_ENOTMAPPED, "upir_buf_wait: buffer not mapped");
+    if (!b->ready) return UPIR_OK;
+    cudaError_t e = cudaEventSynchronize(b->ready);
+    return e == cudaSuccess ? UPIR_OK : cuda_fail(ctx, e, "upir_buf_wait");
+}
+
+// ------------------------------------------------------- two-step sync steps --
+
+extern "C" upir_status upir_ctx_arrive(upir_ctx ctx, upir_event* out) {
+    if (!ctx) return UPIR_EINVAL;
+    if (!out) return fail(ctx, UPIR_EINVAL, "upir_ctx_arrive: out is NULL");
+    upir_event ev = new upir_event_s();
+    cudaError_t e = cudaEventCreateWithFlags(&ev->ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(ev->ev, ctx->stream);
+    if (e != cudaSuccess) {
+        if (ev->ev) cudaEventDestroy(ev->ev);
+        delete ev;
+        return cuda_fail(ctx, e, "upir_ctx_arrive");
+    }
+    *out = ev;
+    return UPIR_OK;
+}
+
+extern "C" upir_status upir_event_query(upir_event ev) {
+    if (!ev) return UPIR_EINVAL;
+    const cudaError_t e = cudaEventQuery(ev->ev);
+    if (e == cudaSuccess) return UPIR_OK;
+    if (e == cudaErrorNotReady) {
+        cudaGetLastError();
+        return UPIR_EBUSY;
+    }
+    return UPIR_ECUDA;
+}
+
+extern "C" upir_status upir_event_wait(upir_event ev) {
+    if (!ev) return UPIR_EINVAL;
+    return cudaEventSynchronize(ev->ev) == cudaSuccess ? UPIR_OK : UPIR_ECUDA;
+}
+
+extern "C" upir_status upir_ctx_wait_event(upir_ctx ctx, upir_event ev) {
+    if (!ctx || !ev) return UPIR_EINVAL;
+    const cudaError_t e = cudaStreamWaitEvent(ctx->stream, ev->ev, 0);
+    return e == cudaSuccess ? UPIR_OK : cuda_fail(ctx, e, "upir_ctx_wait_event");
+}
+
+extern "C" upir_status upir_event_destroy(upir_event ev) {
+    if (!ev) return UPIR_EINVAL;
+    cudaEventDestroy(ev->ev);
+    delete ev;
     return UPIR_OK;
 }
 
@@ -454,6 +636,7 @@ extern "C" upir_status upir_region_submit(upir_region r, int32_t flags) {
     if (!r) return UPIR_EINVAL;
     upir_ctx ctx = r->ctx;
     if (flags & ~UPIR_SUBMIT_GRAPH) return fail(ctx, UPIR_EINVAL, "upir_region_submit: unknown flags");
+    if (upir_status st = wait_region_buffers(r)) return st;
     if (!(flags & UPIR_SUBMIT_GRAPH)) return launch_region_loops(r, ctx->timing);
     if (!r->gexec) {
         upir_status st = capture_graph(ctx, {r}, &r->gexec);

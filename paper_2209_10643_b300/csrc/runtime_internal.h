@@ -18,6 +18,12 @@ struct upir_buf_s {
     bool wrapped = false;  // caller-owned device memory
     bool live = true;
     int refs = 0;          // loops of live regions that use this buffer
+    cudaEvent_t ready = nullptr;  // end of the last asynchronous copy
+    bool pending = false;         // the compute stream has not waited for it yet
+};
+
+struct upir_event_s {
+    cudaEvent_t ev = nullptr;
 };
 
 namespace upir {
@@ -93,6 +99,10 @@ struct upir_ctx_s {
     std::vector<cudaEvent_t> event_pool;
     void* mlp_scratch = nullptr;      // per-team gradient partials of the cost model
     size_t mlp_scratch_bytes = 0;
+    // asynchronous copies, host->device and device->host on separate streams
+    // so that both copy directions and the computation overlap (created on
+    // first use)
+    cudaStream_t copy_stream = nullptr, d2h_stream = nullptr;
     int run_sched = UPIR_SCHED_STATIC;  // what UPIR_SCHED_RUNTIME loops take
     int64_t run_chunk = 0;
     std::vector<float> cm_params, cm_mean, cm_std;  // cost model for UPIR_SCHED_AUTO (empty: none)
@@ -119,6 +129,9 @@ void destroy_region(upir_region r);
 upir_status plan_gemm_tc(upir_region r, LoopRec& lp, int64_t M, int64_t N, int64_t K, upir_status st);
 cudaError_t launch_gemm_tc_loop(upir_ctx ctx, LoopRec& lp, cudaStream_t s);
 void destroy_batch(upir_batch b);
+// make the compute stream wait for pending asynchronous copies of the
+// buffers a region's loops use
+upir_status wait_region_buffers(upir_region r);
 
 // Encode a 2D tiled TMA descriptor (row-major [rows][cols] of `elem_bytes`);
 // swizzle_bytes is 0 (none), 32, 64 or 128.
