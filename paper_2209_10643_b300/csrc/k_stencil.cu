@@ -50,8 +50,38 @@ struct TbLane {
     bool own_c;        // the lane's columns belong to the tile
 };
 
-// One 5-point row update of a lane's four columns (JACOBI5's arithmetic);
-// points the loop does not update keep their value when EDGE.
+// Paired FP32 arithmetic (two lanes of one 64-bit register pair per
+// instruction, each rounded to nearest like its scalar form).
+struct F2 {
+    unsigned long long v;
+};
+__device__ __forceinline__ F2 f2(float a, float b) {
+    F2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r.v) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void f2_split(F2 x, float& a, float& b) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(x.v));
+}
+__device__ __forceinline__ F2 f2_add(F2 a, F2 b) {
+    F2 r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+    return r;
+}
+__device__ __forceinline__ F2 f2_sub(F2 a, F2 b) {
+    F2 r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+    return r;
+}
+__device__ __forceinline__ F2 f2_mul(F2 a, F2 b) {
+    F2 r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+    return r;
+}
+
+// One 5-point row update of a lane's four points, 0.25 * ((N + S) + (W + E))
+// with every operation rounded (JACOBI5's arithmetic), two points per paired
+// instruction; points the loop does not update keep their value when EDGE.
 template <bool EDGE>
 __device__ __forceinline__ float4 tb_point4(const TbLane& L, int i, const float4& N, const float4& C,
                                             const float4& S) {
@@ -59,11 +89,13 @@ __device__ __forceinline__ float4 tb_point4(const TbLane& L, int i, const float4
     // copied in; they only feed points outside the valid region
     const float Wl = __shfl_up_sync(0xffffffffu, C.w, 1);
     const float Er = __shfl_down_sync(0xffffffffu, C.x, 1);
+    const F2 q = f2(0.25f, 0.25f);
+    const F2 ns0 = f2_add(f2(N.x, N.y), f2(S.x, S.y)), ns1 = f2_add(f2(N.z, N.w), f2(S.z, S.w));
+    const F2 we0 = f2_add(f2(Wl, C.x), f2(C.y, C.z)), we1 = f2_add(f2(C.y, C.z), f2(C.w, Er));
+    const F2 v0 = f2_mul(q, f2_add(ns0, we0)), v1 = f2_mul(q, f2_add(ns1, we1));
     float4 v;
-    v.x = __fmul_rn(0.25f, __fadd_rn(__fadd_rn(N.x, S.x), __fadd_rn(Wl, C.y)));
-    v.y = __fmul_rn(0.25f, __fadd_rn(__fadd_rn(N.y, S.y), __fadd_rn(C.x, C.z)));
-    v.z = __fmul_rn(0.25f, __fadd_rn(__fadd_rn(N.z, S.z), __fadd_rn(C.y, C.w)));
-    v.w = __fmul_rn(0.25f, __fadd_rn(__fadd_rn(N.w, S.w), __fadd_rn(C.z, Er)));
+    f2_split(v0, v.x, v.y);
+    f2_split(v1, v.z, v.w);
     if (EDGE) {
         const bool urow = i >= L.ulo && i < L.uhi;
         v.x = urow && L.ucol[0] ? v.x : C.x;
@@ -76,9 +108,10 @@ __device__ __forceinline__ float4 tb_point4(const TbLane& L, int i, const float4
 
 // Largest |v - C| of a lane's four points.
 __device__ __forceinline__ float tb_absdiff_max(const float4& v, const float4& C) {
-    const float a = fmaxf(fabsf(__fsub_rn(v.x, C.x)), fabsf(__fsub_rn(v.y, C.y)));
-    const float b = fmaxf(fabsf(__fsub_rn(v.z, C.z)), fabsf(__fsub_rn(v.w, C.w)));
-    return fmaxf(a, b);
+    float d0, d1, d2, d3;
+    f2_split(f2_sub(f2(v.x, v.y), f2(C.x, C.y)), d0, d1);
+    f2_split(f2_sub(f2(v.z, v.w), f2(C.z, C.w)), d2, d3);
+    return fmaxf(fmaxf(fabsf(d0), fabsf(d1)), fmaxf(fabsf(d2), fabsf(d3)));
 }
 
 // Smallest |v - C| over the owned points the loop updates (min reductions).
