@@ -14,10 +14,13 @@ namespace {
 
 __device__ __forceinline__ void axpy_tile(const BatchParams& P, const BatchRegion& R, int64_t t) {
     __shared__ int last;
+    // the region's fields, read once (the stores to y could alias them)
+    const float a = R.a;
+    const int fop = R.fop;
     const int64_t e0 = R.lb + t * P.axpy_tile;
     const int64_t e1 = min(e0 + (int64_t)P.axpy_tile, R.lb + R.trip);
-    FAcc f = facc_identity(R.fop);
-    const bool red = R.fop != 0;
+    FAcc f = facc_identity(fop);
+    const bool red = fop != 0;
     const bool xy = R.fterm == UPIR_TERM_XY;
     auto term = [&](float xv, float yn) {
         if (!red) return;
@@ -38,10 +41,10 @@ __device__ __forceinline__ void axpy_tile(const BatchParams& P, const BatchRegio
             const float4 xv = __ldcs(reinterpret_cast<const float4*>(x + e0) + g);
             const float4 yv = __ldcs(reinterpret_cast<const float4*>(y + e0) + g);
             float4 yn;
-            yn.x = __fmaf_rn(R.a, xv.x, yv.x);
-            yn.y = __fmaf_rn(R.a, xv.y, yv.y);
-            yn.z = __fmaf_rn(R.a, xv.z, yv.z);
-            yn.w = __fmaf_rn(R.a, xv.w, yv.w);
+            yn.x = __fmaf_rn(a, xv.x, yv.x);
+            yn.y = __fmaf_rn(a, xv.y, yv.y);
+            yn.z = __fmaf_rn(a, xv.z, yv.z);
+            yn.w = __fmaf_rn(a, xv.w, yv.w);
             __stcs(reinterpret_cast<float4*>(y + e0) + g, yn);
             term(xv.x, yn.x);
             term(xv.y, yn.y);
@@ -49,13 +52,13 @@ __device__ __forceinline__ void axpy_tile(const BatchParams& P, const BatchRegio
             term(xv.w, yn.w);
         }
         for (int64_t e = e0 + 4 * n4 + threadIdx.x; e < e1; e += blockDim.x) {
-            const float yn = __fmaf_rn(R.a, x[e], y[e]);
+            const float yn = __fmaf_rn(a, x[e], y[e]);
             y[e] = yn;
             term(x[e], yn);
         }
     } else {
         for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-            const float yn = __fmaf_rn(R.a, x[e], y[e]);
+            const float yn = __fmaf_rn(a, x[e], y[e]);
             y[e] = yn;
             term(x[e], yn);
         }
@@ -78,120 +81,214 @@ __device__ __forceinline__ void axpy_tile(const BatchParams& P, const BatchRegio
     }
 }
 
-// Halo rows of the tile are staged in shared memory; shared column j holds
-// grid column c0 - 4 + j, so the tile's first column sits on a 16-byte
-// boundary.  Rows whose width is a multiple of 4 use 128-bit loads, stores
-// and shared-memory reads; other widths take the scalar path.
-__device__ __forceinline__ void jacobi_tile(const BatchParams& P, const BatchRegion& R, int64_t t,
-                                            float* halo) {
-    constexpr int HW = kBatchJacCols + 8;
+constexpr int kHaloW = kBatchJacCols + 8;                          // shared row: 4 + 128 + 4 columns
+constexpr int kHaloFloats = (kBatchMaxJacRows + 2) * kHaloW;
+
+// Rows whose width is a multiple of 4 and 16-byte aligned buffers take the
+// 128-bit paths, including the asynchronous halo copy.
+__device__ __forceinline__ bool jacobi_vec(const BatchRegion& R) {
+    return (R.cols & 3) == 0 && ((reinterpret_cast<uintptr_t>(R.in0) | reinterpret_cast<uintptr_t>(R.out)) & 15) == 0;
+}
+
+// Issue the asynchronous copy of tile t's halo into `halo` and commit it as
+// one group: 16-byte copies for 128-bit-capable regions, 4-byte copies for
+// the others (rows of any width or alignment); columns outside the grid are
+// zero-filled.  Shared column j holds grid column c0 - 4 + j, so the tile's
+// first column sits on a 16-byte boundary.
+__device__ __forceinline__ void jacobi_halo_async(const BatchParams& P, const BatchRegion& R, int64_t t,
+                                                  float* halo) {
     const int64_t band = t / R.tiles_c, tc = t - band * R.tiles_c;
     const int64_t r0 = R.lb + band * P.jac_rows;
     const int nr = (int)min((int64_t)P.jac_rows, R.lb + R.trip - r0);
-    const int64_t c0 = tc * kBatchJacCols;
-    const int64_t cols = R.cols;
-    const float* u = R.in0;
-    const bool vec = (cols & 3) == 0 && ((reinterpret_cast<uintptr_t>(u) | reinterpret_cast<uintptr_t>(R.out)) & 15) == 0;
-    if (vec) {
-        // all of this thread's loads are issued before any shared-memory
-        // store, so their DRAM latencies overlap instead of adding up
-        constexpr int kMaxLd = ((kBatchMaxJacRows + 2) * (HW / 4) + kBatchUnits - 1) / kBatchUnits;
-        const int n4 = (nr + 2) * (HW / 4);
-        float4 v[kMaxLd];
-#pragma unroll
-        for (int k = 0; k < kMaxLd; ++k) {
-            const int idx = threadIdx.x + k * kBatchUnits;
-            v[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (idx < n4) {
-                const int i = idx / (HW / 4), q = idx - i * (HW / 4);
-                const int64_t rr = r0 - 1 + i, cc = c0 - 4 + 4 * q;
-                if (cc >= 0 && cc + 3 < cols) v[k] = __ldcs(reinterpret_cast<const float4*>(u + rr * cols + cc));
+    const int64_t c0 = tc * kBatchJacCols, cols = R.cols;
+    // a warp per halo row; a lane's columns advance by 32 copies at a time
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = kBatchUnits / 32;
+    const int64_t cfirst = c0 - 4;  // grid column of shared column 0
+    if (jacobi_vec(R)) {
+        for (int i = warp; i < nr + 2; i += nw) {
+            const float* grow = R.in0 + (r0 - 1 + i) * cols;
+            const uint32_t srow = smem_u32(halo + i * kHaloW);
+            for (int q = lane; q < kHaloW / 4; q += 32) {
+                const int64_t cc = cfirst + 4 * q;
+                const bool in = cc >= 0 && cc + 3 < cols;
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;"
+                             ::"r"(srow + 16u * q), "l"(in ? grow + cc : R.in0), "r"(in ? 16 : 0) : "memory");
             }
         }
-#pragma unroll
-        for (int k = 0; k < kMaxLd; ++k) {
-            const int idx = threadIdx.x + k * kBatchUnits;
-            if (idx < n4) *reinterpret_cast<float4*>(halo + 4 * idx) = v[k];
-        }
     } else {
-        for (int idx = threadIdx.x; idx < (nr + 2) * HW; idx += blockDim.x) {
-            const int i = idx / HW, j = idx - i * HW;
-            const int64_t rr = r0 - 1 + i, cc = c0 - 4 + j;
-            halo[idx] = (cc >= 0 && cc < cols) ? u[rr * cols + cc] : 0.0f;
+        for (int i = warp; i < nr + 2; i += nw) {
+            const float* grow = R.in0 + (r0 - 1 + i) * cols;
+            const uint32_t srow = smem_u32(halo + i * kHaloW);
+#pragma unroll
+            for (int j = lane; j < kHaloW; j += 32) {
+                const int64_t cc = cfirst + j;
+                const bool in = cc >= 0 && cc < cols;
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;"
+                             ::"r"(srow + 4u * j), "l"(in ? grow + cc : R.in0), "r"(in ? 4 : 0) : "memory");
+            }
         }
     }
-    __syncthreads();
-    float racc = R.fop == UPIR_RED_MIN ? __int_as_float(0x7f800000) : -__int_as_float(0x7f800000);
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5, nty = blockDim.x >> 5;
-    const int64_t c = c0 + 4 * tx;
-    const bool full = vec && c >= 1 && c + 3 <= cols - 2;
-    for (int i = ty; i < nr; i += nty) {
-        const float* cen = halo + (i + 1) * HW + 4 + 4 * tx;
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+// One Jacobi tile.  `staged`: its halo copy was issued into `halo` while the
+// previous item ran.  `next` (may be null): a following Jacobi item whose
+// halo copy is issued into `halo_next` before this tile computes, so that its
+// DRAM latency overlaps this tile's work.
+// The rows i = i0, i0 + step, ... < nr of one lane's four columns, from the
+// staged halo to the output (5-point stencil, JACOBI5's arithmetic), folding
+// |new - old| of the updated points into the residual (FOP 0: none).
+template <int FOP>
+__device__ __forceinline__ float jacobi_rows(const float* cen, float* out, int i0, int nr, int step, int64_t ostep,
+                                             bool inside, bool full, int64_t c, int64_t cols) {
+    constexpr int HW = kHaloW;
+    float racc = FOP == UPIR_RED_MIN ? __int_as_float(0x7f800000) : -__int_as_float(0x7f800000);
+    for (int i = i0; i < nr; i += step, cen += step * HW, out += ostep) {
         const float4 C = *reinterpret_cast<const float4*>(cen);
         const float4 N = *reinterpret_cast<const float4*>(cen - HW);
         const float4 S = *reinterpret_cast<const float4*>(cen + HW);
         const float Wl = cen[-1], Er = cen[4];
-        float vs[4], cs[4] = {C.x, C.y, C.z, C.w};
-        vs[0] = __fmul_rn(0.25f, __fadd_rn(__fadd_rn(N.x, S.x), __fadd_rn(Wl, C.y)));
-        vs[1] = __fmul_rn(0.25f, __fadd_rn(__fadd_rn(N.y, S.y), __fadd_rn(C.x, C.z)));
-        vs[2] = __fmul_rn(0.25f, __fadd_rn(__fadd_rn(N.z, S.z), __fadd_rn(C.y, C.w)));
-        vs[3] = __fmul_rn(0.25f, __fadd_rn(__fadd_rn(N.w, S.w), __fadd_rn(C.z, Er)));
-        float* out = R.out + (r0 + i) * cols + c;
-        if (full) {
-            __stcs(reinterpret_cast<float4*>(out), make_float4(vs[0], vs[1], vs[2], vs[3]));
-            if (R.fop)
-#pragma unroll
-                for (int j = 0; j < 4; ++j) racc = fold(racc, fabsf(__fsub_rn(vs[j], cs[j])), R.fop);
+        float4 v;
+        v.x = __fmul_rn(0.25f, __fadd_rn(__fadd_rn(N.x, S.x), __fadd_rn(Wl, C.y)));
+        v.y = __fmul_rn(0.25f, __fadd_rn(__fadd_rn(N.y, S.y), __fadd_rn(C.x, C.z)));
+        v.z = __fmul_rn(0.25f, __fadd_rn(__fadd_rn(N.z, S.z), __fadd_rn(C.y, C.w)));
+        v.w = __fmul_rn(0.25f, __fadd_rn(__fadd_rn(N.w, S.w), __fadd_rn(C.z, Er)));
+        if (inside) {
+            if (full) {
+                __stcs(reinterpret_cast<float4*>(out), v);
+            } else {
+                __stcs(out, v.x);
+                __stcs(out + 1, v.y);
+                __stcs(out + 2, v.z);
+                __stcs(out + 3, v.w);
+            }
+            if (FOP) {
+                const float a = fold(fabsf(__fsub_rn(v.x, C.x)), fabsf(__fsub_rn(v.y, C.y)), FOP);
+                const float b = fold(fabsf(__fsub_rn(v.z, C.z)), fabsf(__fsub_rn(v.w, C.w)), FOP);
+                racc = fold(racc, fold(a, b, FOP), FOP);
+            }
         } else {
+            const float vs[4] = {v.x, v.y, v.z, v.w}, cs[4] = {C.x, C.y, C.z, C.w};
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 if (c + j >= 1 && c + j <= cols - 2) {
                     out[j] = vs[j];
-                    if (R.fop) racc = fold(racc, fabsf(__fsub_rn(vs[j], cs[j])), R.fop);
+                    if (FOP) racc = fold(racc, fabsf(__fsub_rn(vs[j], cs[j])), FOP);
                 }
             }
         }
     }
-    if (R.fop) {
-        const float b = block_fold(racc, R.fop);
-        if (threadIdx.x == 0) atomic_fold_minmax(R.fvar, b, R.fop);
+    return racc;
+}
+
+__device__ __forceinline__ void jacobi_tile(const BatchParams& P, const BatchRegion& R, int64_t t, float* halo,
+                                            bool staged, const BatchRegion* next, int64_t tn, float* halo_next) {
+    constexpr int HW = kHaloW;
+    // the region's fields, read once (the output stores could alias them)
+    const int64_t cols = R.cols, tiles_c = R.tiles_c, lb = R.lb, trip = R.trip;
+    float* const outb = R.out;
+    float* const fvar = R.fvar;
+    const int fop = R.fop;
+    const bool vec = jacobi_vec(R);
+    const int64_t band = t / tiles_c, tc = t - band * tiles_c;
+    const int64_t r0 = lb + band * P.jac_rows;
+    const int nr = (int)min((int64_t)P.jac_rows, lb + trip - r0);
+    const int64_t c0 = tc * kBatchJacCols;
+    if (!staged) jacobi_halo_async(P, R, t, halo);
+    if (next) {
+        jacobi_halo_async(P, *next, tn, halo_next);
+        asm volatile("cp.async.wait_group 1;" ::: "memory");
+    } else {
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
     }
-    __syncthreads();  // the halo buffer is reused by the next item
+    __syncthreads();
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5, nty = blockDim.x >> 5;
+    const int64_t c = c0 + 4 * tx;
+    const bool inside = c >= 1 && c + 3 <= cols - 2;  // all four points are updated
+    const bool full = vec && inside;
+    const float* cen = halo + (ty + 1) * HW + 4 + 4 * tx;
+    float* out = outb + (r0 + ty) * cols + c;
+    const int64_t ostep = (int64_t)nty * cols;
+    if (fop == UPIR_RED_MAX) {
+        const float r = jacobi_rows<UPIR_RED_MAX>(cen, out, ty, nr, nty, ostep, inside, full, c, cols);
+        const float b = block_fold(r, UPIR_RED_MAX);
+        if (threadIdx.x == 0) atomic_fold_minmax(fvar, b, UPIR_RED_MAX);
+    } else if (fop == UPIR_RED_MIN) {
+        const float r = jacobi_rows<UPIR_RED_MIN>(cen, out, ty, nr, nty, ostep, inside, full, c, cols);
+        const float b = block_fold(r, UPIR_RED_MIN);
+        if (threadIdx.x == 0) atomic_fold_minmax(fvar, b, UPIR_RED_MIN);
+    } else {
+        jacobi_rows<0>(cen, out, ty, nr, nty, ostep, inside, full, c, cols);
+    }
+    __syncthreads();  // the halo buffer is reused by a later item
 }
 
 __device__ __forceinline__ void matvec_tile(const BatchParams& P, const BatchRegion& R, int64_t t) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    // the region's fields, read once (the stores to y could alias them)
+    const float* const A = R.in0;
+    const float* const x = R.in1;
+    float* const y = R.out;
+    const int64_t cols = R.cols;
     const int64_t r0 = R.lb + t * P.mv_rows;
     const int64_t r1 = min(r0 + (int64_t)P.mv_rows, R.lb + R.trip);
     for (int64_t r = r0 + warp; r < r1; r += nw) {
-        const float v = row_dot(R.in0 + r * R.cols, R.in1, R.cols, lane);
-        if (lane == 0) R.out[r] = v;
+        const float v = row_dot(A + r * cols, x, cols, lane);
+        if (lane == 0) y[r] = v;
     }
 }
 
 __global__ void __launch_bounds__(kBatchUnits, 4) batch_persistent_kernel(const BatchParams P) {
-    __shared__ __align__(16) float halo[(kBatchMaxJacRows + 2) * (kBatchJacCols + 8)];
-    __shared__ int64_t item, next_item;
+    // two halo buffers: the current Jacobi tile's and the next one's, whose
+    // asynchronous copy runs while the current item is processed
+    __shared__ __align__(16) float halo[2][kHaloFloats];
+    __shared__ int64_t cur_item, next_item, after_next;
     __shared__ int last_team;
     griddep_wait();
-    if (threadIdx.x == 0) item = (int64_t)atomicAdd(P.counter, 1ull);
+    if (threadIdx.x == 0) {
+        cur_item = (int64_t)atomicAdd(P.counter, 1ull);
+        next_item = (int64_t)atomicAdd(P.counter, 1ull);
+    }
     __syncthreads();
+    int hb = 0;           // halo buffer of the current item
+    bool staged = false;  // its halo copy was issued during the previous item
     for (;;) {
-        const int64_t k = item;
+        const int64_t k = cur_item, kn = next_item;
         if (k >= P.nitems) break;
-        // claim the following item now, so the atomic's latency overlaps this one
-        if (threadIdx.x == 0) next_item = (int64_t)atomicAdd(P.counter, 1ull);
+        // claim the item after next now, so the atomic's latency overlaps this one
+        if (threadIdx.x == 0) after_next = (int64_t)atomicAdd(P.counter, 1ull);
         const int2 it = P.items[k];
         const BatchRegion& R = P.regions[it.x];
-        switch (R.op) {
-            case BOP_AXPY: axpy_tile(P, R, it.y); break;
-            case BOP_JACOBI: jacobi_tile(P, R, it.y, halo); break;
-            default: matvec_tile(P, R, it.y); break;
+        // a following Jacobi tile gets its halo copied while this item runs
+        const BatchRegion* nreg = nullptr;
+        int64_t tn = 0;
+        if (kn < P.nitems) {
+            const int2 itn = P.items[kn];
+            const BatchRegion* q = &P.regions[itn.x];
+            if (q->op == BOP_JACOBI) nreg = q, tn = itn.y;
         }
-        __syncthreads();  // every thread has read `item`
-        if (threadIdx.x == 0) item = next_item;
+        switch (R.op) {
+            case BOP_AXPY:
+                if (nreg) jacobi_halo_async(P, *nreg, tn, halo[hb ^ 1]);
+                axpy_tile(P, R, it.y);
+                break;
+            case BOP_JACOBI: jacobi_tile(P, R, it.y, halo[hb], staged, nreg, tn, halo[hb ^ 1]); break;
+            default:
+                if (nreg) jacobi_halo_async(P, *nreg, tn, halo[hb ^ 1]);
+                matvec_tile(P, R, it.y);
+                break;
+        }
+        if (nreg) hb ^= 1;
+        staged = nreg != nullptr;
+        __syncthreads();  // every thread has read the item slots
+        if (threadIdx.x == 0) {
+            cur_item = next_item;
+            next_item = after_next;
+        }
         __syncthreads();
     }
+    // no copy may still be landing in shared memory when the team exits
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
     // the last team returns the work counter to zero for the next launch
     if (threadIdx.x == 0) {
         __threadfence();
