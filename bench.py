@@ -120,6 +120,7 @@ class Runtime:
         torch.cuda.set_stream(self.stream)
         self.ctx = U.upir_init(device, self.stream.cuda_stream)
         self.flush_buf = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+        self.flush_rd = torch.zeros(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
         self.host = []
         self.handles = []
 
@@ -131,11 +132,15 @@ class Runtime:
         return h
 
     def flush_l2(self):
-        # Stream-ordered and not waited for: the GPU is still busy with the
-        # fill while the host enqueues the timed work, so the timed region
-        # starts with the GPU's own start of that work, not with the host's
-        # launch latency after an idle gap.
+        # Write a buffer larger than L2, then read another one: the read
+        # evicts the written lines (their write-back happens inside it), so
+        # the timed work starts with an L2 that holds neither its inputs nor
+        # dirty lines whose write-back it would pay for.  Stream-ordered and
+        # not waited for: the GPU is still busy with the flush while the host
+        # enqueues the timed work, so the timed region starts with the GPU's
+        # own start of that work, not with the host's launch latency.
         self.flush_buf.fill_(1.0)
+        self.flush_rd.sum()
 
     def region(self, loops, teams=0, units=0):
         r = self.U.upir_spmd_region(self.ctx, teams, units)
@@ -281,8 +286,12 @@ def extra_axpy(rt: Runtime, n: int, pk: dict) -> dict:
     r = rt.region([dict(lb=0, ub=n, body=U.UPIR_BODY_AXPY, bufs=[hx, hy], scalars=[2.5, 3, 1000],
                         reductions=[(U.UPIR_RED_ADD, U.UPIR_F32, U.UPIR_TERM_Y, hf, 0),
                                     (U.UPIR_RED_ADD, U.UPIR_I64, U.UPIR_TERM_IMOD, hi, 0)])])
-    ms, _, _ = rt.timed_submits(lambda: U.upir_region_submit(r, 0), 20)
-    gms, _, _ = rt.timed_submits(lambda: U.upir_region_submit(r, U.UPIR_SUBMIT_GRAPH), 20)
+    # CUDA event timestamps on this GPU step in 2.048 us, so a region of a few
+    # microseconds reads as a multiple of that: the mean over the repetitions
+    # (each phase-shifted against the timer) is the estimate, not the median.
+    _, per, _ = rt.timed_submits(lambda: U.upir_region_submit(r, 0), 60)
+    _, gper, _ = rt.timed_submits(lambda: U.upir_region_submit(r, U.UPIR_SUBMIT_GRAPH), 60)
+    ms, gms = statistics.fmean(per), statistics.fmean(gper)
     U.upir_region_destroy(r)
     for h in (hx, hy, hf, hi):
         U.upir_data_unmap(rt.ctx, h)
@@ -632,7 +641,7 @@ def run_ours(args) -> None:
             "config": {"workload": "jacobi5_4096x4096_100sweeps_maxresidual",
                        "grid": [N_GRID, N_GRID], "sweeps": SWEEPS, "schedule": "static",
                        "parallelism": f"independent problem per rank x{world}",
-                       "l2": "flushed before each step (256 MiB write); working set 134 MB > 126 MB L2",
+                       "l2": "flushed before each step (256 MiB write, then 256 MiB read); working set 134 MB > 126 MB L2",
                        "submission": "CUDA graph of the 100 sweep launches (programmatic dependent launch)"},
             "roofline": h["roofline"], "clocks": h["clocks"], "gpu_launches": h["gpu_launches"],
             "e2e": h["e2e"], "cpu_baseline": cpu,

@@ -108,18 +108,34 @@ __device__ __forceinline__ Partial identity_partial(int fop, int iop) {
     return make_partial(facc_identity(fop), iacc_identity(iop));
 }
 
-__device__ __forceinline__ Partial shfl_xor_partial(const Partial& p, int m) {
+__device__ __forceinline__ Partial shfl_xor_partial(const Partial& p, int m, unsigned mask) {
     Partial q;
-    q.s = __shfl_xor_sync(0xffffffffu, p.s, m);
-    q.c = __shfl_xor_sync(0xffffffffu, p.c, m);
-    q.i = __shfl_xor_sync(0xffffffffu, p.i, m);
+    q.s = __shfl_xor_sync(mask, p.s, m);
+    q.c = __shfl_xor_sync(mask, p.c, m);
+    q.i = __shfl_xor_sync(mask, p.i, m);
     return q;
 }
 
-// Butterfly over the 32 lanes: every lane ends with the same combined value.
+// Lanes of the calling thread's warp that exist: 32 except in the last warp
+// of a block whose size is not a multiple of 32.
+__device__ __forceinline__ int warp_lanes() {
+    const int rest = (int)blockDim.x - (int)(threadIdx.x & ~31u);
+    return rest < 32 ? rest : 32;
+}
+
+__device__ __forceinline__ unsigned lanes_mask(int n) { return n >= 32 ? 0xffffffffu : (1u << n) - 1u; }
+
+// Butterfly over the warp's lanes: every lane ends with the same combined
+// value.  In a partial warp the missing partners contribute the identity.
 __device__ __forceinline__ Partial warp_reduce_partial(Partial p, int fop, int iop) {
+    const int n = warp_lanes(), lane = threadIdx.x & 31;
+    const unsigned mask = lanes_mask(n);
 #pragma unroll
-    for (int m = 16; m >= 1; m >>= 1) p = combine_partial(p, shfl_xor_partial(p, m), fop, iop);
+    for (int m = 16; m >= 1; m >>= 1) {
+        Partial q = shfl_xor_partial(p, m, mask);
+        if ((lane ^ m) >= n) q = identity_partial(fop, iop);
+        p = combine_partial(p, q, fop, iop);
+    }
     return p;
 }
 
@@ -155,12 +171,59 @@ __device__ __forceinline__ Partial load_partial_cg(const Partial* src) {
 
 // Reduce slots [0, n) in a fixed order: thread t folds t, t + B, t + 2B, ...
 // sequentially, then the block tree.  Every thread of the block must call it.
+// Fold slots v, v + stride, v + 2 stride, ... below n into the identity in
+// that order; the loads are issued four at a time so that one L2 round trip
+// covers four slots.
+__device__ __forceinline__ Partial fold_strided_slots(const Partial* slots, int64_t n, int64_t v,
+                                                      int64_t stride, int fop, int iop) {
+    Partial acc = identity_partial(fop, iop);
+    int64_t k = v;
+    for (; k + 3 * stride < n; k += 4 * stride) {
+        const Partial a0 = load_partial_cg(slots + k), a1 = load_partial_cg(slots + k + stride);
+        const Partial a2 = load_partial_cg(slots + k + 2 * stride), a3 = load_partial_cg(slots + k + 3 * stride);
+        acc = combine_partial(acc, a0, fop, iop);
+        acc = combine_partial(acc, a1, fop, iop);
+        acc = combine_partial(acc, a2, fop, iop);
+        acc = combine_partial(acc, a3, fop, iop);
+    }
+    for (; k < n; k += stride) acc = combine_partial(acc, load_partial_cg(slots + k), fop, iop);
+    return acc;
+}
+
 __device__ __forceinline__ Partial block_reduce_slots(const Partial* slots, int64_t n,
                                                       int fop, int iop) {
-    Partial acc = identity_partial(fop, iop);
-    for (int64_t k = threadIdx.x; k < n; k += blockDim.x)
-        acc = combine_partial(acc, load_partial_cg(slots + k), fop, iop);
+    const Partial acc = fold_strided_slots(slots, n, threadIdx.x, blockDim.x, fop, iop);
     return block_reduce_partial(acc, fop, iop);
+}
+
+// The same fold as block_reduce_slots run by a block of 256 threads, computed
+// by a block of any size that is a multiple of 32: 256 virtual threads fold
+// their strided slots into shared memory, then the eight virtual warps and the
+// final warp take the same butterflies.  A loop's last team finishes the
+// reduction with it, giving the value the separate finalize kernel would.
+// Every thread of the block must call it, and the block size must be a
+// multiple of 32.
+__device__ __forceinline__ Partial block_reduce_slots_v256(const Partial* slots, int64_t n,
+                                                           int fop, int iop) {
+    __shared__ Partial vpart[256];
+    __shared__ Partial vwarp[8];
+    __shared__ Partial vresult;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwarps = (int)(blockDim.x >> 5);  // >= 1: the block size is a multiple of 32
+    for (int v = threadIdx.x; v < 256; v += blockDim.x) vpart[v] = fold_strided_slots(slots, n, v, 256, fop, iop);
+    __syncthreads();
+    for (int vw = warp; vw < 8; vw += nwarps) {
+        const Partial q = warp_reduce_partial(vpart[vw * 32 + lane], fop, iop);
+        if (lane == 0) vwarp[vw] = q;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        Partial q = lane < 8 ? vwarp[lane] : identity_partial(fop, iop);
+        q = warp_reduce_partial(q, fop, iop);
+        if (lane == 0) vresult = q;
+    }
+    __syncthreads();
+    return vresult;
 }
 
 // Combine the reduction variables' values before the loop with the final
@@ -198,19 +261,28 @@ __device__ __forceinline__ float fold(float a, float b, int op) {
     return op == UPIR_RED_MIN ? fminf(a, b) : fmaxf(a, b);
 }
 
+// max / min over the warp's lanes; in a partial warp a missing partner
+// stands in with the lane's own value (the fold is idempotent).
+__device__ __forceinline__ float warp_fold(float v, int op) {
+    const int n = warp_lanes(), lane = threadIdx.x & 31;
+    const unsigned mask = lanes_mask(n);
+#pragma unroll
+    for (int m = 16; m >= 1; m >>= 1) {
+        const float q = __shfl_xor_sync(mask, v, m);
+        v = fold(v, (lane ^ m) < n ? q : v, op);
+    }
+    return v;
+}
+
 __device__ __forceinline__ float block_fold(float v, int op) {
     __shared__ float part[32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-    for (int m = 16; m >= 1; m >>= 1) v = fold(v, __shfl_xor_sync(0xffffffffu, v, m), op);
+    v = warp_fold(v, op);
     if (lane == 0) part[warp] = v;
     __syncthreads();
     if (warp == 0) {
         const int nw = (blockDim.x + 31) >> 5;
-        float q = lane < nw ? part[lane] : v;
-#pragma unroll
-        for (int m = 16; m >= 1; m >>= 1) q = fold(q, __shfl_xor_sync(0xffffffffu, q, m), op);
-        v = q;
+        v = warp_fold(lane < nw ? part[lane] : v, op);
     }
     return v;  // valid in thread 0
 }

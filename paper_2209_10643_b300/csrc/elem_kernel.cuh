@@ -7,7 +7,8 @@
 // two reduction operators (FOP for the FP32 clause, IOP for the int64 one; 0
 // when the loop has none), so the per-iteration accumulation compiles to
 // straight-line code.  Each team leaves one partial per team (static) or per
-// chunk (dynamic) in scratch; finalize_kernel folds them afterwards.
+// chunk (dynamic) in scratch; the last team to finish folds them when they
+// fit one fold, finalize_kernel afterwards otherwise.
 #pragma once
 
 #include "device_common.cuh"
@@ -140,6 +141,36 @@ __device__ __forceinline__ void body_range(const ElemParams& p, Terms& t, int64_
     }
 }
 
+// The closing barrier of a loop whose partials fit one fold (§3.1.2): every
+// team takes a ticket once its partials are written; the team holding the
+// last one folds them (block_reduce_slots_v256, so the value equals the
+// separate finalize kernel's), stores the reduction variables and returns the
+// ticket and the dynamic chunk counter to zero.  Saves a launch per loop.
+template <bool DYN, int FOP, int IOP>
+__device__ __forceinline__ void elem_finish(const ElemParams& p) {
+    constexpr bool HR = FOP != 0 || IOP != 0;
+    __shared__ int last;
+    // the team's partial slots, written by any of its threads, are ordered
+    // before the ticket by the barrier and thread 0's device-scope fence
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(p.sc.ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    if (HR) {
+        const int64_t nslots = DYN ? p.nchunks : (int64_t)gridDim.x;
+        const Partial fin = block_reduce_slots_v256(p.sc.partials, nslots, FOP, IOP);
+        if (threadIdx.x == 0) write_reduction_vars(p.rv, fin);
+    }
+    if (threadIdx.x == 0) {
+        *p.sc.ticket = 0;
+        if (DYN) *p.sc.chunk_counter = 0;
+    }
+}
+
 template <int BODY, bool DYN, int FOP, int IOP>
 __global__ void __launch_bounds__(1024, 1) elem_kernel(const ElemParams p) {
     constexpr bool HR = FOP != 0 || IOP != 0;
@@ -165,6 +196,7 @@ __global__ void __launch_bounds__(1024, 1) elem_kernel(const ElemParams p) {
             if (HR) p.sc.partials[k] = make_partial(t.f, t.i);
         }
     }
+    if (p.fuse_fin) elem_finish<DYN, FOP, IOP>(p);
 }
 
 template <int BODY, bool DYN, int FOP>

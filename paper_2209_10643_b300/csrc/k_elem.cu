@@ -89,10 +89,16 @@ cudaError_t launch_elem_main(int body, bool dyn, int fop, int iop, int teams, in
 
 cudaError_t launch_elem(int body, bool dyn, int fop, int iop, int teams, int units,
                         const ElemParams& p, cudaStream_t s) {
+    const bool red = fop || iop;
+    const int64_t nslots = dyn ? p.nchunks : teams;
+    if ((red || dyn) && (!red || (nslots <= kFinSeg && units % 32 == 0))) {
+        ElemParams q = p;  // the loop kernel's last team finishes the loop
+        q.fuse_fin = 1;
+        return launch_elem_main(body, dyn, fop, iop, teams, units, q, s);
+    }
     cudaError_t e = launch_elem_main(body, dyn, fop, iop, teams, units, p, s);
     if (e != cudaSuccess) return e;
-    if (fop || iop) return launch_finalize(p.rv, p.sc, dyn ? p.nchunks : teams, dyn, s);
-    if (dyn) return launch_finalize(p.rv, p.sc, 0, true, s);
+    if (red) return launch_finalize(p.rv, p.sc, nslots, dyn, s);
     return cudaSuccess;
 }
 

@@ -71,6 +71,7 @@ struct ElemParams {
     unsigned long long imod_minv;            // floor(2^64 / m) for Barrett reduction (m >= 2)
     SchedConst sk;
     int wait_prior;                          // wait for the previous kernel (implicit barrier)
+    int fuse_fin;                            // the last team finishes the reductions (few partials)
     RedVars rv;
     Scratch sc;
 };

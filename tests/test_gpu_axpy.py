@@ -85,6 +85,48 @@ def test_axpy_schedules_reach_the_same_result(s, teams, units, sched, chunk):
     assert isum == O.imod_sum_closed_form(n, 3, 1000)
 
 
+# Partials of up to 2048 teams (static) or chunks (dynamic) are folded by the
+# loop's last team; more take the separate finalize kernel.  Both sides of the
+# boundary reach the oracle's result.
+@pytest.mark.parametrize("n,teams,units,sched,chunk", [
+    (300_001, 2048, 32, 0, 0), (300_001, 2049, 32, 0, 0), (300_001, 5000, 32, 0, 0),
+    (299_008, 0, 0, 1, 146), (299_009, 0, 0, 1, 146), (1 << 20, 0, 0, 1, 1),
+])
+def test_axpy_reduction_fold_sizes(s, n, teams, units, sched, chunk):
+    x, y0, y, fs, isum = run_axpy(s, n, [(U.UPIR_F32, U.UPIR_RED_ADD, U.UPIR_TERM_Y),
+                                         (U.UPIR_I64, U.UPIR_RED_ADD, U.UPIR_TERM_IMOD)],
+                                  teams=teams, units=units, sched=sched, chunk=chunk)
+    want = O.axpy(2.5, x, y0)
+    assert np.array_equal(y, want)
+    ref = O.reduce_f64(O.RED_ADD, 0.0, want)
+    assert abs(fs - ref) <= 2 * np.spacing(np.float32(abs(ref)))
+    assert isum == O.imod_sum_closed_form(n, 3, 1000)
+
+
+@pytest.mark.parametrize("sched,chunk,flags", [(0, 0, 0), (1, 97, 0), (0, 0, 1), (1, 97, 1)])
+def test_resubmitted_region_folds_every_time(s, sched, chunk, flags):
+    """The same recorded loop submitted four times (directly or as a CUDA
+    graph): each submission folds its partials once into the variables."""
+    n = 100_003
+    x, y = I.axpy_inputs(n, seed=4)
+    fvar = np.zeros(1, np.float32)
+    ivar = np.zeros(1, np.int64)
+    hx, hy = s.map(x, U.UPIR_MAP_TO), s.map(y.copy(), U.UPIR_MAP_TOFROM)
+    hf, hi = s.map(fvar, U.UPIR_MAP_TOFROM), s.map(ivar, U.UPIR_MAP_TOFROM)
+    r = U.upir_spmd_region(s.ctx, 0, 0)
+    U.upir_loop_checked(s.ctx, r, U.make_loop_desc(**axpy_loop(
+        hx, hy, n, a=0.0, sched=sched, chunk=chunk,
+        reds=[(U.UPIR_RED_MAX, U.UPIR_F32, U.UPIR_TERM_Y, hf, 0), (U.UPIR_RED_ADD, U.UPIR_I64, U.UPIR_TERM_IMOD, hi, 0)])))
+    for _ in range(4):
+        U.upir_region_submit(r, U.UPIR_SUBMIT_GRAPH if flags else 0)
+    U.upir_ctx_wait(s.ctx)
+    U.upir_region_destroy(r)
+    for h in (hx, hy, hf, hi):
+        s.unmap(h)
+    assert int(ivar[0]) == 4 * O.imod_sum_closed_form(n, 3, 1000)
+    assert float(fvar[0]) == float(y.max())
+
+
 @pytest.mark.parametrize("sched,chunk", [(0, 0), (1, 3)])
 def test_axpy_reductions_are_bitwise_repeatable(s, sched, chunk):
     outs = set()
@@ -103,6 +145,24 @@ def test_axpy_float_ops_combine_initial_value(s, op, init):
     want = O.axpy(2.5, x, y0)
     ref = O.reduce_f64(op, init, want)
     assert abs(fs - ref) <= REL_F32 * abs(ref)
+
+
+# Teams whose size is not a multiple of the 32-lane warp: the missing lanes
+# of the last warp take no part in the team's reduction tree.
+@pytest.mark.parametrize("op", [U.UPIR_RED_MAX, U.UPIR_RED_MIN, U.UPIR_RED_ADD])
+@pytest.mark.parametrize("teams,units", [(3, 45), (1, 1), (2, 17), (5, 1000)])
+def test_axpy_partial_warp_teams(s, op, teams, units):
+    x, y0, y, fs, isum = run_axpy(s, 20_011, [(U.UPIR_F32, op, U.UPIR_TERM_Y),
+                                              (U.UPIR_I64, U.UPIR_RED_MAX, U.UPIR_TERM_IMOD)],
+                                  teams=teams, units=units, finit=0.0, iinit=-1)
+    want = O.axpy(2.5, x, y0)
+    assert np.array_equal(y, want)
+    ref = O.reduce_f64(op, 0.0, want)
+    if op == U.UPIR_RED_ADD:
+        assert abs(fs - ref) <= 2 * np.spacing(np.float32(abs(ref)))
+    else:
+        assert fs == ref  # max / min are exact
+    assert isum == 999
 
 
 def test_mul_reduction_short_loop(s):

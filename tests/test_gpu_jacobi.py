@@ -74,7 +74,8 @@ def test_field_and_residuals_bit_exact_vs_fp32_mirror(s, rows, cols, sweeps, hin
 
 
 @pytest.mark.parametrize("teams,units,sched,chunk", [(5, 256, 0, 0), (3, 64, 0, 2), (7, 128, 1, 1),
-                                                     (0, 0, 1, 3), (1, 32, 0, 0)])
+                                                     (0, 0, 1, 3), (1, 32, 0, 0),
+                                                     (4, 100, 0, 0), (2, 20, 0, 0), (3, 1, 1, 1)])
 def test_schedules_over_tiles(s, teams, units, sched, chunk):
     u0 = I.jacobi_grid(150, 332, seed=4)
     u, res = run_sweeps(s, u0, 3, teams=teams, units=units, sched=sched, chunk=chunk)
