@@ -293,7 +293,7 @@ typedef enum {
     UPIR_HINT_VARIANT   = 1, /* kernel variant of the body (body-specific, 0 = default)       */
     UPIR_HINT_TILE_M    = 2, /* tile rows (JACOBI5 tiled variant, GEMM)                       */
     UPIR_HINT_TILE_N    = 3, /* tile cols                                                     */
-    UPIR_HINT_VEC       = 4, /* iterations per worker the planner aims for (1, 4, 8 or 16)    */
+    UPIR_HINT_VEC       = 4, /* iterations per worker the planner aims for (1, 4, 8, 16, 32) */
     UPIR_HINT_STAGES    = 5, /* shared-memory pipeline depth of the tiled JACOBI5 (1..4)      */
     UPIR_HINT_GRAINSIZE = 6, /* taskloop grainsize (>= 1; schedule TASKLOOP only)             */
     UPIR_HINT_NUM_TASKS = 7  /* taskloop num_tasks (>= 1; schedule TASKLOOP only)             */

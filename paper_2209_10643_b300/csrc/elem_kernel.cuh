@@ -73,6 +73,73 @@ __device__ __forceinline__ void axpy_one(const ElemParams& p, Terms& t, int64_t 
     add_int_term<IOP>(p, t, iv);
 }
 
+// The AXPY iterations [i, iend) of one worker, 32-byte aligned x + i and
+// y + i, in groups of eight with 256-bit accesses; leaves i at the first
+// iteration not done (fewer than eight remain).  PAIR: reduction(+) over y
+// with two compensated accumulators, one per lane of paired FP32
+// instructions (even and odd iterations), merged into t at the end.  IMOD32:
+// reduction(+) over (mul * iv) mod m with m < 2^28, the eight terms of a
+// group summed in 32 bits before the 64-bit accumulation.
+template <int FOP, int IOP, bool PAIR, bool IMOD32>
+__device__ __forceinline__ void axpy_v8(const ElemParams& p, Terms& t, int64_t& i, int64_t iend) {
+    F2 S = f2(0.0f, 0.0f), C = f2(0.0f, 0.0f);
+    uint32_t tm = (uint32_t)t.imod;
+    const uint32_t inc = (uint32_t)p.imod_inc, m = (uint32_t)p.imod_mod;
+    auto group = [&](const float* xv, float* yv, int64_t i0) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) yv[j] = __fmaf_rn(p.a, xv[j], yv[j]);
+        st_v8_cs_f(p.y + i0, yv);
+        if (PAIR) {
+#pragma unroll
+            for (int j = 0; j < 8; j += 2) {
+                F2 s2, e2;
+                two_sum2(S, f2(yv[j], yv[j + 1]), s2, e2);
+                S = s2;
+                C = f2_add(C, e2);
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) add_axpy_term<FOP>(p, t, xv[j], yv[j]);
+        }
+        if (IMOD32) {
+            uint32_t g = 0;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                g += tm;
+                tm += inc;
+                tm = min(tm, tm - m);  // tm - m wraps above tm when tm < m
+            }
+            t.i = (long long)((unsigned long long)t.i + g);
+        } else {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) add_int_term<IOP>(p, t, i0 + j);
+        }
+    };
+    for (; i + 16 <= iend; i += 16) {
+        float x0[8], y0[8], x1[8], y1[8];
+        ld_v8_cs(p.x + i, x0);
+        ld_v8_cs(p.y + i, y0);
+        ld_v8_cs(p.x + i + 8, x1);
+        ld_v8_cs(p.y + i + 8, y1);
+        group(x0, y0, i);
+        group(x1, y1, i + 8);
+    }
+    if (i + 8 <= iend) {
+        float x0[8], y0[8];
+        ld_v8_cs(p.x + i, x0);
+        ld_v8_cs(p.y + i, y0);
+        group(x0, y0, i);
+        i += 8;
+    }
+    if (IMOD32) t.imod = tm;
+    if (PAIR) {
+        float s0, s1, c0, c1;
+        f2_split(S, s0, s1);
+        f2_split(C, c0, c1);
+        t.f = facc_combine(facc_combine(t.f, FAcc{s0, c0}, UPIR_RED_ADD), FAcc{s1, c1}, UPIR_RED_ADD);
+    }
+}
+
 template <int FOP, int IOP>
 __device__ __forceinline__ void axpy_range(const ElemParams& p, Terms& t, int64_t k0, int64_t k1) {
     if (p.step != 1) {
@@ -81,9 +148,21 @@ __device__ __forceinline__ void axpy_range(const ElemParams& p, Terms& t, int64_
     }
     int64_t i = p.lb + k0;
     const int64_t iend = p.lb + k1;
-    const bool same_phase =
-        ((reinterpret_cast<uintptr_t>(p.x + i) ^ reinterpret_cast<uintptr_t>(p.y + i)) & 15) == 0;
-    if (same_phase) {
+    const uintptr_t phase = reinterpret_cast<uintptr_t>(p.x + i) ^ reinterpret_cast<uintptr_t>(p.y + i);
+    // loops without reductions keep the 128-bit path (one access per worker
+    // by default, and fewer registers)
+    constexpr bool kV8 = FOP != 0 || IOP != 0;
+    if (kV8 && (phase & 31) == 0 && iend - i >= 8) {
+        while (i < iend && (reinterpret_cast<uintptr_t>(p.x + i) & 31)) axpy_one<FOP, IOP>(p, t, i++);
+        constexpr bool kPairOk = FOP == UPIR_RED_ADD;
+        constexpr bool kImodOk = IOP == UPIR_RED_ADD;
+        const bool pair = kPairOk && p.rv.fterm == UPIR_TERM_Y;
+        const bool im32 = kImodOk && p.rv.iterm == UPIR_TERM_IMOD && p.imod32;
+        if (pair && im32) axpy_v8<FOP, IOP, kPairOk, kImodOk>(p, t, i, iend);
+        else if (pair) axpy_v8<FOP, IOP, kPairOk, false>(p, t, i, iend);
+        else if (im32) axpy_v8<FOP, IOP, false, kImodOk>(p, t, i, iend);
+        else axpy_v8<FOP, IOP, false, false>(p, t, i, iend);
+    } else if ((phase & 15) == 0) {
         while (i < iend && (reinterpret_cast<uintptr_t>(p.x + i) & 15)) axpy_one<FOP, IOP>(p, t, i++);
 #pragma unroll 2
         for (; i + 4 <= iend; i += 4) {

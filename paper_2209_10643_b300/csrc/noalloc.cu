@@ -87,6 +87,7 @@ extern "C" upir_status upir_axpy_reduce_noalloc(const float* x, float* y, int64_
     const __int128 inc = (__int128)imod_mul % imod_mod;
     p.imod_inc = (long long)(inc < 0 ? inc + imod_mod : inc);
     p.imod_minv = imod_mod >= 2 ? (unsigned long long)(((unsigned __int128)1 << 64) / (unsigned long long)imod_mod) : 0;
+    p.imod32 = imod_mod < (1ll << 28) ? 1 : 0;
     p.sk = make_sched_const(n, 0, teams * kNoAllocUnits);
     p.wait_prior = 1;
     p.rv = RedVars{sum_y, reinterpret_cast<long long*>(imod_sum), UPIR_RED_ADD, UPIR_RED_ADD,

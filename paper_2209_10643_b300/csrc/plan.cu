@@ -216,7 +216,7 @@ upir_status plan_loop(upir_region r, const upir_loop_desc* d, LoopRec& lp) {
         if (k == UPIR_HINT_VARIANT) ok(v >= 0 && v <= 3, UPIR_EINVAL, "variant hint out of range"), lp.variant = (int)v;
         else if (k == UPIR_HINT_TILE_M) ok(v >= 1 && v <= 254, UPIR_EINVAL, "tile_m hint out of range"), lp.tile_m = (int)v;
         else if (k == UPIR_HINT_TILE_N) ok(v >= 4 && v <= 248 && v % 4 == 0, UPIR_EINVAL, "tile_n hint must be a multiple of 4 in [4, 248]"), lp.tile_n = (int)v;
-        else if (k == UPIR_HINT_VEC) ok(v == 1 || v == 4 || v == 8 || v == 16, UPIR_EINVAL, "vec hint must be 1, 4, 8 or 16"), lp.vec = (int)v;
+        else if (k == UPIR_HINT_VEC) ok(v == 1 || v == 4 || v == 8 || v == 16 || v == 32, UPIR_EINVAL, "vec hint must be 1, 4, 8, 16 or 32"), lp.vec = (int)v;
         else if (k == UPIR_HINT_STAGES) ok(v >= 1 && v <= 4, UPIR_EINVAL, "stages hint must be in [1, 4]"), lp.stages = (int)v;
         else if (k == UPIR_HINT_GRAINSIZE) ok(v >= 1, UPIR_EINVAL, "grainsize hint must be >= 1"), lp.grainsize = v;
         else if (k == UPIR_HINT_NUM_TASKS) ok(v >= 1, UPIR_EINVAL, "num_tasks hint must be >= 1"), lp.num_tasks = v;
@@ -754,11 +754,17 @@ upir_status plan_loop(upir_region r, const upir_loop_desc* d, LoopRec& lp) {
     ep.imod_mod = imod_mod;
     ep.imod_inc = imod_inc;
     ep.imod_minv = imod_mod >= 2 ? (unsigned long long)(((unsigned __int128)1 << 64) / (unsigned long long)imod_mod) : 0;
+    ep.imod32 = imod_mod < (1ll << 28) ? 1 : 0;
     const int64_t trip = lp.trip;
-    // iterations per worker the blocked schedule aims for: 4 (one 128-bit access)
-    // without reductions, 8 with them (halves the per-element share of the
-    // warp-level reduction tree at the same coalescing)
-    const int64_t vdef = has_red ? 8 : 4;
+    // iterations per worker the blocked schedule aims for.  Without
+    // reductions: 4 (one 128-bit access), 8 once every SM's thread slots stay
+    // busy at 8 per worker.  With reductions: 8 (one 256-bit access), 16 once
+    // the slots stay busy at 16 (the reduction tree and the range set-up
+    // amortised over twice the iterations).  Longer ranges spread a warp's
+    // accesses over more DRAM pages: measured on 2^28 iterations, 32 per
+    // worker ran 30 % slower than 16.
+    const int64_t slots = (int64_t)kNumSMs * 2048;
+    const int64_t vdef = !has_red ? (trip >= 8 * slots ? 8 : 4) : (trip >= 16 * slots ? 16 : 8);
     // reducing element loops run better in smaller teams (more, shorter-lived
     // blocks overlap their block-level reduction trees with other blocks' loads)
     if (!U0 && !auto_units && has_red && lp.body == UPIR_BODY_AXPY) lp.units = 128;

@@ -69,6 +69,7 @@ struct ElemParams {
     int64_t rows, cols;
     long long imod_mul, imod_mod, imod_inc;  // imod_inc = (mul * step) mod m, in [0, m)
     unsigned long long imod_minv;            // floor(2^64 / m) for Barrett reduction (m >= 2)
+    int imod32;                              // m < 2^28: eight terms sum in 32 bits
     SchedConst sk;
     int wait_prior;                          // wait for the previous kernel (implicit barrier)
     int fuse_fin;                            // the last team finishes the reductions (few partials)

@@ -22,7 +22,7 @@ def s():
 
 
 def run_axpy(s, n, reds_spec, teams=0, units=0, sched=0, chunk=0, a=2.5, seed=0,
-             finit=0.0, iinit=0, lb=0, ub=None, step=1, hints=()):
+             finit=0.0, iinit=0, lb=0, ub=None, step=1, hints=(), imod=(3, 1000)):
     x, y = I.axpy_inputs(n, seed=seed)
     y0 = y.copy()
     fvar = np.array([finit], np.float32)
@@ -33,7 +33,7 @@ def run_axpy(s, n, reds_spec, teams=0, units=0, sched=0, chunk=0, a=2.5, seed=0,
     for kind, op, term in reds_spec:
         reds.append((op, kind, term, hf if kind == U.UPIR_F32 else hi, 0))
     s.run([axpy_loop(hx, hy, n, a=a, reds=reds, sched=sched, chunk=chunk, lb=lb, ub=ub, step=step,
-                     hints=hints)], teams, units)
+                     hints=hints, imod=imod)], teams, units)
     for h in (hx, hy, hf, hi):
         s.unmap(h)
     return x, y0, y, float(fvar[0]), int(ivar[0])
@@ -83,6 +83,43 @@ def test_axpy_schedules_reach_the_same_result(s, teams, units, sched, chunk):
     ref = O.reduce_f64(O.RED_ADD, 0.0, x.astype(np.float64) * want.astype(np.float64))
     assert abs(fs - ref) <= REL_F32 * abs(ref)
     assert isum == O.imod_sum_closed_form(n, 3, 1000)
+
+
+# Unit-step ranges whose x and y share a 32-byte phase run in groups of eight
+# iterations with 256-bit accesses after a scalar prologue up to the boundary;
+# (+, y) pairs even and odd iterations in paired FP32 accumulators and
+# (+, mul*iv mod m) sums groups in 32 bits when m < 2^28.  Ranges of every
+# alignment and length, with each accumulation variant.
+@pytest.mark.parametrize("lb,n,teams,units,vec", [
+    (5, 100_003, 3, 32, 0), (3, 4099, 1, 32, 32), (0, 1 << 20, 0, 0, 32), (7, 300_001, 0, 0, 16),
+    (1, 1000, 2, 64, 8), (0, 64, 1, 1, 32), (6, 23, 1, 1, 32), (0, 1 << 22, 0, 0, 0),
+])
+@pytest.mark.parametrize("fterm,mod", [(U.UPIR_TERM_Y, 1000), (U.UPIR_TERM_XY, 1000), (U.UPIR_TERM_Y, (1 << 30) + 3)])
+def test_axpy_256bit_groups(s, lb, n, teams, units, vec, fterm, mod):
+    hints = [(U.UPIR_HINT_VEC, vec)] if vec else []
+    x, y0, y, fs, isum = run_axpy(s, n, [(U.UPIR_F32, U.UPIR_RED_ADD, fterm),
+                                         (U.UPIR_I64, U.UPIR_RED_ADD, U.UPIR_TERM_IMOD)],
+                                  teams=teams, units=units, lb=lb, hints=hints, imod=(7, mod))
+    want, idx = expected_y(x, y0, 2.5, lb, n, 1)
+    assert np.array_equal(y.view(np.uint32), want.view(np.uint32))
+    terms = want[idx].astype(np.float64)
+    if fterm == U.UPIR_TERM_XY:
+        terms = terms * x[idx].astype(np.float64)
+    ref = O.reduce_f64(O.RED_ADD, 0.0, terms)
+    tol = 2 * np.spacing(np.float32(abs(ref))) if fterm == U.UPIR_TERM_Y else REL_F32 * abs(ref)
+    assert abs(fs - ref) <= tol
+    assert isum == sum(O.imod_terms(lb, 1, n - lb, 7, mod))
+
+
+@pytest.mark.parametrize("op", [U.UPIR_RED_MAX, U.UPIR_RED_MIN])
+def test_axpy_256bit_groups_min_max(s, op):
+    x, y0, y, fs, isum = run_axpy(s, 100_003, [(U.UPIR_F32, op, U.UPIR_TERM_Y),
+                                               (U.UPIR_I64, op, U.UPIR_TERM_IMOD)],
+                                  lb=3, hints=[(U.UPIR_HINT_VEC, 32)], iinit=500 if op == U.UPIR_RED_MIN else 0)
+    want, idx = expected_y(x, y0, 2.5, 3, 100_003, 1)
+    assert np.array_equal(y, want)
+    assert fs == O.reduce_f64(op, 0.0, want[idx])
+    assert isum == O.reduce_i64(op, 500 if op == U.UPIR_RED_MIN else 0, O.imod_terms(3, 1, 100_000, 3, 1000))
 
 
 # Partials of up to 2048 teams (static) or chunks (dynamic) are folded by the
