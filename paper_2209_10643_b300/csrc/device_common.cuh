@@ -54,6 +54,12 @@ __device__ __forceinline__ F2 f2_mul(F2 a, F2 b) {
     return r;
 }
 
+__device__ __forceinline__ F2 f2_fma(F2 a, F2 b, F2 c) {
+    F2 r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r.v) : "l"(a.v), "l"(b.v), "l"(c.v));
+    return r;
+}
+
 // TwoSum on both lanes of a pair.
 __device__ __forceinline__ void two_sum2(F2 a, F2 b, F2& s, F2& e) {
     s = f2_add(a, b);
@@ -78,6 +84,33 @@ __device__ __forceinline__ void st_v8_cs_f(float* p, const float* v) {
 struct FAcc {
     float s, c;
 };
+
+// Two compensated (+) accumulators advanced by paired instructions: lane 0
+// takes the even terms of a stream, lane 1 the odd ones.
+struct FAcc2 {
+    F2 s, c;
+};
+
+__device__ __forceinline__ FAcc2 facc2_zero() { return FAcc2{f2(0.0f, 0.0f), f2(0.0f, 0.0f)}; }
+
+// acc += v (both lanes), TwoSum error into the compensation.
+__device__ __forceinline__ void facc2_add(FAcc2& a, F2 v) {
+    F2 s, e;
+    two_sum2(a.s, v, s, e);
+    a.s = s;
+    a.c = f2_add(a.c, e);
+}
+
+// acc += x * y (both lanes): TwoProduct by FMA, then TwoSum; both errors go
+// to the compensation.
+__device__ __forceinline__ void facc2_add_prod(FAcc2& a, F2 x, F2 y) {
+    const F2 p = f2_mul(x, y);
+    const F2 perr = f2_fma(x, y, f2_sub(f2(0.0f, 0.0f), p));
+    F2 s, e;
+    two_sum2(a.s, p, s, e);
+    a.s = s;
+    a.c = f2_add(a.c, f2_add(e, perr));
+}
 
 __device__ __forceinline__ FAcc facc_identity(int op) {
     switch (op) {
@@ -119,6 +152,15 @@ __device__ __forceinline__ FAcc facc_combine(FAcc a, FAcc b, int op) {
         case UPIR_RED_MIN: return {fminf(a.s, b.s), 0.0f};
         default: return a;
     }
+}
+
+// Fold both lanes of a paired accumulator into a (+) accumulator: lane 0,
+// then lane 1.
+__device__ __forceinline__ FAcc facc_merge2(FAcc a, const FAcc2& b) {
+    float s0, s1, c0, c1;
+    f2_split(b.s, s0, s1);
+    f2_split(b.c, c0, c1);
+    return facc_combine(facc_combine(a, FAcc{s0, c0}, UPIR_RED_ADD), FAcc{s1, c1}, UPIR_RED_ADD);
 }
 
 __device__ __forceinline__ long long iacc_identity(int op) {

@@ -82,7 +82,7 @@ __device__ __forceinline__ void axpy_one(const ElemParams& p, Terms& t, int64_t 
 // group summed in 32 bits before the 64-bit accumulation.
 template <int FOP, int IOP, bool PAIR, bool IMOD32>
 __device__ __forceinline__ void axpy_v8(const ElemParams& p, Terms& t, int64_t& i, int64_t iend) {
-    F2 S = f2(0.0f, 0.0f), C = f2(0.0f, 0.0f);
+    FAcc2 acc2 = facc2_zero();
     uint32_t tm = (uint32_t)t.imod;
     const uint32_t inc = (uint32_t)p.imod_inc, m = (uint32_t)p.imod_mod;
     auto group = [&](const float* xv, float* yv, int64_t i0) {
@@ -91,12 +91,7 @@ __device__ __forceinline__ void axpy_v8(const ElemParams& p, Terms& t, int64_t& 
         st_v8_cs_f(p.y + i0, yv);
         if (PAIR) {
 #pragma unroll
-            for (int j = 0; j < 8; j += 2) {
-                F2 s2, e2;
-                two_sum2(S, f2(yv[j], yv[j + 1]), s2, e2);
-                S = s2;
-                C = f2_add(C, e2);
-            }
+            for (int j = 0; j < 8; j += 2) facc2_add(acc2, f2(yv[j], yv[j + 1]));
         } else {
 #pragma unroll
             for (int j = 0; j < 8; ++j) add_axpy_term<FOP>(p, t, xv[j], yv[j]);
@@ -132,12 +127,7 @@ __device__ __forceinline__ void axpy_v8(const ElemParams& p, Terms& t, int64_t& 
         i += 8;
     }
     if (IMOD32) t.imod = tm;
-    if (PAIR) {
-        float s0, s1, c0, c1;
-        f2_split(S, s0, s1);
-        f2_split(C, c0, c1);
-        t.f = facc_combine(facc_combine(t.f, FAcc{s0, c0}, UPIR_RED_ADD), FAcc{s1, c1}, UPIR_RED_ADD);
-    }
+    if (PAIR) t.f = facc_merge2(t.f, acc2);
 }
 
 template <int FOP, int IOP>
@@ -188,9 +178,7 @@ __device__ __forceinline__ void axpy_range(const ElemParams& p, Terms& t, int64_
 }
 
 template <int FOP>
-__device__ __forceinline__ void jacobi_point(const ElemParams& p, Terms& t, int64_t k) {
-    const int64_t inner = p.cols - 2;
-    const int64_t r = p.lb + k / inner, c = 1 + k % inner;
+__device__ __forceinline__ void jacobi_point(const ElemParams& p, Terms& t, int64_t r, int64_t c) {
     const float* u = p.uin;
     const int64_t at = r * p.cols + c;
     const float ns = __fadd_rn(u[at - p.cols], u[at + p.cols]);
@@ -208,7 +196,14 @@ __device__ __forceinline__ void body_range(const ElemParams& p, Terms& t, int64_
     if (BODY == UPIR_BODY_AXPY) {
         axpy_range<FOP, IOP>(p, t, k0, k1);
     } else if (BODY == UPIR_BODY_JACOBI5) {
-        for (int64_t k = k0; k < k1; ++k) jacobi_point<FOP>(p, t, k);
+        // iteration k is interior point (lb + k / (cols - 2), 1 + k % (cols - 2)):
+        // one division per range, then the column advances
+        const int64_t inner = p.cols - 2;
+        int64_t r = p.lb + k0 / inner, c = 1 + k0 % inner;
+        for (int64_t k = k0; k < k1; ++k) {
+            jacobi_point<FOP>(p, t, r, c);
+            if (++c == p.cols - 1) c = 1, ++r;
+        }
     } else if (BODY == UPIR_BODY_COVERAGE) {
         for (int64_t k = k0; k < k1; ++k) {
             p.owner[k] = worker;

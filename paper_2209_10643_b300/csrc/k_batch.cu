@@ -33,8 +33,48 @@ __device__ __forceinline__ void axpy_tile(const BatchParams& P, const BatchRegio
     };
     const float* x = R.in0;
     float* y = R.out;
-    const bool vec = ((reinterpret_cast<uintptr_t>(x + e0) | reinterpret_cast<uintptr_t>(y + e0)) & 15) == 0;
-    if (vec) {
+    const uintptr_t al = reinterpret_cast<uintptr_t>(x + e0) | reinterpret_cast<uintptr_t>(y + e0);
+    if ((al & 31) == 0) {
+        // groups of eight iterations on 256-bit accesses, two groups per
+        // unit in flight; the reduction terms go to paired accumulators
+        FAcc2 acc2 = facc2_zero();
+        const int64_t n8 = (e1 - e0) / 8;
+        const int B = blockDim.x;
+        auto group = [&](const float* xv, float* yv, int64_t g) {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) yv[j] = __fmaf_rn(a, xv[j], yv[j]);
+            st_v8_cs_f(y + e0 + 8 * g, yv);
+            if (red) {
+#pragma unroll
+                for (int j = 0; j < 8; j += 2) {
+                    if (xy) facc2_add_prod(acc2, f2(xv[j], xv[j + 1]), f2(yv[j], yv[j + 1]));
+                    else facc2_add(acc2, f2(yv[j], yv[j + 1]));
+                }
+            }
+        };
+        int64_t g = threadIdx.x;
+        for (; g + B < n8; g += 2 * B) {
+            float x0[8], y0[8], x1[8], y1[8];
+            ld_v8_cs(x + e0 + 8 * g, x0);
+            ld_v8_cs(y + e0 + 8 * g, y0);
+            ld_v8_cs(x + e0 + 8 * (g + B), x1);
+            ld_v8_cs(y + e0 + 8 * (g + B), y1);
+            group(x0, y0, g);
+            group(x1, y1, g + B);
+        }
+        if (g < n8) {
+            float x0[8], y0[8];
+            ld_v8_cs(x + e0 + 8 * g, x0);
+            ld_v8_cs(y + e0 + 8 * g, y0);
+            group(x0, y0, g);
+        }
+        for (int64_t e = e0 + 8 * n8 + threadIdx.x; e < e1; e += B) {
+            const float yn = __fmaf_rn(a, x[e], y[e]);
+            y[e] = yn;
+            term(x[e], yn);
+        }
+        if (red) f = facc_merge2(f, acc2);
+    } else if ((al & 15) == 0) {
         const int64_t n4 = (e1 - e0) / 4;
 #pragma unroll 4
         for (int64_t g = threadIdx.x; g < n4; g += blockDim.x) {

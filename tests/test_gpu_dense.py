@@ -37,7 +37,8 @@ def check_matvec(a, x, y):
     assert np.all(np.abs(y - ref) <= 1e-5 * absax + 1e-30)
 
 
-@pytest.mark.parametrize("rows,cols", [(1, 1), (5, 3), (33, 517), (1000, 1003), (257, 4096), (64, 20000)])
+@pytest.mark.parametrize("rows,cols", [(1, 1), (5, 3), (33, 517), (1000, 1003), (257, 4096), (64, 20000),
+                                       (3, 2), (17, 130), (40, 5501), (300, 2481), (9, 642)])
 def test_matvec_shapes(s, rows, cols):
     a, x = I.matvec_inputs(rows, cols)
     check_matvec(a, x, run_matvec(s, a, x))
