@@ -530,6 +530,17 @@ __device__ __forceinline__ void tma_load_2d(void* smem_dst, const void* tmap, ui
         : "memory");
 }
 
+// One-dimensional tiled copy of box elements starting at element x (x times
+// the element size a multiple of 16 bytes; elements past either end of the
+// tensor read as zero).  The destination must be 128-byte aligned.
+__device__ __forceinline__ void tma_load_1d(void* smem_dst, const void* tmap, uint64_t* bar, int32_t x) {
+    asm volatile(
+        "cp.async.bulk.tensor.1d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2}], [%3];"
+        ::"r"(smem_u32(smem_dst)), "l"(tmap), "r"(x), "r"(smem_u32(bar))
+        : "memory");
+}
+
 __device__ __forceinline__ void prefetch_tmap(const void* tmap) {
     asm volatile("prefetch.tensormap [%0];" ::"l"(tmap) : "memory");
 }

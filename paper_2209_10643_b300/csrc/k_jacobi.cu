@@ -10,6 +10,15 @@
 // max-norm residual is folded into the reduction variable with one atomic per
 // team; max/min are exact in any order, so the result does not depend on
 // which team finishes first.
+//
+// Grids whose width is not a multiple of 4 have rows that do not start on a
+// 16-byte boundary, which a 2D tensor map cannot describe (its row pitch must
+// be a multiple of 16 bytes).  jacobi_rows_kernel views such a grid as one
+// dimension and copies each halo row on its own, from the 16-byte boundary at
+// or before the row's first column; a row then sits in shared memory shifted
+// by 0-3 columns, the same shift for the whole row.  Its lanes take the
+// tile's columns cyclically (lane q: columns q, q + TN/4, ...), so 32-bit
+// shared loads from any shift and 32-bit global stores stay unit-stride.
 #include <cstring>
 
 #include "device_common.cuh"
@@ -142,22 +151,158 @@ __global__ void __launch_bounds__(1024) jacobi_tma_kernel(const JacobiParams p,
     }
 }
 
+// The row-copy variant (widths that are not a multiple of 4).  Per stage,
+// thread 0 takes the next tile and arms the stage's barrier while the team
+// computes; once the team has finished with the stage, threads 0 .. TM + 1
+// issue one halo-row copy each, so the copies cost every thread at most one
+// instruction.
+template <int S, int ROP>
+__global__ void __launch_bounds__(1024) jacobi_rows_kernel(const JacobiParams p,
+                                                          const __grid_constant__ CUtensorMap tmap) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bar[S];
+    __shared__ int2 stage_rc[S];  // (first row, first column) of the tile in each stage; x < 0: none
+    __shared__ int last_team;
+    const int TM = p.tile_m, TN = p.tile_n;
+    const int SW = jacobi_rt_pitch(TN);  // every row copy lands on a 128-byte boundary
+    const int stage_floats = ((TM + 2) * SW + 255) / 256 * 256;
+    float* ring = smem_align1k<float>(smem_raw);
+    const int tpr = TN / 4;
+    const int tx = threadIdx.x % tpr, ty = threadIdx.x / tpr;
+    const int nty = blockDim.x / tpr;
+    const bool active = threadIdx.x < nty * tpr;
+    const uint32_t box_bytes = (uint32_t)((TM + 2) * (TN + 8) * sizeof(float));
+    const int cols = (int)p.cols, r_ub = (int)p.r_ub;
+    const uint32_t cq = (uint32_t)cols & 3u;
+    float racc = ROP == UPIR_RED_MIN ? __int_as_float(0x7f800000) : -__int_as_float(0x7f800000);
+
+    TileIter it = tile_iter_begin(p);
+    // thread 0: the team's next tile into stage s, arming the stage's barrier
+    auto take_next = [&](int s) {
+        const int64_t t = tile_iter_next(it, p);
+        if (t < 0) {
+            stage_rc[s] = make_int2(-1, -1);
+            return;
+        }
+        const int tr = (int)(t / p.tiles_c), tc = (int)(t - (int64_t)tr * p.tiles_c);
+        stage_rc[s] = make_int2((int)p.r_lb + tr * TM, tc * TN);
+        mbar_arrive_expect_tx(&bar[s], box_bytes);
+    };
+    // halo row i of the tile in stage s, from the 16-byte boundary at or
+    // before its grid column c0 - 4 (a multiple of 4 elements of the 1D view)
+    auto copy_rows = [&](int s) {
+        const int2 rc = stage_rc[s];
+        if (rc.x < 0) return;
+        for (int i = threadIdx.x; i < TM + 2; i += blockDim.x) {
+            const int64_t g = (int64_t)(rc.x - 1 + i) * cols + rc.y - 4;
+            tma_load_1d(ring + s * stage_floats + i * SW, &tmap, &bar[s], (int32_t)(g & ~(int64_t)3));
+        }
+    };
+
+    if (threadIdx.x == 0) {
+        prefetch_tmap(&tmap);
+#pragma unroll
+        for (int s = 0; s < S; ++s) mbar_init(&bar[s], 1);
+        fence_mbar_init();
+    }
+    // the previous sweep's output is this sweep's input: wait for it
+    if (p.wait_prior) griddep_wait();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int s = 0; s < S; ++s) take_next(s);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int s = 0; s < S; ++s) copy_rows(s);
+    griddep_launch_dependents();
+
+    bool failed = false;
+    int s = 0;
+    uint32_t parity = 0;
+    for (;;) {
+        const int2 rc = stage_rc[s];
+        if (rc.x < 0) break;
+        if (!__syncthreads_and(mbar_wait_bounded(&bar[s], parity, p.spin_limit, p.err_word))) {
+            failed = true;
+            break;
+        }
+        // every thread has read stage_rc[s] and the stage's phase is complete:
+        // the stage's next tile can be taken and its barrier re-armed
+        if (threadIdx.x == 0) take_next(s);
+        if (active) {
+            const float* st = ring + s * stage_floats;
+            const int nrows = min(TM, r_ub - rc.x);
+            // halo row h sits shifted by ((r0 - 1 + h) * cols + c0) mod 4 columns
+            const uint32_t sh0 = ((uint32_t)(rc.x - 1) * cq + (uint32_t)rc.y) & 3u;
+            for (int i2 = ty; i2 < nrows; i2 += nty) {
+                // grid column c0 of the rows above, at and below the output row
+                const float* rn = st + i2 * SW + ((sh0 + (uint32_t)i2 * cq) & 3u) + 4;
+                const float* rm = st + (i2 + 1) * SW + ((sh0 + (uint32_t)(i2 + 1) * cq) & 3u) + 4;
+                const float* rs = st + (i2 + 2) * SW + ((sh0 + (uint32_t)(i2 + 2) * cq) & 3u) + 4;
+                float* orow = p.uout + (size_t)(rc.x + i2) * cols + rc.y;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int q = tx + tpr * j;
+                    const int c = rc.y + q;
+                    const float cv = rm[q];
+                    const float v = __fmul_rn(0.25f, __fadd_rn(__fadd_rn(rn[q], rs[q]), __fadd_rn(rm[q - 1], rm[q + 1])));
+                    if (c >= 1 && c <= cols - 2) {
+                        __stcs(orow + q, v);
+                        if (ROP) racc = fold(racc, fabsf(__fsub_rn(v, cv)), ROP);
+                    }
+                }
+            }
+        }
+        __syncthreads();  // every thread is done with stage s; stage_rc[s] holds its next tile
+        copy_rows(s);
+        if (++s == S) {
+            s = 0;
+            parity ^= 1u;
+        }
+    }
+
+    if (ROP && !failed) {
+        const float b = block_fold(racc, ROP);
+        if (threadIdx.x == 0) atomic_fold_minmax(p.rvar, b, ROP);
+    }
+    tile_iter_reset(p, &last_team);
+    if (failed && threadIdx.x == 0) {
+        // copies still in flight get a bounded chance to land before the
+        // shared memory is released
+        for (int k = 0; k < S; ++k) {
+            if (stage_rc[k].x < 0) continue;
+            if (!mbar_wait_bounded(&bar[k], 0, p.spin_limit, nullptr))
+                mbar_wait_bounded(&bar[k], 1, p.spin_limit, nullptr);
+        }
+    }
+}
+
 using JacobiKernel = void (*)(const JacobiParams, const CUtensorMap);
 
-template <int S>
+template <int S, bool ROWS>
 JacobiKernel pick_rop(int rop) {
+    if (ROWS) {
+        if (rop == UPIR_RED_MAX) return jacobi_rows_kernel<S, UPIR_RED_MAX>;
+        if (rop == UPIR_RED_MIN) return jacobi_rows_kernel<S, UPIR_RED_MIN>;
+        return jacobi_rows_kernel<S, 0>;
+    }
     if (rop == UPIR_RED_MAX) return jacobi_tma_kernel<S, UPIR_RED_MAX>;
     if (rop == UPIR_RED_MIN) return jacobi_tma_kernel<S, UPIR_RED_MIN>;
     return jacobi_tma_kernel<S, 0>;
 }
 
-JacobiKernel pick_kernel(int stages, int rop) {
+template <bool ROWS>
+JacobiKernel pick_stages(int stages, int rop) {
     switch (stages) {
-        case 1: return pick_rop<1>(rop);
-        case 2: return pick_rop<2>(rop);
-        case 3: return pick_rop<3>(rop);
-        default: return pick_rop<4>(rop);
+        case 1: return pick_rop<1, ROWS>(rop);
+        case 2: return pick_rop<2, ROWS>(rop);
+        case 3: return pick_rop<3, ROWS>(rop);
+        default: return pick_rop<4, ROWS>(rop);
     }
+}
+
+JacobiKernel pick_kernel(int stages, int rop, bool rows) {
+    return rows ? pick_stages<true>(stages, rop) : pick_stages<false>(stages, rop);
 }
 
 bool configure_jacobi(JacobiKernel k) {
@@ -177,17 +322,18 @@ bool configure_jacobi(JacobiKernel k) {
 
 }  // namespace
 
-size_t jacobi_tma_smem_bytes(int tile_m, int tile_n, int stages) {
-    const size_t stage_floats = ((size_t)(tile_m + 2) * (tile_n + 8) + 255) / 256 * 256;
+size_t jacobi_tma_smem_bytes(int tile_m, int tile_n, int stages, bool rows) {
+    const size_t sw = rows ? (size_t)jacobi_rt_pitch(tile_n) : (size_t)tile_n + 8;
+    const size_t stage_floats = ((size_t)(tile_m + 2) * sw + 255) / 256 * 256;
     return stage_floats * sizeof(float) * stages + 1024;
 }
 
-int jacobi_tma_max_teams_per_sm(int units, int tile_m, int tile_n, int stages) {
-    JacobiKernel k = pick_kernel(stages, UPIR_RED_MAX);
+int jacobi_tma_max_teams_per_sm(int units, int tile_m, int tile_n, int stages, bool rows) {
+    JacobiKernel k = pick_kernel(stages, UPIR_RED_MAX, rows);
     if (!configure_jacobi(k)) return 0;
     int n = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, units,
-                                                      jacobi_tma_smem_bytes(tile_m, tile_n, stages)) != cudaSuccess) {
+                                                      jacobi_tma_smem_bytes(tile_m, tile_n, stages, rows)) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
@@ -196,11 +342,12 @@ int jacobi_tma_max_teams_per_sm(int units, int tile_m, int tile_n, int stages) {
 
 cudaError_t launch_jacobi_tma(int teams, int units, const JacobiParams& p, const void* tmap,
                               cudaStream_t s) {
-    JacobiKernel k = pick_kernel(p.stages, p.rvar ? p.rop : 0);
+    JacobiKernel k = pick_kernel(p.stages, p.rvar ? p.rop : 0, p.rows_tma != 0);
     if (!configure_jacobi(k)) return cudaGetLastError();
     CUtensorMap m;
     memcpy(&m, tmap, sizeof(m));
-    return launch_pdl(k, teams, units, jacobi_tma_smem_bytes(p.tile_m, p.tile_n, p.stages), s, p, m);
+    return launch_pdl(k, teams, units, jacobi_tma_smem_bytes(p.tile_m, p.tile_n, p.stages, p.rows_tma != 0), s,
+                      p, m);
 }
 
 }  // namespace upir

@@ -139,19 +139,42 @@ using PFN_encodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32
                                      const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
                                      CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
-upir_status encode_tmap_2d(upir_ctx ctx, CUtensorMap* m, const void* base, int dtype_code,
-                           int elem_bytes, uint64_t cols, uint64_t rows, uint32_t box_cols,
-                           uint32_t box_rows, int swizzle_bytes) {
+static PFN_encodeTiled encode_fn(upir_ctx ctx) {
     static PFN_encodeTiled fn = nullptr;
     if (!fn) {
         cudaDriverEntryPointQueryResult q;
         void* f = nullptr;
         cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000,
                                                          cudaEnableDefault, &q);
-        if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !f)
-            return fail(ctx, UPIR_ECUDA, "cuTensorMapEncodeTiled entry point unavailable");
+        if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !f) {
+            fail(ctx, UPIR_ECUDA, "cuTensorMapEncodeTiled entry point unavailable");
+            return nullptr;
+        }
         fn = reinterpret_cast<PFN_encodeTiled>(f);
     }
+    return fn;
+}
+
+upir_status encode_tmap_1d(upir_ctx ctx, CUtensorMap* m, const void* base, int dtype_code, uint64_t n,
+                           uint32_t box) {
+    PFN_encodeTiled fn = encode_fn(ctx);
+    if (!fn) return UPIR_ECUDA;
+    const cuuint64_t dims[1] = {n};
+    const cuuint64_t strides[1] = {0};  // a rank-1 map has no strides; the array is not read
+    const cuuint32_t boxd[1] = {box};
+    const cuuint32_t estr[1] = {1};
+    CUresult r = fn(m, (CUtensorMapDataType)dtype_code, 1, const_cast<void*>(base), dims, strides, boxd, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(ctx, UPIR_ECUDA, "cuTensorMapEncodeTiled (1D) failed (%d)", (int)r);
+    return UPIR_OK;
+}
+
+upir_status encode_tmap_2d(upir_ctx ctx, CUtensorMap* m, const void* base, int dtype_code,
+                           int elem_bytes, uint64_t cols, uint64_t rows, uint32_t box_cols,
+                           uint32_t box_rows, int swizzle_bytes) {
+    PFN_encodeTiled fn = encode_fn(ctx);
+    if (!fn) return UPIR_ECUDA;
     const cuuint64_t dims[2] = {cols, rows};
     const cuuint64_t strides[1] = {cols * (uint64_t)elem_bytes};
     const cuuint32_t box[2] = {box_cols, box_rows};
@@ -368,20 +391,29 @@ upir_status plan_loop(upir_region r, const upir_loop_desc* d, LoopRec& lp) {
             if (ok.st) return ok.st;
             const float* uin = static_cast<const float*>(lp.bufs[0]->dev);
             float* uout = static_cast<float*>(lp.bufs[1]->dev);
-            const bool tma_ok = C % 4 == 0 && (reinterpret_cast<uintptr_t>(uin) & 15) == 0 &&
-                                (reinterpret_cast<uintptr_t>(uout) & 15) == 0 &&
-                                (!has_f || rv.fop == UPIR_RED_MAX || rv.fop == UPIR_RED_MIN);
-            if (lp.variant == 0 && tma_ok) {
+            const bool aligned = (reinterpret_cast<uintptr_t>(uin) & 15) == 0 &&
+                                 (reinterpret_cast<uintptr_t>(uout) & 15) == 0 &&
+                                 (!has_f || rv.fop == UPIR_RED_MAX || rv.fop == UPIR_RED_MIN);
+            // widths that are not a multiple of 4: one copy per halo row from a
+            // 1D view of the grid (its element indices must fit 32 bits, and
+            // the view holds at least one box of up to 256 elements)
+            const bool rows_tma = C % 4 != 0 && R * C < (1ll << 31) - 4096 && R * C >= 256;
+            if (lp.variant == 0 && aligned && (C % 4 == 0 || rows_tma)) {
                 lp.kind = LK_JACOBI_TMA;
                 JacobiParams& jp = lp.jp;
                 memset(&jp, 0, sizeof(jp));
+                jp.rows_tma = rows_tma ? 1 : 0;
+                // row copies: teams of 512 units on 64-row tiles, two stages
+                // (4095^2 grid: 28.9 us per sweep; 256 units, 32 rows and
+                // three stages 32.0 us)
+                if (rows_tma && !U0 && !auto_units) lp.units = 512;
                 lp.tile_m = lp.tile_m ? lp.tile_m : 64;
                 lp.tile_n = lp.tile_n ? lp.tile_n : 128;
                 lp.tile_n = (int)std::min<int64_t>(lp.tile_n, 4 * (int64_t)lp.units);
-                jp.stages = lp.stages ? lp.stages : 3;
-                while (jp.stages > 1 && jacobi_tma_smem_bytes(lp.tile_m, lp.tile_n, jp.stages) > 220 * 1024)
+                jp.stages = lp.stages ? lp.stages : (rows_tma ? 2 : 3);
+                while (jp.stages > 1 && jacobi_tma_smem_bytes(lp.tile_m, lp.tile_n, jp.stages, rows_tma) > 220 * 1024)
                     --jp.stages;
-                lp.smem = jacobi_tma_smem_bytes(lp.tile_m, lp.tile_n, jp.stages);
+                lp.smem = jacobi_tma_smem_bytes(lp.tile_m, lp.tile_n, jp.stages, rows_tma);
                 if (!ok(lp.smem <= 220 * 1024, UPIR_EINVAL, "Jacobi tile too large for shared memory"))
                     return ok.st;
                 jp.uin = uin;
@@ -403,14 +435,18 @@ upir_status plan_loop(upir_region r, const upir_loop_desc* d, LoopRec& lp) {
                 jp.err_word = ctx->err_word;
                 jp.wait_prior = wait_prior;
                 if (lp.trip) {
-                    upir_status st = encode_tmap_2d(ctx, &lp.tmap[0], uin, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4,
-                                                    (uint64_t)C, (uint64_t)R, (uint32_t)(lp.tile_n + 8),
-                                                    (uint32_t)(lp.tile_m + 2), 0);
+                    upir_status st =
+                        rows_tma ? encode_tmap_1d(ctx, &lp.tmap[0], uin, CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                                                  (uint64_t)(R * C), (uint32_t)(lp.tile_n + 8))
+                                 : encode_tmap_2d(ctx, &lp.tmap[0], uin, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4,
+                                                  (uint64_t)C, (uint64_t)R, (uint32_t)(lp.tile_n + 8),
+                                                  (uint32_t)(lp.tile_m + 2), 0);
                     if (st != UPIR_OK) return st;
                 }
                 // persistent teams: as many as are resident at once, balanced so
                 // every team gets the same number of tiles (to within one)
-                const int per_sm = std::max(1, jacobi_tma_max_teams_per_sm(lp.units, lp.tile_m, lp.tile_n, jp.stages));
+                const int per_sm =
+                    std::max(1, jacobi_tma_max_teams_per_sm(lp.units, lp.tile_m, lp.tile_n, jp.stages, rows_tma));
                 const int64_t slots = (int64_t)kNumSMs * per_sm;
                 if (T0) lp.teams = T0;
                 else if (lp.sched == UPIR_SCHED_STATIC && lp.chunk == 0) {

@@ -135,6 +135,8 @@ upir_status wait_region_buffers(upir_region r);
 
 // Encode a 2D tiled TMA descriptor (row-major [rows][cols] of `elem_bytes`);
 // swizzle_bytes is 0 (none), 32, 64 or 128.
+upir_status encode_tmap_1d(upir_ctx ctx, CUtensorMap* m, const void* base, int dtype_code, uint64_t n,
+                           uint32_t box);
 upir_status encode_tmap_2d(upir_ctx ctx, CUtensorMap* m, const void* base, int dtype_code,
                            int elem_bytes, uint64_t cols, uint64_t rows, uint32_t box_cols,
                            uint32_t box_rows, int swizzle_bytes);

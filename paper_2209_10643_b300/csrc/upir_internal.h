@@ -90,6 +90,7 @@ struct JacobiParams {
     float* rvar;  // reduction variable (max/min of |u_out - u_in|), or nullptr
     int rop;
     int stages;   // shared-memory pipeline depth
+    int rows_tma; // one copy per halo row from a 1D view of the grid (width not a multiple of 4)
     long long spin_limit;
     int* err_word;
     SchedConst sk;
@@ -218,7 +219,10 @@ cudaError_t launch_finalize(const RedVars& rv, const Scratch& sc, int64_t nslots
 int64_t finalize_groups(int64_t nslots);
 cudaError_t launch_jacobi_tma(int teams, int units, const JacobiParams& p, const void* tmap,
                               cudaStream_t s);
-size_t jacobi_tma_smem_bytes(int tile_m, int tile_n, int stages);
+size_t jacobi_tma_smem_bytes(int tile_m, int tile_n, int stages, bool rows);
+// shared row pitch (floats) of the row-copy Jacobi variant: the halo box width
+// tile_n + 8 rounded up to 128 bytes
+__host__ __device__ constexpr int jacobi_rt_pitch(int tile_n) { return (tile_n + 8 + 31) / 32 * 32; }
 constexpr int kJacobiTBUnits = 1024, kFilter7Units = 256, kFilter7Stages = 2;
 constexpr size_t kStencilSmemBudget = 222 * 1024;  // dynamic shared memory of the stencil kernels
 size_t jacobi_tb_plane_floats(int tile_m, int tile_n, int sweeps, int halo_c);
@@ -227,7 +231,7 @@ cudaError_t launch_jacobi_tb(int teams, int units, const JacobiTBParams& p, cons
 size_t filter7_smem_bytes(int tile_m, int tile_n);
 int filter7_max_teams_per_sm(int tile_m, int tile_n);
 cudaError_t launch_filter7(int teams, const Filter7Params& p, const void* tmap, cudaStream_t s);
-int jacobi_tma_max_teams_per_sm(int units, int tile_m, int tile_n, int stages);
+int jacobi_tma_max_teams_per_sm(int units, int tile_m, int tile_n, int stages, bool rows);
 cudaError_t launch_matvec(int teams, int units, const MatvecParams& p, cudaStream_t s);
 cudaError_t launch_gemm_f32(int teams, int units, const GemmParams& p, cudaStream_t s);
 cudaError_t launch_split_bf16(int teams, int units, const SplitParams& p, cudaStream_t s);

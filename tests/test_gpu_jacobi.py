@@ -60,7 +60,9 @@ def test_hand_worked_5x5():
 @pytest.mark.parametrize("rows,cols,sweeps,hints", [
     (64, 64, 7, ()),
     (131, 260, 5, ()),                                  # several tiles, ragged in both directions
-    (37, 61, 4, ()),                                    # cols % 4 != 0: per-point variant
+    (37, 61, 4, ()),                                    # cols % 4 != 0: one copy per halo row
+    (131, 259, 5, ()), (70, 1022, 3, ()), (45, 129, 4, ((U.UPIR_HINT_TILE_M, 5), (U.UPIR_HINT_TILE_N, 12))),
+    (33, 61, 3, ((U.UPIR_HINT_VARIANT, 1),)),           # per-point variant forced on an unaligned width
     (200, 516, 3, ((U.UPIR_HINT_TILE_M, 7), (U.UPIR_HINT_TILE_N, 20))),
     (300, 300, 3, ((U.UPIR_HINT_VARIANT, 1),)),         # per-point variant forced
     (3, 3, 2, ()), (3, 8, 2, ()), (8, 3, 2, ()),        # degenerate grids
@@ -81,6 +83,24 @@ def test_schedules_over_tiles(s, teams, units, sched, chunk):
     u, res = run_sweeps(s, u0, 3, teams=teams, units=units, sched=sched, chunk=chunk)
     um, rm = O.jacobi_run(u0, 3, mirror_f32=True)
     assert np.array_equal(u, um) and np.array_equal(res, rm)
+
+
+@pytest.mark.parametrize("teams,units,sched,chunk", [(5, 256, 0, 0), (3, 64, 0, 2), (7, 128, 1, 1),
+                                                     (0, 0, 1, 3), (4, 100, 0, 0), (3, 1, 1, 1)])
+@pytest.mark.parametrize("cols", [331, 330, 329])
+def test_unaligned_widths_over_tiles(s, teams, units, sched, chunk, cols):
+    u0 = I.jacobi_grid(150, cols, seed=4)
+    u, res = run_sweeps(s, u0, 3, teams=teams, units=units, sched=sched, chunk=chunk)
+    um, rm = O.jacobi_run(u0, 3, mirror_f32=True)
+    assert np.array_equal(u, um) and np.array_equal(res, rm)
+
+
+def test_unaligned_width_4095_ten_sweeps(s):
+    u0 = I.jacobi_grid(4095, seed=1)
+    u, res = run_sweeps(s, u0, 10)
+    um, rm = O.jacobi_run(u0, 10, mirror_f32=True)
+    assert np.array_equal(u.view(np.uint32), um.view(np.uint32))
+    assert np.array_equal(res.view(np.uint32), rm.view(np.uint32))
 
 
 def test_graph_submission_matches(s):
