@@ -361,6 +361,44 @@ def extra_jacobi_tb(rt: Runtime, pk: dict, sweeps_per_loop: int) -> dict:
             "note": "algorithmic bytes count 8 B per point per sweep; the grid crosses HBM once per loop"}
 
 
+def extra_jacobi_unaligned(rt: Runtime, pk: dict, n: int = 4095, sweeps: int = 20) -> dict:
+    """Jacobi sweeps on an n x n grid whose width is not a multiple of 4 (rows
+    off the 16-byte grid: the row-copy TMA kernel), one CUDA-graph submission
+    of `sweeps` loops, L2 flushed before each repetition."""
+    U, torch = rt.U, rt.torch
+    u0 = I.jacobi_grid(n, seed=1)
+    a, b = u0.copy(), u0.copy()
+    res = np.full(sweeps, -np.inf, np.float32)
+    ha, hb = rt.map(a, U.UPIR_MAP_TOFROM), rt.map(b, U.UPIR_MAP_TOFROM)
+    hr = rt.map(res, U.UPIR_MAP_TOFROM)
+    loops = []
+    for k in range(sweeps):
+        src, dst = (ha, hb) if k % 2 == 0 else (hb, ha)
+        loops.append(dict(lb=1, ub=n - 1, step=1, collapse=2, body=U.UPIR_BODY_JACOBI5, bufs=[src, dst],
+                          scalars=[n, n], reductions=[(U.UPIR_RED_MAX, U.UPIR_F32, U.UPIR_TERM_RESID, hr, k)]))
+    r = rt.region(loops)
+    U.upir_region_submit(r, U.UPIR_SUBMIT_GRAPH)
+    U.upir_ctx_wait(rt.ctx)
+    times = []
+    for _ in range(8):
+        rt.flush_l2()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        U.upir_region_submit(r, U.UPIR_SUBMIT_GRAPH)
+        ev1.record()
+        ev1.synchronize()
+        times.append(ev0.elapsed_time(ev1))
+    tm, tn = U.upir_region_loop_geometry(r, 0)
+    U.upir_region_destroy(r)
+    for h in (ha, hb, hr):
+        U.upir_data_unmap(rt.ctx, h)
+    rt.host.clear()
+    ms = statistics.median(times)
+    gbs = sweeps * 8 * (n - 2) ** 2 / (ms / 1e3) / 1e9
+    return {"grid": [n, n], "sweeps": sweeps, "teams": tm, "units": tn, "us_per_sweep": ms * 1e3 / sweeps,
+            "algorithmic_GB/s": gbs, "frac_hbm": gbs / pk["hbm_gbs"]}
+
+
 def extra_filter7(rt: Runtime, pk: dict) -> dict:
     """The size-7 filter (7 x 7 window, FMA chain) over a 4096^2 grid."""
     U = rt.U
@@ -602,6 +640,7 @@ def extra_workloads(rt: Runtime, pk: dict) -> dict:
             "matvec_16384": lambda: extra_matvec(rt, pk),
             "jacobi_tb4_4096": lambda: extra_jacobi_tb(rt, pk, 4),
             "jacobi_tb8_4096": lambda: extra_jacobi_tb(rt, pk, 8),
+            "jacobi_4095": lambda: extra_jacobi_unaligned(rt, pk),
             "filter7_4096": lambda: extra_filter7(rt, pk),
             "pipelined_regions": lambda: extra_pipeline(rt),
             "gemm_f32_4096": lambda: extra_gemm_f32(rt),
