@@ -541,9 +541,13 @@ def extra_gemm_tc(rt: Runtime, pk: dict) -> dict:
     pms, _, _ = rt.timed_submits(lambda: U.upir_region_submit(prep, 0), 5)
     out = {"shape": [m, n, k], "split_ms": pms}
     flops = 2.0 * m * n * k
-    for name, body, bufs, mult in (("bf16", U.UPIR_BODY_GEMM_BF16, [hah, hbh, hc], 1),
-                                   ("bf16x3", U.UPIR_BODY_GEMM_BF16X3, [hah, hal, hbh, hbl, hc], 3)):
-        r = rt.region([dict(lb=0, ub=m, collapse=2, body=body, bufs=bufs, scalars=[m, n, k])])
+    # bf16: the planner's kernel (CTA pairs at this size); bf16_one_sm: the
+    # one-SM kernel (variant 1) for comparison
+    for name, body, bufs, mult, hints in (
+            ("bf16", U.UPIR_BODY_GEMM_BF16, [hah, hbh, hc], 1, []),
+            ("bf16_one_sm", U.UPIR_BODY_GEMM_BF16, [hah, hbh, hc], 1, [(U.UPIR_HINT_VARIANT, 1)]),
+            ("bf16x3", U.UPIR_BODY_GEMM_BF16X3, [hah, hal, hbh, hbl, hc], 3, [])):
+        r = rt.region([dict(lb=0, ub=m, collapse=2, body=body, bufs=bufs, scalars=[m, n, k], hints=hints)])
         ms, _, _ = rt.timed_submits(lambda: U.upir_region_submit(r, 0), 10)
         U.upir_region_destroy(r)
         tf = flops / (ms / 1e3) / 1e12

@@ -1,0 +1,353 @@
+// The bfloat16 GEMM body (the matrix multiplication workload of §6) on CTA
+// pairs: tcgen05.mma with cta_group::2 computes a 256 x 256 output tile per
+// pair of SMs, each SM holding 128 rows of the accumulator in its own TMEM.
+//
+// Why pairs: with one SM per 128 x 256 tile every k-block moves 48 KB of
+// operands into shared memory (TMA) and 48 KB out of it (MMA), which caps the
+// tensor pipe below its rate on one SM's shared-memory bandwidth.  A pair
+// shares B: each SM loads its own 128 rows of A and half (128 rows) of the
+// tile's 256 rows of B^T, and the pair's MMA reads A from each SM and B from
+// both, so an SM moves 32 KB in and 32 KB out per k-block for the same flops.
+//
+// Roles per CTA (576 threads), as in the one-SM kernel:
+//   warp 0      one thread copies this CTA's A and B^T halves of each
+//               k-block into a 6-stage ring; the copies of both CTAs complete
+//               on the leading CTA's (rank 0) full barrier, which the leading
+//               producer arms with the bytes of both;
+//   warp 1      allocates 512 TMEM columns in both CTAs (cta_group::2); in the
+//               leading CTA one thread issues the pair's MMAs (M = 256,
+//               N = 256, K = 16) and commits each stage back to the empty
+//               barriers of both CTAs and each finished tile to the full-TMEM
+//               barriers of both;
+//   warps 2..17 read this CTA's 128 accumulator rows with tcgen05.ld, write
+//               them to C with 32-byte stores and release the accumulator to
+//               the leading CTA (one remote arrival per warp).
+// Pair tiles are dealt to clusters in blocked static runs; the planner uses
+// this kernel when every cluster gets at least one tile and K is one
+// accumulation segment.  Every wait is bounded; a CTA that gives up records
+// the timeout, lets its copies and MMAs land, and both CTAs meet at a cluster
+// barrier before the TMEM is freed.
+#include <cstring>
+
+#include "tc_common.cuh"
+
+namespace upir {
+
+namespace {
+
+constexpr int P2_BK = 64;                               // k-block: one 128-byte swizzled row
+constexpr int P2_STAGES = 6;
+constexpr int P2_A_BYTES = 128 * P2_BK * 2;             // this CTA's 128 rows of A
+constexpr int P2_B_BYTES = 128 * P2_BK * 2;             // this CTA's 128 rows of B^T
+constexpr int P2_STAGE_BYTES = P2_A_BYTES + P2_B_BYTES;  // 32 KB
+constexpr size_t P2_SMEM = (size_t)P2_STAGES * P2_STAGE_BYTES + 1024;
+constexpr int P2_TILE = 256;                             // pair tile: 256 x 256
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+// The shared::cluster address of `p`'s counterpart in CTA `rank` of the pair.
+__device__ __forceinline__ uint32_t pair_addr(const void* p, uint32_t rank) {
+    uint32_t a;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(a) : "r"(smem_u32(p)), "r"(rank));
+    return a;
+}
+
+__device__ __forceinline__ void cluster_sync_all() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_remote(uint32_t caddr) {
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(caddr) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait_cluster(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity) : "memory");
+    return ok != 0;
+}
+
+// A copy into this CTA's shared memory whose completion is counted on an
+// mbarrier of either CTA of the pair (given by its shared::cluster address).
+__device__ __forceinline__ void tma_load_2d_pair(void* dst, const void* tmap, uint32_t bar_caddr, int32_t x,
+                                                 int32_t y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];"
+        ::"r"(smem_u32(dst)), "l"(tmap), "r"(x), "r"(y), "r"(bar_caddr)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_pair(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+        ::"r"(d_tmem), "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+}
+
+// Arrive on the barrier at this offset in both CTAs once the pair's MMAs
+// issued so far have completed.
+__device__ __forceinline__ void commit_both(uint64_t* bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;"
+        ::"r"(smem_u32(bar)), "h"((uint16_t)3) : "memory");
+}
+
+__device__ __forceinline__ void commit_own(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                 ::"r"(smem_u32(bar)) : "memory");
+}
+
+// kind::f16 instruction descriptor for the pair: FP32 accumulator, bfloat16
+// A and B, both K-major, M = 256, N = 256.
+__host__ __device__ constexpr uint32_t pair_idesc() {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(P2_TILE >> 3) << 17) | ((uint32_t)(P2_TILE >> 4) << 24);
+}
+
+// Bounded wait; `cluster` waits acquire at cluster scope (the barrier is
+// arrived on from the other CTA).
+__device__ __forceinline__ bool p2_wait(uint64_t* bar, uint32_t parity, const TcParams& p, volatile int* abort_flag,
+                                        bool cluster = false) {
+    for (long long n = 0; n < p.spin_limit; ++n) {
+        if (cluster ? mbar_try_wait_cluster(bar, parity) : mbar_try_wait(bar, parity)) return true;
+        if ((n & 255) == 255 && *abort_flag) return false;
+    }
+    atomicCAS(p.err_word, 0, UPIR_ERR_WAIT_TIMEOUT);
+    *abort_flag = 1;
+    return false;
+}
+
+// This cluster's pair tiles: a blocked run of the tile loop.
+struct P2Run {
+    int64_t next, end;
+};
+
+__device__ __forceinline__ P2Run p2_run(const TcParams& p) {
+    const int64_t c = blockIdx.x >> 1;
+    P2Run r;
+    r.next = c * p.sk.base + min(c, p.sk.extra);
+    r.end = r.next + p.sk.base + (c < p.sk.extra ? 1 : 0);
+    return r;
+}
+
+// NACC accumulator buffers of 256 TMEM columns (2: the epilogue of one tile
+// overlaps the MMAs of the next).
+template <int NACC>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(TC_THREADS, 1)
+gemm_tc2_kernel(const TcParams p, const __grid_constant__ CUtensorMap tm_a, const __grid_constant__ CUtensorMap tm_b) {
+    constexpr uint32_t kCols = 256u * NACC;
+    using Cfg = TcCfg<false>;  // BK 64, 128-byte swizzle: the same operand layout
+    constexpr int S = P2_STAGES;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t full[S], empty[S], tfull[NACC], tempty[NACC], mma_done;
+    __shared__ uint32_t tmem_base_sh;
+    __shared__ volatile int abort_flag;
+    unsigned char* ring = reinterpret_cast<unsigned char*>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t rank = cluster_rank();
+    const bool leader = rank == 0;
+    const int nkb = (int)((p.K + P2_BK - 1) / P2_BK);
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int a = 0; a < NACC; ++a) {
+            mbar_init(&tfull[a], 1);
+            mbar_init(&tempty[a], 2 * (TC_EPI_THREADS / 32));  // every epilogue warp of both CTAs
+        }
+        mbar_init(&mma_done, 1);
+        abort_flag = 0;
+        fence_mbar_init();
+        prefetch_tmap(&tm_a);
+        prefetch_tmap(&tm_b);
+    }
+    if (warp == 1) {
+        // one warp of each CTA of the pair takes part in the allocation
+        asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;"
+                     ::"r"(smem_u32(&tmem_base_sh)), "r"(kCols) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    // both CTAs' barriers are initialised (and their TMEM allocated) before
+    // either CTA's copies, commits or arrivals can reach them
+    cluster_sync_all();
+    tc_fence_after();
+    const uint32_t tmem_base = tmem_base_sh;
+    // the pair's MMAs write the same TMEM columns in both CTAs: a pair whose
+    // allocations differ records an error and does no work
+    uint32_t peer_base;
+    asm volatile("ld.shared::cluster.u32 %0, [%1];" : "=r"(peer_base) : "r"(pair_addr(&tmem_base_sh, rank ^ 1u)) : "memory");
+    const bool pair_bad = peer_base != tmem_base;
+    if (pair_bad && threadIdx.x == 0) atomicCAS(p.err_word, 0, UPIR_ERR_WAIT_TIMEOUT);
+
+    auto stage_a = [&](int s) { return ring + (size_t)s * P2_STAGE_BYTES; };
+    auto stage_b = [&](int s) { return ring + (size_t)s * P2_STAGE_BYTES + P2_A_BYTES; };
+
+    if (pair_bad) {
+        // nothing to do: both CTAs go straight to the teardown
+    } else if (warp == 0) {
+        if (lane == 0) {
+            // ---------------- producer: this CTA's halves of each k-block ----------------
+            P2Run run = p2_run(p);
+            int s = 0;
+            uint32_t ph = 0;
+            uint32_t issued_parity[S];
+            bool issued[S];
+            for (int k = 0; k < S; ++k) issued[k] = false, issued_parity[k] = 0;
+            for (int64_t u = run.next; u < run.end && !abort_flag; ++u) {
+                const int64_t mt = u % p.tiles_m, nt = u / p.tiles_m;
+                const int32_t m0 = (int32_t)(p.row_lb + mt * P2_TILE + 128 * (int64_t)rank);
+                const int32_t n0 = (int32_t)(nt * P2_TILE + 128 * (int64_t)rank);
+                for (int kb = 0; kb < nkb; ++kb) {
+                    if (!p2_wait(&empty[s], ph ^ 1u, p, &abort_flag)) break;
+                    const uint32_t fb = pair_addr(&full[s], 0);
+                    if (leader) mbar_arrive_expect_tx(&full[s], 2u * P2_STAGE_BYTES);
+                    tma_load_2d_pair(stage_a(s), &tm_a, fb, kb * P2_BK, m0);
+                    tma_load_2d_pair(stage_b(s), &tm_b, fb, kb * P2_BK, n0);
+                    issued[s] = true;
+                    issued_parity[s] = ph;
+                    if (++s == S) s = 0, ph ^= 1u;
+                }
+            }
+            if (abort_flag && leader) {
+                // copies in flight get a bounded chance to land before the ring is released
+                for (int k = 0; k < S; ++k)
+                    if (issued[k]) mbar_wait_bounded(&full[k], issued_parity[k], p.spin_limit, nullptr);
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0 && leader) {
+            // ---------------- MMA issuer (leading CTA) ----------------
+            constexpr uint32_t idesc = pair_idesc();
+            P2Run run = p2_run(p);
+            int s = 0, acc = 0;
+            uint32_t ph = 0, aph = 0;
+            bool issued_any = false, ok = true;
+            for (int64_t u = run.next; u < run.end && ok && !abort_flag; ++u) {
+                if (!p2_wait(&tempty[acc], aph ^ 1u, p, &abort_flag, true)) break;
+                tc_fence_after();
+                const uint32_t d_tmem = tmem_base + (uint32_t)(acc * TC_BN);
+                for (int kb = 0; kb < nkb; ++kb) {
+                    if (!p2_wait(&full[s], ph, p, &abort_flag, true)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t a = smem_u32(stage_a(s)), b = smem_u32(stage_b(s));
+#pragma unroll
+                    for (int k = 0; k < P2_BK / 16; ++k) {
+                        const uint32_t koff = (uint32_t)k * 32u;  // 16 bfloat16 along K
+                        mma_pair(d_tmem, smem_desc<Cfg>(a + koff), smem_desc<Cfg>(b + koff), idesc,
+                                 (kb > 0 || k > 0) ? 1u : 0u);
+                    }
+                    issued_any = true;
+                    commit_both(&empty[s]);  // both CTAs' stage s is free once these MMAs have read it
+                    if (++s == S) s = 0, ph ^= 1u;
+                }
+                if (!ok) break;
+                commit_both(&tfull[acc]);
+                if (++acc == NACC) acc = 0, aph ^= 1u;
+            }
+            if (abort_flag && issued_any) {
+                // MMAs in flight must finish before either CTA frees its TMEM
+                commit_own(&mma_done);
+                mbar_wait_bounded(&mma_done, 0, p.spin_limit, nullptr);
+            }
+        }
+    } else {
+        // ---------------- epilogue: this CTA's 128 accumulator rows -> C ----------------
+        const int q = warp & 3;               // TMEM lane quadrant this warp may access
+        const int quarter = (warp - 2) >> 2;  // which 64 of the 256 columns
+        P2Run run = p2_run(p);
+        int acc = 0;
+        uint32_t aph = 0;
+        const bool v8_ok = (p.N % 8) == 0 && (reinterpret_cast<uintptr_t>(p.C) & 31) == 0;
+        const uint32_t te0 = pair_addr(&tempty[0], 0), te1 = pair_addr(&tempty[NACC - 1], 0);
+        for (int64_t u = run.next; u < run.end && !abort_flag; ++u) {
+            const int64_t mt = u % p.tiles_m, nt = u / p.tiles_m;
+            const int64_t row = p.row_lb + mt * P2_TILE + 128 * (int64_t)rank + 32 * q + lane;
+            const int64_t n0 = nt * P2_TILE + quarter * TC_EPI_COLS;
+            float* crow = row < p.row_ub ? p.C + row * p.N : nullptr;
+            const bool full_row = v8_ok && n0 + TC_EPI_COLS <= p.N;
+            if (!p2_wait(&tfull[acc], aph, p, &abort_flag)) break;
+            tc_fence_after();
+            const uint32_t ta = tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(quarter * TC_EPI_COLS) +
+                                (uint32_t)(acc * TC_BN);
+#pragma unroll
+            for (int h = 0; h < TC_EPI_COLS; h += 32) {
+                float v[32];
+                tmem_ld32(ta + (uint32_t)h, v);
+                if (crow) store_row(crow, n0 + h, p.N, full_row, v, 32);
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive_remote(acc ? te1 : te0);
+            if (++acc == NACC) acc = 0, aph ^= 1u;
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    // neither CTA frees its TMEM or leaves while the pair's MMAs, copies or
+    // arrivals may still reach it
+    cluster_sync_all();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;"
+                     ::"r"(tmem_base), "r"(kCols) : "memory");
+    }
+}
+
+constexpr int kNacc = 2;
+
+}  // namespace
+
+size_t gemm_tc2_smem_bytes() { return P2_SMEM; }
+
+int gemm_tc2_max_clusters() {
+    static int cached = -1;
+    if (cached >= 0) return cached;
+    if (cudaFuncSetAttribute(gemm_tc2_kernel<kNacc>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P2_SMEM) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        return cached = 0;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(2 * kNumSMs / 2);
+    cfg.blockDim = dim3(TC_THREADS);
+    cfg.dynamicSmemBytes = P2_SMEM;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, gemm_tc2_kernel<kNacc>, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return cached = 0;
+    }
+    return cached = n;
+}
+
+cudaError_t launch_gemm_tc2(const TcParams& tp, int ctas, const CUtensorMap* a, const CUtensorMap* b,
+                            cudaStream_t s) {
+    static bool configured = false;
+    if (!configured) {
+        const cudaError_t e =
+            cudaFuncSetAttribute(gemm_tc2_kernel<kNacc>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P2_SMEM);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    gemm_tc2_kernel<kNacc><<<ctas, TC_THREADS, P2_SMEM, s>>>(tp, *a, *b);
+    return cudaGetLastError();
+}
+
+}  // namespace upir

@@ -136,7 +136,7 @@ def test_split_bf16_bit_exact(s, rows, cols, transpose):
 
 # --- tensor-core GEMM (tcgen05): bfloat16 and split-bfloat16 -----------------------
 
-def run_gemm_tc(s, a, b, x3=False, teams=0, chunk=0, lb=0, ub=None):
+def run_gemm_tc(s, a, b, x3=False, teams=0, chunk=0, lb=0, ub=None, variant=0):
     m, k = a.shape
     n = b.shape[1]
     ah, al = np.zeros(m * k, np.uint16), np.zeros(m * k, np.uint16)
@@ -150,8 +150,9 @@ def run_gemm_tc(s, a, b, x3=False, teams=0, chunk=0, lb=0, ub=None):
            dict(lb=0, ub=k, body=U.UPIR_BODY_SPLIT_BF16, bufs=[hb, hbh, hbl], scalars=[k, n, 1])])
     body = U.UPIR_BODY_GEMM_BF16X3 if x3 else U.UPIR_BODY_GEMM_BF16
     bufs = [hah, hal, hbh, hbl, hc] if x3 else [hah, hbh, hc]
+    hints = [(U.UPIR_HINT_VARIANT, variant)] if variant else []
     s.run([dict(lb=lb, ub=m if ub is None else ub, collapse=2, body=body, bufs=bufs, scalars=[m, n, k],
-                chunk=chunk)], teams, 0)
+                chunk=chunk, hints=hints)], teams, 0)
     for h in (ha, hb, hah, hal, hbh, hbl, hc):
         s.unmap(h)
     return c
@@ -185,6 +186,38 @@ def test_gemm_tc_k_split_exact_and_repeatable(s, x3):
     c1 = run_gemm_tc(s, a, b, x3)
     c2 = run_gemm_tc(s, a, b, x3)
     assert np.array_equal(c1, c2)
+
+
+# The CTA-pair kernel (tcgen05 cta_group::2, 256 x 256 tiles): the planner's
+# choice for large bfloat16 GEMMs, forced here (variant 2) on small and ragged
+# shapes; variant 1 is the one-SM kernel.
+@pytest.mark.parametrize("m,n,k", [(200, 300, 136), (2382, 1948, 64), (513, 257, 72), (256, 256, 64), (1, 9, 8)])
+def test_gemm_tc_pair_exact_small_integers(s, m, n, k):
+    a = I.small_int_matrix(m, k, -8, 8, seed=7)
+    b = I.small_int_matrix(k, n, -8, 8, seed=8)
+    assert np.array_equal(run_gemm_tc(s, a, b, variant=2), O.gemm(a, b))
+
+
+def test_gemm_tc_pair_matches_one_sm_kernel(s):
+    # the same K16 MMA sequence per output; the tensor core's own (not
+    # round-to-nearest) accumulation differs between M = 128 and M = 256
+    # instructions in the last bits only
+    a, b = I.gemm_inputs(1024, 768, 1000)
+    c1 = run_gemm_tc(s, a, b, variant=1)
+    c2 = run_gemm_tc(s, a, b, variant=2)
+    refb = O.gemm_bf16(a, b)
+    absab = np.abs(a.astype(np.float64)) @ np.abs(b.astype(np.float64))
+    check_tc(c2, refb, absab, 1000, tc_accum_tol(1000))
+    assert np.linalg.norm(c2 - c1) <= tc_accum_tol(1000) * np.linalg.norm(refb)
+    assert np.array_equal(c2, run_gemm_tc(s, a, b, variant=2))  # repeatable
+
+
+def test_gemm_tc_pair_row_subrange(s):
+    a, b = I.gemm_inputs(600, 300, 64)
+    c = run_gemm_tc(s, a, b, False, lb=70, ub=530, variant=2)
+    ref = O.gemm_bf16(a, b)
+    assert np.linalg.norm(c[70:530] - ref[70:530]) <= tc_accum_tol(64) * np.linalg.norm(ref[70:530])
+    assert np.all(c[:70] == -3.0) and np.all(c[530:] == -3.0)
 
 
 def tc_accum_tol(k):
