@@ -149,8 +149,12 @@ class Runtime:
         return r
 
     def timed_submits(self, submit, reps, warmup=3, flush=True):
-        """Median per-rep device time (ms) of ``submit()``, measured with the
-        library's per-launch CUDA events; also the per-launch records."""
+        """Mean per-rep device time (ms) of ``submit()``, measured with the
+        library's per-launch CUDA events; also the per-rep times and the
+        per-launch records.  The mean, not the median: event pairs around a
+        launch that follows other work read in steps of 2.048 us on this GPU,
+        and with the start's phase against those steps varying from rep to
+        rep only the mean converges on the duration."""
         U = self.U
         for _ in range(warmup):
             submit()
@@ -167,7 +171,7 @@ class Runtime:
             rec = U.upir_ctx_timings(self.ctx)
             per_rep.append(sum(ms for _, ms in rec))
             launches.extend(rec)
-        return statistics.median(per_rep), per_rep, launches
+        return statistics.fmean(per_rep), per_rep, launches
 
 
 def jacobi_region_loops(U, ha, hb, hr):
@@ -286,12 +290,8 @@ def extra_axpy(rt: Runtime, n: int, pk: dict) -> dict:
     r = rt.region([dict(lb=0, ub=n, body=U.UPIR_BODY_AXPY, bufs=[hx, hy], scalars=[2.5, 3, 1000],
                         reductions=[(U.UPIR_RED_ADD, U.UPIR_F32, U.UPIR_TERM_Y, hf, 0),
                                     (U.UPIR_RED_ADD, U.UPIR_I64, U.UPIR_TERM_IMOD, hi, 0)])])
-    # CUDA event timestamps on this GPU step in 2.048 us, so a region of a few
-    # microseconds reads as a multiple of that: the mean over the repetitions
-    # (each phase-shifted against the timer) is the estimate, not the median.
-    _, per, _ = rt.timed_submits(lambda: U.upir_region_submit(r, 0), 60)
-    _, gper, _ = rt.timed_submits(lambda: U.upir_region_submit(r, U.UPIR_SUBMIT_GRAPH), 60)
-    ms, gms = statistics.fmean(per), statistics.fmean(gper)
+    ms, _, _ = rt.timed_submits(lambda: U.upir_region_submit(r, 0), 60)
+    gms, _, _ = rt.timed_submits(lambda: U.upir_region_submit(r, U.UPIR_SUBMIT_GRAPH), 60)
     U.upir_region_destroy(r)
     for h in (hx, hy, hf, hi):
         U.upir_data_unmap(rt.ctx, h)
@@ -307,7 +307,7 @@ def extra_matvec(rt: Runtime, pk: dict) -> dict:
     y = np.zeros(n, np.float32)
     ha, hx, hy = rt.map(a, U.UPIR_MAP_TO), rt.map(x, U.UPIR_MAP_TO), rt.map(y, U.UPIR_MAP_TOFROM)
     r = rt.region([dict(lb=0, ub=n, body=U.UPIR_BODY_MATVEC, bufs=[ha, hx, hy], scalars=[n, n])])
-    ms, _, _ = rt.timed_submits(lambda: U.upir_region_submit(r, 0), 10)
+    ms, _, _ = rt.timed_submits(lambda: U.upir_region_submit(r, 0), 20)
     U.upir_region_destroy(r)
     for h in (ha, hx, hy):
         U.upir_data_unmap(rt.ctx, h)
@@ -409,7 +409,7 @@ def extra_filter7(rt: Runtime, pk: dict) -> dict:
     hx, ho = rt.map(x, U.UPIR_MAP_TO), rt.map(out, U.UPIR_MAP_TOFROM)
     r = rt.region([dict(lb=3, ub=N_GRID - 3, step=1, collapse=2, body=U.UPIR_BODY_FILTER7, bufs=[hx, ho],
                         scalars=[N_GRID, N_GRID] + [float(v) for v in w.ravel()])])
-    ms, _, _ = rt.timed_submits(lambda: U.upir_region_submit(r, 0), 10)
+    ms, _, _ = rt.timed_submits(lambda: U.upir_region_submit(r, 0), 30)
     tm, tn = U.upir_region_loop_geometry(r, 0)
     U.upir_region_destroy(r)
     for h in (hx, ho):
@@ -548,7 +548,7 @@ def extra_gemm_tc(rt: Runtime, pk: dict) -> dict:
             ("bf16_one_sm", U.UPIR_BODY_GEMM_BF16, [hah, hbh, hc], 1, [(U.UPIR_HINT_VARIANT, 1)]),
             ("bf16x3", U.UPIR_BODY_GEMM_BF16X3, [hah, hal, hbh, hbl, hc], 3, [])):
         r = rt.region([dict(lb=0, ub=m, collapse=2, body=body, bufs=bufs, scalars=[m, n, k], hints=hints)])
-        ms, _, _ = rt.timed_submits(lambda: U.upir_region_submit(r, 0), 10)
+        ms, _, _ = rt.timed_submits(lambda: U.upir_region_submit(r, 0), 30)
         U.upir_region_destroy(r)
         tf = flops / (ms / 1e3) / 1e12
         out[name] = {"ms": ms, "TFLOP/s": tf, "tensor_TFLOP/s": tf * mult,

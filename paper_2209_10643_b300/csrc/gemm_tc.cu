@@ -443,23 +443,27 @@ upir_status plan_gemm_tc(upir_region r, LoopRec& lp, int64_t M, int64_t N, int64
         if (maxc <= 0 && lp.variant == 2)
             return fail(ctx, UPIR_EUNSUPPORTED, "upir_loop: no cluster of two 576-thread teams fits this GPU");
         if (maxc > 0 && (nt2 >= maxc || lp.variant == 2)) {
-            const int64_t clusters = ceil_div(nt2, ceil_div(nt2, (int64_t)maxc));
+            // units dealt round-robin to the clusters; a last wave that would
+            // leave at least half of them idle is cut into 128-column halves
+            const int64_t C = maxc, whole = nt2 / C, rem = nt2 % C;
             tp.pair = 1;
             tp.tiles_m = tm2;
             tp.tiles_n = tn2;
             tp.ntiles = nt2;
-            tp.nunits = nt2;
             tp.full_tiles = nt2;
             tp.half_tiles = tp.split_tiles = 0;
+            if (whole > 0 && rem > 0 && 2 * rem <= C) {
+                tp.full_tiles = whole * C;
+                tp.half_tiles = rem;
+            }
+            tp.nunits = tp.full_tiles + 2 * tp.half_tiles;
             tp.parts = 1;
-            lp.teams = (int)(2 * clusters);
-            chunk_eff = 0;
-            tp.chunk = 0;
-            tp.sk = make_sched_const(nt2, 0, clusters);
+            lp.teams = (int)(2 * std::min<int64_t>(C, tp.nunits));
+            chunk_eff = 1;
         }
     }
     tp.chunk = chunk_eff;
-    if (!tp.pair) tp.sk = make_sched_const(tp.nunits, chunk_eff, lp.teams);
+    tp.sk = make_sched_const(tp.nunits, chunk_eff, tp.pair ? lp.teams / 2 : lp.teams);
     if (tp.parts > 1) {
         // partial tiles of every part, then one arrival counter per 32 x 64 block
         const size_t work_bytes = (size_t)tp.split_tiles * tp.parts * TC_BM * TC_BN * sizeof(float);
@@ -487,8 +491,11 @@ upir_status plan_gemm_tc(upir_region r, LoopRec& lp, int64_t M, int64_t N, int64
     const uint64_t rows[6] = {(uint64_t)M, (uint64_t)M, (uint64_t)N, (uint64_t)N, (uint64_t)N, (uint64_t)N};
     const uint32_t box_rows[6] = {TC_BM, TC_BM, TC_BN, TC_BN, TC_BN / 2, TC_BN / 2};
     for (int i = 0; i < 6; ++i) {
+        // the CTA-pair kernel's half tiles take 64 rows of B^T per CTA (the
+        // sixth map, unused by the plain bfloat16 one-SM kernel)
+        const uint32_t br = (tp.pair && i == 5) ? 64u : box_rows[i];
         upir_status s2 = encode_tmap_2d(ctx, &lp.tmap[i], bases[i], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
-                                        (uint64_t)K, rows[i], (uint32_t)bk, box_rows[i], bk * 2);
+                                        (uint64_t)K, rows[i], (uint32_t)bk, br, bk * 2);
         if (s2 != UPIR_OK) return s2;
     }
     return UPIR_OK;
@@ -502,7 +509,7 @@ cudaError_t launch_gemm_tc_loop(upir_ctx, LoopRec& lp, cudaStream_t s) {
     const int nkb = (int)((tp.K + (lp.body == UPIR_BODY_GEMM_BF16X3 ? TcCfg<true>::BK : TcCfg<false>::BK) - 1) /
                           (lp.body == UPIR_BODY_GEMM_BF16X3 ? TcCfg<true>::BK : TcCfg<false>::BK));
     const bool mseg = tp.seg_kb < nkb;
-    if (tp.pair) return launch_gemm_tc2(tp, lp.teams, &m[0], &m[4], s);
+    if (tp.pair) return launch_gemm_tc2(tp, lp.teams, &m[0], &m[4], &m[5], s);
     if (lp.body == UPIR_BODY_GEMM_BF16X3)
         return mseg ? tc_launch<true, true>(tp, lp.teams, m, s) : tc_launch<true, false>(tp, lp.teams, m, s);
     return mseg ? tc_launch<false, true>(tp, lp.teams, m, s) : tc_launch<false, false>(tp, lp.teams, m, s);

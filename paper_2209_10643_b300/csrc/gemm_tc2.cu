@@ -22,9 +22,10 @@
 //   warps 2..17 read this CTA's 128 accumulator rows with tcgen05.ld, write
 //               them to C with 32-byte stores and release the accumulator to
 //               the leading CTA (one remote arrival per warp).
-// Pair tiles are dealt to clusters in blocked static runs; the planner uses
-// this kernel when every cluster gets at least one tile and K is one
-// accumulation segment.  Every wait is bounded; a CTA that gives up records
+// Pair tiles are dealt to clusters round-robin; a last partial wave of tiles
+// is cut into 128-column halves when that leaves fewer clusters idle.  The
+// planner uses this kernel when every cluster gets at least one tile and K is
+// one accumulation segment.  Every wait is bounded; a CTA that gives up records
 // the timeout, lets its copies and MMAs land, and both CTAs meet at a cluster
 // barrier before the TMEM is freed.
 #include <cstring>
@@ -108,9 +109,9 @@ __device__ __forceinline__ void commit_own(uint64_t* bar) {
 }
 
 // kind::f16 instruction descriptor for the pair: FP32 accumulator, bfloat16
-// A and B, both K-major, M = 256, N = 256.
-__host__ __device__ constexpr uint32_t pair_idesc() {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(P2_TILE >> 3) << 17) | ((uint32_t)(P2_TILE >> 4) << 24);
+// A and B, both K-major, M = 256, N = 256 (128 for half tiles).
+__host__ __device__ constexpr uint32_t pair_idesc(int n = P2_TILE) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(P2_TILE >> 4) << 24);
 }
 
 // Bounded wait; `cluster` waits acquire at cluster scope (the barrier is
@@ -126,24 +127,26 @@ __device__ __forceinline__ bool p2_wait(uint64_t* bar, uint32_t parity, const Tc
     return false;
 }
 
-// This cluster's pair tiles: a blocked run of the tile loop.
-struct P2Run {
-    int64_t next, end;
+// Work units: the full pair tiles, then (a last partial wave) `half_tiles`
+// tiles cut into two 128-column halves (N = 128 MMAs, 64 rows of B^T per CTA).
+// Units are dealt to clusters round-robin.
+struct P2Unit {
+    int64_t tile;
+    int half;  // 0: all 256 columns; 1, 2: the first or second 128
 };
 
-__device__ __forceinline__ P2Run p2_run(const TcParams& p) {
-    const int64_t c = blockIdx.x >> 1;
-    P2Run r;
-    r.next = c * p.sk.base + min(c, p.sk.extra);
-    r.end = r.next + p.sk.base + (c < p.sk.extra ? 1 : 0);
-    return r;
+__device__ __forceinline__ P2Unit p2_unit(int64_t u, const TcParams& p) {
+    if (u < p.full_tiles) return P2Unit{u, 0};
+    const int64_t v = u - p.full_tiles;
+    return P2Unit{p.full_tiles + (v >> 1), 1 + (int)(v & 1)};
 }
 
 // NACC accumulator buffers of 256 TMEM columns (2: the epilogue of one tile
 // overlaps the MMAs of the next).
 template <int NACC>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(TC_THREADS, 1)
-gemm_tc2_kernel(const TcParams p, const __grid_constant__ CUtensorMap tm_a, const __grid_constant__ CUtensorMap tm_b) {
+gemm_tc2_kernel(const TcParams p, const __grid_constant__ CUtensorMap tm_a, const __grid_constant__ CUtensorMap tm_b,
+                const __grid_constant__ CUtensorMap tm_b64) {
     constexpr uint32_t kCols = 256u * NACC;
     using Cfg = TcCfg<false>;  // BK 64, 128-byte swizzle: the same operand layout
     constexpr int S = P2_STAGES;
@@ -172,6 +175,7 @@ gemm_tc2_kernel(const TcParams p, const __grid_constant__ CUtensorMap tm_a, cons
         fence_mbar_init();
         prefetch_tmap(&tm_a);
         prefetch_tmap(&tm_b);
+        prefetch_tmap(&tm_b64);
     }
     if (warp == 1) {
         // one warp of each CTA of the pair takes part in the allocation
@@ -201,22 +205,25 @@ gemm_tc2_kernel(const TcParams p, const __grid_constant__ CUtensorMap tm_a, cons
     } else if (warp == 0) {
         if (lane == 0) {
             // ---------------- producer: this CTA's halves of each k-block ----------------
-            P2Run run = p2_run(p);
             int s = 0;
             uint32_t ph = 0;
             uint32_t issued_parity[S];
             bool issued[S];
             for (int k = 0; k < S; ++k) issued[k] = false, issued_parity[k] = 0;
-            for (int64_t u = run.next; u < run.end && !abort_flag; ++u) {
-                const int64_t mt = u % p.tiles_m, nt = u / p.tiles_m;
+            for (int64_t u = blockIdx.x >> 1; u < p.nunits && !abort_flag; u += gridDim.x >> 1) {
+                const P2Unit w = p2_unit(u, p);
+                const int64_t mt = w.tile % p.tiles_m, nt = w.tile / p.tiles_m;
+                const int bh = w.half ? 64 : 128;  // this CTA's rows of B^T
                 const int32_t m0 = (int32_t)(p.row_lb + mt * P2_TILE + 128 * (int64_t)rank);
-                const int32_t n0 = (int32_t)(nt * P2_TILE + 128 * (int64_t)rank);
+                const int32_t n0 = (int32_t)(nt * P2_TILE + (w.half == 2 ? 128 : 0) + bh * (int64_t)rank);
+                const CUtensorMap* mb = w.half ? &tm_b64 : &tm_b;
+                const uint32_t bytes = 2u * (uint32_t)(P2_A_BYTES + (w.half ? P2_B_BYTES / 2 : P2_B_BYTES));
                 for (int kb = 0; kb < nkb; ++kb) {
                     if (!p2_wait(&empty[s], ph ^ 1u, p, &abort_flag)) break;
                     const uint32_t fb = pair_addr(&full[s], 0);
-                    if (leader) mbar_arrive_expect_tx(&full[s], 2u * P2_STAGE_BYTES);
+                    if (leader) mbar_arrive_expect_tx(&full[s], bytes);
                     tma_load_2d_pair(stage_a(s), &tm_a, fb, kb * P2_BK, m0);
-                    tma_load_2d_pair(stage_b(s), &tm_b, fb, kb * P2_BK, n0);
+                    tma_load_2d_pair(stage_b(s), mb, fb, kb * P2_BK, n0);
                     issued[s] = true;
                     issued_parity[s] = ph;
                     if (++s == S) s = 0, ph ^= 1u;
@@ -231,12 +238,12 @@ gemm_tc2_kernel(const TcParams p, const __grid_constant__ CUtensorMap tm_a, cons
     } else if (warp == 1) {
         if (lane == 0 && leader) {
             // ---------------- MMA issuer (leading CTA) ----------------
-            constexpr uint32_t idesc = pair_idesc();
-            P2Run run = p2_run(p);
+            constexpr uint32_t idesc_full = pair_idesc(), idesc_half = pair_idesc(P2_TILE / 2);
             int s = 0, acc = 0;
             uint32_t ph = 0, aph = 0;
             bool issued_any = false, ok = true;
-            for (int64_t u = run.next; u < run.end && ok && !abort_flag; ++u) {
+            for (int64_t u = blockIdx.x >> 1; u < p.nunits && ok && !abort_flag; u += gridDim.x >> 1) {
+                const uint32_t idesc = p2_unit(u, p).half ? idesc_half : idesc_full;
                 if (!p2_wait(&tempty[acc], aph ^ 1u, p, &abort_flag, true)) break;
                 tc_fence_after();
                 const uint32_t d_tmem = tmem_base + (uint32_t)(acc * TC_BN);
@@ -270,27 +277,30 @@ gemm_tc2_kernel(const TcParams p, const __grid_constant__ CUtensorMap tm_a, cons
     } else {
         // ---------------- epilogue: this CTA's 128 accumulator rows -> C ----------------
         const int q = warp & 3;               // TMEM lane quadrant this warp may access
-        const int quarter = (warp - 2) >> 2;  // which 64 of the 256 columns
-        P2Run run = p2_run(p);
+        const int quarter = (warp - 2) >> 2;  // which quarter of the tile's columns
         int acc = 0;
         uint32_t aph = 0;
         const bool v8_ok = (p.N % 8) == 0 && (reinterpret_cast<uintptr_t>(p.C) & 31) == 0;
         const uint32_t te0 = pair_addr(&tempty[0], 0), te1 = pair_addr(&tempty[NACC - 1], 0);
-        for (int64_t u = run.next; u < run.end && !abort_flag; ++u) {
-            const int64_t mt = u % p.tiles_m, nt = u / p.tiles_m;
+        for (int64_t u = blockIdx.x >> 1; u < p.nunits && !abort_flag; u += gridDim.x >> 1) {
+            const P2Unit w = p2_unit(u, p);
+            const int cw = w.half ? TC_EPI_COLS / 2 : TC_EPI_COLS;  // columns of this warp
+            const int64_t mt = w.tile % p.tiles_m, nt = w.tile / p.tiles_m;
             const int64_t row = p.row_lb + mt * P2_TILE + 128 * (int64_t)rank + 32 * q + lane;
-            const int64_t n0 = nt * P2_TILE + quarter * TC_EPI_COLS;
+            const int64_t n0 = nt * P2_TILE + (w.half == 2 ? 128 : 0) + quarter * cw;
             float* crow = row < p.row_ub ? p.C + row * p.N : nullptr;
-            const bool full_row = v8_ok && n0 + TC_EPI_COLS <= p.N;
+            const bool full_row = v8_ok && n0 + cw <= p.N;
             if (!p2_wait(&tfull[acc], aph, p, &abort_flag)) break;
             tc_fence_after();
-            const uint32_t ta = tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(quarter * TC_EPI_COLS) +
+            const uint32_t ta = tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(quarter * cw) +
                                 (uint32_t)(acc * TC_BN);
 #pragma unroll
             for (int h = 0; h < TC_EPI_COLS; h += 32) {
-                float v[32];
-                tmem_ld32(ta + (uint32_t)h, v);
-                if (crow) store_row(crow, n0 + h, p.N, full_row, v, 32);
+                if (h < cw) {
+                    float v[32];
+                    tmem_ld32(ta + (uint32_t)h, v);
+                    if (crow) store_row(crow, n0 + h, p.N, full_row, v, 32);
+                }
             }
             tc_fence_before();
             __syncwarp();
@@ -338,7 +348,7 @@ int gemm_tc2_max_clusters() {
 }
 
 cudaError_t launch_gemm_tc2(const TcParams& tp, int ctas, const CUtensorMap* a, const CUtensorMap* b,
-                            cudaStream_t s) {
+                            const CUtensorMap* b64, cudaStream_t s) {
     static bool configured = false;
     if (!configured) {
         const cudaError_t e =
@@ -346,7 +356,7 @@ cudaError_t launch_gemm_tc2(const TcParams& tp, int ctas, const CUtensorMap* a, 
         if (e != cudaSuccess) return e;
         configured = true;
     }
-    gemm_tc2_kernel<kNacc><<<ctas, TC_THREADS, P2_SMEM, s>>>(tp, *a, *b);
+    gemm_tc2_kernel<kNacc><<<ctas, TC_THREADS, P2_SMEM, s>>>(tp, *a, *b, *b64);
     return cudaGetLastError();
 }
 

@@ -231,6 +231,6 @@ __device__ __forceinline__ TcTiles tc_first(const TcParams& p) {
 size_t gemm_tc2_smem_bytes();
 int gemm_tc2_max_clusters();
 cudaError_t launch_gemm_tc2(const TcParams& tp, int ctas, const CUtensorMap* a, const CUtensorMap* b,
-                            cudaStream_t s);
+                            const CUtensorMap* b64, cudaStream_t s);
 
 }  // namespace upir

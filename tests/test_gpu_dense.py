@@ -198,6 +198,14 @@ def test_gemm_tc_pair_exact_small_integers(s, m, n, k):
     assert np.array_equal(run_gemm_tc(s, a, b, variant=2), O.gemm(a, b))
 
 
+def test_gemm_tc_pair_half_tiles_exact(s):
+    # 12 x 7 = 84 pair tiles: one wave on the resident clusters (fewer than 84
+    # on a B300), then the rest cut into 128-column halves; ragged edges
+    a = I.small_int_matrix(3055, 64, -8, 8, seed=9)
+    b = I.small_int_matrix(64, 1787, -8, 8, seed=10)
+    assert np.array_equal(run_gemm_tc(s, a, b), O.gemm(a, b))
+
+
 def test_gemm_tc_pair_matches_one_sm_kernel(s):
     # the same K16 MMA sequence per output; the tensor core's own (not
     # round-to-nearest) accumulation differs between M = 128 and M = 256
