@@ -170,6 +170,7 @@ upir_status build_persistent(upir_batch b) {
     P.partials = reinterpret_cast<Partial*>(base + off_partials);
     P.counter = reinterpret_cast<unsigned long long*>(base);
     P.exit_ticket = reinterpret_cast<unsigned*>(base + 8);
+    P.nregions = n;
     P.axpy_tile = b->axpy_tile;
     P.jac_rows = b->jac_rows;
     P.mv_rows = b->mv_rows;

@@ -121,7 +121,9 @@ __device__ __forceinline__ void axpy_tile(const BatchParams& P, const BatchRegio
     }
 }
 
-constexpr int kHaloW = kBatchJacCols + 8;                          // shared row: 4 + 128 + 4 columns
+// shared row: 4 + 128 + 4 columns, and up to 3 more for a row copied from
+// the 16-byte boundary before its first column
+constexpr int kHaloW = kBatchJacCols + 12;
 constexpr int kHaloFloats = (kBatchMaxJacRows + 2) * kHaloW;
 
 // Rows whose width is a multiple of 4 and 16-byte aligned buffers take the
@@ -130,10 +132,17 @@ __device__ __forceinline__ bool jacobi_vec(const BatchRegion& R) {
     return (R.cols & 3) == 0 && ((reinterpret_cast<uintptr_t>(R.in0) | reinterpret_cast<uintptr_t>(R.out)) & 15) == 0;
 }
 
+// Other widths with a 16-byte aligned input grid: each halo row is copied in
+// 16-byte pieces from the boundary at or before its first column, so the row
+// sits in shared memory shifted by ((row * cols + c0) mod 4) columns.
+__device__ __forceinline__ bool jacobi_shifted(const BatchRegion& R) {
+    return !jacobi_vec(R) && (reinterpret_cast<uintptr_t>(R.in0) & 15) == 0;
+}
+
 // Issue the asynchronous copy of tile t's halo into `halo` and commit it as
-// one group: 16-byte copies for 128-bit-capable regions, 4-byte copies for
-// the others (rows of any width or alignment); columns outside the grid are
-// zero-filled.  Shared column j holds grid column c0 - 4 + j, so the tile's
+// one group: 16-byte copies for 128-bit-capable regions and for shifted rows,
+// 4-byte copies for the others; columns outside the grid are zero-filled.
+// Unshifted, shared column j holds grid column c0 - 4 + j, so the tile's
 // first column sits on a 16-byte boundary.
 __device__ __forceinline__ void jacobi_halo_async(const BatchParams& P, const BatchRegion& R, int64_t t,
                                                   float* halo) {
@@ -144,7 +153,20 @@ __device__ __forceinline__ void jacobi_halo_async(const BatchParams& P, const Ba
     // a warp per halo row; a lane's columns advance by 32 copies at a time
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = kBatchUnits / 32;
     const int64_t cfirst = c0 - 4;  // grid column of shared column 0
-    if (jacobi_vec(R)) {
+    if (jacobi_shifted(R)) {
+        const int64_t total = R.rows * cols;  // elements of the grid
+        for (int i = warp; i < nr + 2; i += nw) {
+            const int64_t g = (r0 - 1 + i) * cols + cfirst;  // grid column c0 - 4 of halo row i
+            const int64_t base = g & ~(int64_t)3;
+            const uint32_t srow = smem_u32(halo + i * kHaloW);
+            for (int q = lane; q < kHaloW / 4; q += 32) {
+                const int64_t idx = base + 4 * q;
+                const int64_t nv = idx < 0 ? 0 : min(max(total - idx, (int64_t)0), (int64_t)4);
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;"
+                             ::"r"(srow + 16u * q), "l"(nv ? R.in0 + idx : R.in0), "r"((int)(4 * nv)) : "memory");
+            }
+        }
+    } else if (jacobi_vec(R)) {
         for (int i = warp; i < nr + 2; i += nw) {
             const float* grow = R.in0 + (r0 - 1 + i) * cols;
             const uint32_t srow = smem_u32(halo + i * kHaloW);
@@ -221,13 +243,60 @@ __device__ __forceinline__ float jacobi_rows(const float* cen, float* out, int i
     return racc;
 }
 
+// A Jacobi region's max (min) residual over its tiles, kept as an unsigned
+// key in the region's slot with a fire-and-forget atomic max: the key of a
+// non-NaN float orders like the float (sign bit flipped for non-negative
+// values, all bits flipped for negative ones), complemented for min; 0 means
+// no tile has reported.  The last team to finish folds each slot into the
+// reduction variable (maxNum / minNum, NaN residuals ignored) and clears it.
+__device__ __forceinline__ unsigned resid_key(float v, int op) {
+    const unsigned b = __float_as_uint(v);
+    const unsigned k = (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+    return op == UPIR_RED_MIN ? ~k : k;
+}
+
+__device__ __forceinline__ float resid_value(unsigned key, int op) {
+    const unsigned k = op == UPIR_RED_MIN ? ~key : key;
+    return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
+}
+
+// The shifted-row form: lane tx takes columns c0 + tx + 32 j (j = 0..3), so
+// 32-bit shared loads from rows of any shift and the 32-bit global stores
+// stay unit-stride across the warp.
+template <int FOP>
+__device__ __forceinline__ float jacobi_rows_shifted(const float* halo, float* outb, int64_t r0, int nr, int ty,
+                                                     int nty, int tx, int64_t c0, int64_t cols) {
+    constexpr int HW = kHaloW;
+    float racc = FOP == UPIR_RED_MIN ? __int_as_float(0x7f800000) : -__int_as_float(0x7f800000);
+    const uint32_t cq = (uint32_t)cols & 3u;
+    const uint32_t sh0 = ((uint32_t)(r0 - 1) * cq + (uint32_t)c0) & 3u;  // shift of halo row 0
+    for (int i = ty; i < nr; i += nty) {
+        const float* rn = halo + i * HW + ((sh0 + (uint32_t)i * cq) & 3u) + 4;
+        const float* rm = halo + (i + 1) * HW + ((sh0 + (uint32_t)(i + 1) * cq) & 3u) + 4;
+        const float* rs = halo + (i + 2) * HW + ((sh0 + (uint32_t)(i + 2) * cq) & 3u) + 4;
+        float* orow = outb + (r0 + i) * cols + c0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int q = tx + 32 * j;
+            const int64_t c = c0 + q;
+            const float cv = rm[q];
+            const float v = __fmul_rn(0.25f, __fadd_rn(__fadd_rn(rn[q], rs[q]), __fadd_rn(rm[q - 1], rm[q + 1])));
+            if (c >= 1 && c <= cols - 2) {
+                __stcs(orow + q, v);
+                if (FOP) racc = fold(racc, fabsf(__fsub_rn(v, cv)), FOP);
+            }
+        }
+    }
+    return racc;
+}
+
 __device__ __forceinline__ void jacobi_tile(const BatchParams& P, const BatchRegion& R, int64_t t, float* halo,
                                             bool staged, const BatchRegion* next, int64_t tn, float* halo_next) {
     constexpr int HW = kHaloW;
     // the region's fields, read once (the output stores could alias them)
     const int64_t cols = R.cols, tiles_c = R.tiles_c, lb = R.lb, trip = R.trip;
     float* const outb = R.out;
-    float* const fvar = R.fvar;
+    unsigned* const rslot = R.ticket;
     const int fop = R.fop;
     const bool vec = jacobi_vec(R);
     const int64_t band = t / tiles_c, tc = t - band * tiles_c;
@@ -249,14 +318,24 @@ __device__ __forceinline__ void jacobi_tile(const BatchParams& P, const BatchReg
     const float* cen = halo + (ty + 1) * HW + 4 + 4 * tx;
     float* out = outb + (r0 + ty) * cols + c;
     const int64_t ostep = (int64_t)nty * cols;
-    if (fop == UPIR_RED_MAX) {
+    if (jacobi_shifted(R)) {
+        if (fop == UPIR_RED_MAX || fop == UPIR_RED_MIN) {
+            const float r = fop == UPIR_RED_MAX
+                                ? jacobi_rows_shifted<UPIR_RED_MAX>(halo, outb, r0, nr, ty, nty, tx, c0, cols)
+                                : jacobi_rows_shifted<UPIR_RED_MIN>(halo, outb, r0, nr, ty, nty, tx, c0, cols);
+            const float b = block_fold(r, fop);
+            if (threadIdx.x == 0 && !isnan(b)) atomicMax(rslot, resid_key(b, fop));
+        } else {
+            jacobi_rows_shifted<0>(halo, outb, r0, nr, ty, nty, tx, c0, cols);
+        }
+    } else if (fop == UPIR_RED_MAX) {
         const float r = jacobi_rows<UPIR_RED_MAX>(cen, out, ty, nr, nty, ostep, inside, full, c, cols);
         const float b = block_fold(r, UPIR_RED_MAX);
-        if (threadIdx.x == 0) atomic_fold_minmax(fvar, b, UPIR_RED_MAX);
+        if (threadIdx.x == 0 && !isnan(b)) atomicMax(rslot, resid_key(b, UPIR_RED_MAX));
     } else if (fop == UPIR_RED_MIN) {
         const float r = jacobi_rows<UPIR_RED_MIN>(cen, out, ty, nr, nty, ostep, inside, full, c, cols);
         const float b = block_fold(r, UPIR_RED_MIN);
-        if (threadIdx.x == 0) atomic_fold_minmax(fvar, b, UPIR_RED_MIN);
+        if (threadIdx.x == 0 && !isnan(b)) atomicMax(rslot, resid_key(b, UPIR_RED_MIN));
     } else {
         jacobi_rows<0>(cen, out, ty, nr, nty, ostep, inside, full, c, cols);
     }
@@ -336,6 +415,17 @@ __global__ void __launch_bounds__(kBatchUnits, 4) batch_persistent_kernel(const 
         if (last_team) {
             *P.exit_ticket = 0;
             *P.counter = 0;
+        }
+    }
+    __syncthreads();
+    if (last_team) {
+        // fold the Jacobi regions' residual keys into their variables
+        __threadfence();
+        for (int i = threadIdx.x; i < P.nregions; i += blockDim.x) {
+            const BatchRegion& R = P.regions[i];
+            if (R.op != BOP_JACOBI || !R.fop) continue;
+            const unsigned key = atomicExch(R.ticket, 0u);
+            if (key) atomic_fold_minmax(R.fvar, resid_value(key, R.fop), R.fop);
         }
     }
 }

@@ -189,7 +189,7 @@ struct BatchRegion {
     int64_t tiles_c;    // JACOBI: tiles per row band
     int64_t slot0;      // AXPY: first partial slot
     float* fvar;        // reduction variable, or nullptr
-    unsigned* ticket;   // AXPY with a reduction: tiles finished so far
+    unsigned* ticket;   // AXPY with a reduction: tiles finished so far; JACOBI: residual key (0: none yet)
 };
 
 struct BatchParams {
@@ -199,6 +199,7 @@ struct BatchParams {
     Partial* partials;
     unsigned long long* counter;   // next work item
     unsigned* exit_ticket;         // teams finished
+    int nregions;
     int axpy_tile;                 // AXPY iterations per tile (multiple of 1024)
     int jac_rows;                  // JACOBI rows per tile (tiles are 128 columns wide)
     int mv_rows;                   // MATVEC rows per tile

@@ -197,6 +197,40 @@ def test_batch_of_regions_equals_each_region(s, mode, tune):
             assert np.linalg.norm(out - want) <= 1e-5 * np.linalg.norm(want)
 
 
+@pytest.mark.parametrize("op,init", [(U.UPIR_RED_MAX, -np.inf), (U.UPIR_RED_MAX, 0.3), (U.UPIR_RED_MAX, np.nan),
+                                     (U.UPIR_RED_MIN, np.inf), (U.UPIR_RED_MIN, 1e-6)])
+def test_persistent_batch_jacobi_residual_ops(s, op, init):
+    """Jacobi regions of widths of every residue mod 4 in one persistent
+    batch, each residual folded over its tiles and then into the variable's
+    prior value (maxNum / minNum)."""
+    sides = [(67, 64), (130, 301), (45, 258), (33, 131), (200, 75)]
+    regions, checks = [], []
+    for k, (rows, cols) in enumerate(sides):
+        u0 = I.jacobi_grid(rows, cols, seed=20 + k)
+        a, b = u0.copy(), u0.copy()
+        res = np.array([init], np.float32)
+        ha, hb, hr = s.map(a, U.UPIR_MAP_TO), s.map(b, U.UPIR_MAP_TOFROM), s.map(res, U.UPIR_MAP_TOFROM)
+        r = U.upir_spmd_region(s.ctx, 0, 0)
+        U.upir_loop_checked(s.ctx, r, U.make_loop_desc(**jacobi_loop(ha, hb, rows, cols, hres=hr, op=op)))
+        regions.append(r)
+        checks.append((u0, b, res, (ha, hb, hr)))
+    bt = U.upir_batch_create(s.ctx, regions, U.UPIR_BATCH_PERSISTENT)
+    U.upir_batch_submit(bt)
+    U.upir_ctx_wait(s.ctx)
+    U.upir_batch_destroy(bt)
+    for r in regions:
+        U.upir_region_destroy(r)
+    for u0, b, res, hs in checks:
+        for h in hs:
+            s.unmap(h)
+        v, _ = O.jacobi_sweep_f32(u0)
+        assert np.array_equal(b, v)
+        d = np.abs(v[1:-1, 1:-1] - u0[1:-1, 1:-1])
+        r = float(d.max() if op == U.UPIR_RED_MAX else d.min())
+        want = r if np.isnan(init) else (max(init, r) if op == U.UPIR_RED_MAX else min(init, r))
+        assert float(res[0]) == np.float32(want)
+
+
 def test_persistent_batch_rejects_unsupported_regions(s):
     x = np.ones(64, np.float32)
     hx, hy = s.map(x, U.UPIR_MAP_TO), s.map(x.copy(), U.UPIR_MAP_TOFROM)
