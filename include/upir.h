@@ -288,7 +288,14 @@ typedef struct {
     int64_t  index;
 } upir_reduction;
 
-/* Tuning hints (§2.4 "UPIR extension": key-value pairs).  Unknown keys: EINVAL. */
+/* Tuning hints (§2.4 "UPIR extension": key-value pairs).  Unknown keys: EINVAL.
+ * UPIR_HINT_VARIANT values: JACOBI5 1 = the per-point kernel (a unit per
+ * point) instead of the tiled one (2D TMA boxes, or one TMA copy per halo row
+ * for widths that are not a multiple of 4); GEMM_BF16 1 = one SM per 128 x 256
+ * tile, 2 = CTA pairs (tcgen05 cta_group::2, 256 x 256 tiles; EUNSUPPORTED
+ * with explicit teams, a chunk, a TILE_M hint or when no two-CTA cluster
+ * fits), 0 = the planner's choice (pairs when every resident cluster gets a
+ * tile). */
 typedef enum {
     UPIR_HINT_VARIANT   = 1, /* kernel variant of the body (body-specific, 0 = default)       */
     UPIR_HINT_TILE_M    = 2, /* tile rows (JACOBI5 tiled variant, GEMM)                       */
