@@ -12,15 +12,20 @@ namespace upir {
 namespace {
 
 constexpr int BM = 128, BN = 128, BK = 16;
+constexpr int AP = BM + 4;  // A tile pitch: the transposing stores of 16 k per row hit distinct banks
 
-__global__ void __launch_bounds__(256) gemm_f32_kernel(const GemmParams p) {
-    __shared__ __align__(16) float As[2][BK][BM];
+__global__ void __launch_bounds__(256, 2) gemm_f32_kernel(const GemmParams p) {
+    __shared__ __align__(16) float As[2][BK][AP];
     __shared__ __align__(16) float Bs[2][BK][BN];
     const int t = threadIdx.x;
     const int tx = t % 16, ty = t / 16;
     const int64_t rows = p.row_ub - p.row_lb;
     const int64_t tiles_m = (rows + BM - 1) / BM, tiles_n = (p.N + BN - 1) / BN;
     const int64_t ntiles = tiles_m * tiles_n;
+    // 128-bit loads of A rows (along k) and B rows (along n) when rows start
+    // on 16-byte boundaries; element loads otherwise and at the edges
+    const bool vec_a = (p.K & 3) == 0 && (reinterpret_cast<uintptr_t>(p.A) & 15) == 0;
+    const bool vec_b = (p.N & 3) == 0 && (reinterpret_cast<uintptr_t>(p.B) & 15) == 0;
 
     auto do_tile = [&](int64_t tile) {
         const int64_t m0 = p.row_lb + (tile / tiles_n) * BM;
@@ -31,25 +36,43 @@ __global__ void __launch_bounds__(256) gemm_f32_kernel(const GemmParams p) {
 #pragma unroll
             for (int j = 0; j < 8; ++j) acc[i][j] = 0.0f;
 
-        float ra[8], rb[8];
+        // per k-tile each thread moves two groups of 4 of A (row f / 4, k
+        // 4 (f % 4) ..) and two of B (k f / 32, columns 4 (f % 32) ..), f = t + 256 i
+        float4 ra[2], rb[2];
         auto load_regs = [&](int64_t k0) {
 #pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const int idx = t + i * 256;
-                const int r = idx / BK, k = idx % BK;  // A: 128 rows x 16 k
-                const int64_t gm = m0 + r, gk = k0 + k;
-                ra[i] = (gm < p.row_ub && gk < p.K) ? p.A[gm * p.K + gk] : 0.0f;
-                const int kb = idx / BN, c = idx % BN;  // B: 16 k x 128 cols
-                const int64_t gkb = k0 + kb, gn = n0 + c;
-                rb[i] = (gkb < p.K && gn < p.N) ? p.B[gkb * p.N + gn] : 0.0f;
+            for (int i = 0; i < 2; ++i) {
+                const int f = t + i * 256;
+                const int64_t gm = m0 + (f >> 2), gk = k0 + 4 * (f & 3);
+                const float* pa = p.A + gm * p.K + gk;
+                if (vec_a && gm < p.row_ub && gk + 3 < p.K) {
+                    ra[i] = __ldg(reinterpret_cast<const float4*>(pa));
+                } else {
+                    const bool rin = gm < p.row_ub;
+                    ra[i] = make_float4(rin && gk < p.K ? pa[0] : 0.f, rin && gk + 1 < p.K ? pa[1] : 0.f,
+                                        rin && gk + 2 < p.K ? pa[2] : 0.f, rin && gk + 3 < p.K ? pa[3] : 0.f);
+                }
+                const int64_t gkb = k0 + (f >> 5), gn = n0 + 4 * (f & 31);
+                const float* pb = p.B + gkb * p.N + gn;
+                if (vec_b && gkb < p.K && gn + 3 < p.N) {
+                    rb[i] = __ldg(reinterpret_cast<const float4*>(pb));
+                } else {
+                    const bool kin = gkb < p.K;
+                    rb[i] = make_float4(kin && gn < p.N ? pb[0] : 0.f, kin && gn + 1 < p.N ? pb[1] : 0.f,
+                                        kin && gn + 2 < p.N ? pb[2] : 0.f, kin && gn + 3 < p.N ? pb[3] : 0.f);
+                }
             }
         };
         auto store_regs = [&](int buf) {
 #pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const int idx = t + i * 256;
-                As[buf][idx % BK][idx / BK] = ra[i];
-                Bs[buf][idx / BN][idx % BN] = rb[i];
+            for (int i = 0; i < 2; ++i) {
+                const int f = t + i * 256;
+                const int r = f >> 2, kq = 4 * (f & 3);
+                As[buf][kq + 0][r] = ra[i].x;
+                As[buf][kq + 1][r] = ra[i].y;
+                As[buf][kq + 2][r] = ra[i].z;
+                As[buf][kq + 3][r] = ra[i].w;
+                *reinterpret_cast<float4*>(&Bs[buf][f >> 5][4 * (f & 31)]) = rb[i];
             }
         };
 
