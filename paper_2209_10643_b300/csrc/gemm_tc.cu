@@ -431,13 +431,12 @@ upir_status plan_gemm_tc(upir_region r, LoopRec& lp, int64_t M, int64_t N, int64
         }
         chunk_eff = 1;
     }
-    // The CTA-pair kernel (plain bfloat16, one accumulation segment, planner
-    // geometry) when its 256 x 256 tiles give every resident cluster at least
-    // one; UPIR_HINT_VARIANT 1 keeps the one-SM kernel, 2 asks for pairs.
-    if (lp.variant == 2 && (x3 || lp.tile_m != 0 || r->teams || lp.chunk != 0))
-        return fail(ctx, UPIR_EUNSUPPORTED,
-                    "upir_loop: the CTA-pair GEMM takes GEMM_BF16 with planner teams, chunk 0 and one K segment");
-    if (!x3 && lp.tile_m == 0 && !r->teams && lp.chunk == 0 && lp.variant != 1 && tp.ntiles > 0) {
+    // The CTA-pair kernel (planner geometry) when its 256 x 256 tiles give
+    // every resident cluster at least one; UPIR_HINT_VARIANT 1 keeps the
+    // one-SM kernel, 2 asks for pairs.
+    if (lp.variant == 2 && (r->teams || lp.chunk != 0))
+        return fail(ctx, UPIR_EUNSUPPORTED, "upir_loop: the CTA-pair GEMM takes planner teams and chunk 0");
+    if (!r->teams && lp.chunk == 0 && lp.variant != 1 && tp.ntiles > 0) {
         const int64_t tm2 = ceil_div(lp.trip, 256), tn2 = ceil_div(N, 256), nt2 = tm2 * tn2;
         const int maxc = gemm_tc2_max_clusters();
         if (maxc <= 0 && lp.variant == 2)
@@ -490,10 +489,11 @@ upir_status plan_gemm_tc(upir_region r, LoopRec& lp, int64_t M, int64_t N, int64
                             lp.bufs[x3 ? na + 1 : na]->dev, lp.bufs[na]->dev, lp.bufs[x3 ? na + 1 : na]->dev};
     const uint64_t rows[6] = {(uint64_t)M, (uint64_t)M, (uint64_t)N, (uint64_t)N, (uint64_t)N, (uint64_t)N};
     const uint32_t box_rows[6] = {TC_BM, TC_BM, TC_BN, TC_BN, TC_BN / 2, TC_BN / 2};
+    // the CTA-pair kernel: every operand box is 128 rows (a CTA's share),
+    // the last two maps 64 rows of B^T for half tiles
+    const uint32_t pair_rows[6] = {128, 128, 128, 128, 64, 64};
     for (int i = 0; i < 6; ++i) {
-        // the CTA-pair kernel's half tiles take 64 rows of B^T per CTA (the
-        // sixth map, unused by the plain bfloat16 one-SM kernel)
-        const uint32_t br = (tp.pair && i == 5) ? 64u : box_rows[i];
+        const uint32_t br = tp.pair ? pair_rows[i] : box_rows[i];
         upir_status s2 = encode_tmap_2d(ctx, &lp.tmap[i], bases[i], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
                                         (uint64_t)K, rows[i], (uint32_t)bk, br, bk * 2);
         if (s2 != UPIR_OK) return s2;
@@ -509,7 +509,7 @@ cudaError_t launch_gemm_tc_loop(upir_ctx, LoopRec& lp, cudaStream_t s) {
     const int nkb = (int)((tp.K + (lp.body == UPIR_BODY_GEMM_BF16X3 ? TcCfg<true>::BK : TcCfg<false>::BK) - 1) /
                           (lp.body == UPIR_BODY_GEMM_BF16X3 ? TcCfg<true>::BK : TcCfg<false>::BK));
     const bool mseg = tp.seg_kb < nkb;
-    if (tp.pair) return launch_gemm_tc2(tp, lp.teams, &m[0], &m[4], &m[5], s);
+    if (tp.pair) return launch_gemm_tc2(tp, lp.teams, lp.body == UPIR_BODY_GEMM_BF16X3, mseg, m, s);
     if (lp.body == UPIR_BODY_GEMM_BF16X3)
         return mseg ? tc_launch<true, true>(tp, lp.teams, m, s) : tc_launch<true, false>(tp, lp.teams, m, s);
     return mseg ? tc_launch<false, true>(tp, lp.teams, m, s) : tc_launch<false, false>(tp, lp.teams, m, s);

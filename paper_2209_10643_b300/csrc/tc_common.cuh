@@ -230,7 +230,6 @@ __device__ __forceinline__ TcTiles tc_first(const TcParams& p) {
 
 size_t gemm_tc2_smem_bytes();
 int gemm_tc2_max_clusters();
-cudaError_t launch_gemm_tc2(const TcParams& tp, int ctas, const CUtensorMap* a, const CUtensorMap* b,
-                            const CUtensorMap* b64, cudaStream_t s);
+cudaError_t launch_gemm_tc2(const TcParams& tp, int ctas, bool x3, bool mseg, const CUtensorMap* m, cudaStream_t s);
 
 }  // namespace upir

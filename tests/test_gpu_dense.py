@@ -136,7 +136,7 @@ def test_split_bf16_bit_exact(s, rows, cols, transpose):
 
 # --- tensor-core GEMM (tcgen05): bfloat16 and split-bfloat16 -----------------------
 
-def run_gemm_tc(s, a, b, x3=False, teams=0, chunk=0, lb=0, ub=None, variant=0):
+def run_gemm_tc(s, a, b, x3=False, teams=0, chunk=0, lb=0, ub=None, variant=0, seg_kb=0):
     m, k = a.shape
     n = b.shape[1]
     ah, al = np.zeros(m * k, np.uint16), np.zeros(m * k, np.uint16)
@@ -150,7 +150,7 @@ def run_gemm_tc(s, a, b, x3=False, teams=0, chunk=0, lb=0, ub=None, variant=0):
            dict(lb=0, ub=k, body=U.UPIR_BODY_SPLIT_BF16, bufs=[hb, hbh, hbl], scalars=[k, n, 1])])
     body = U.UPIR_BODY_GEMM_BF16X3 if x3 else U.UPIR_BODY_GEMM_BF16
     bufs = [hah, hal, hbh, hbl, hc] if x3 else [hah, hbh, hc]
-    hints = [(U.UPIR_HINT_VARIANT, variant)] if variant else []
+    hints = ([(U.UPIR_HINT_VARIANT, variant)] if variant else []) + ([(U.UPIR_HINT_TILE_M, seg_kb)] if seg_kb else [])
     s.run([dict(lb=lb, ub=m if ub is None else ub, collapse=2, body=body, bufs=bufs, scalars=[m, n, k],
                 chunk=chunk, hints=hints)], teams, 0)
     for h in (ha, hb, hah, hal, hbh, hbl, hc):
@@ -191,11 +191,28 @@ def test_gemm_tc_k_split_exact_and_repeatable(s, x3):
 # The CTA-pair kernel (tcgen05 cta_group::2, 256 x 256 tiles): the planner's
 # choice for large bfloat16 GEMMs, forced here (variant 2) on small and ragged
 # shapes; variant 1 is the one-SM kernel.
+@pytest.mark.parametrize("x3", [False, True])
 @pytest.mark.parametrize("m,n,k", [(200, 300, 136), (2382, 1948, 64), (513, 257, 72), (256, 256, 64), (1, 9, 8)])
-def test_gemm_tc_pair_exact_small_integers(s, m, n, k):
+def test_gemm_tc_pair_exact_small_integers(s, m, n, k, x3):
     a = I.small_int_matrix(m, k, -8, 8, seed=7)
     b = I.small_int_matrix(k, n, -8, 8, seed=8)
-    assert np.array_equal(run_gemm_tc(s, a, b, variant=2), O.gemm(a, b))
+    assert np.array_equal(run_gemm_tc(s, a, b, x3, variant=2), O.gemm(a, b))
+
+
+@pytest.mark.parametrize("x3,seg_kb", [(False, 3), (True, 5), (True, 32)])
+def test_gemm_tc_pair_k_segments(s, x3, seg_kb):
+    # K in accumulation segments of seg_kb k-blocks (64 or 32 deep), the
+    # segments added in FP32 by the epilogue; the last segment is partial
+    a = I.small_int_matrix(520, 1000, -8, 8, seed=11)
+    b = I.small_int_matrix(1000, 300, -8, 8, seed=12)
+    assert np.array_equal(run_gemm_tc(s, a, b, x3, variant=2, seg_kb=seg_kb), O.gemm(a, b))
+    a, b = I.gemm_inputs(512, 512, 2048)
+    c = run_gemm_tc(s, a, b, x3, variant=2, seg_kb=seg_kb)
+    absab = np.abs(a.astype(np.float64)) @ np.abs(b.astype(np.float64))
+    if x3:
+        check_tc(c, O.gemm(a, b), absab, 2048)
+    else:
+        check_tc(c, O.gemm_bf16(a, b), absab, 2048, tc_accum_tol(2048))
 
 
 def test_gemm_tc_pair_half_tiles_exact(s):
