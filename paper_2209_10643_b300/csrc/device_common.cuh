@@ -541,6 +541,16 @@ __device__ __forceinline__ void tma_load_1d(void* smem_dst, const void* tmap, ui
         : "memory");
 }
 
+// Ask for [p, p + bytes) to be brought into L2 (a bulk prefetch: no
+// registers, no completion to wait for).  The range is shrunk to whole
+// 16-byte units inside it, as the instruction requires.
+__device__ __forceinline__ void prefetch_l2_range(const void* p, size_t bytes) {
+    const uintptr_t a = (reinterpret_cast<uintptr_t>(p) + 15) & ~uintptr_t(15);
+    const uintptr_t e = (reinterpret_cast<uintptr_t>(p) + bytes) & ~uintptr_t(15);
+    if (e > a)
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a), "r"((uint32_t)(e - a)) : "memory");
+}
+
 __device__ __forceinline__ void prefetch_tmap(const void* tmap) {
     asm volatile("prefetch.tensormap [%0];" ::"l"(tmap) : "memory");
 }
