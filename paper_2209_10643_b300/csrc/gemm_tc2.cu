@@ -353,7 +353,7 @@ struct P2Cfg {
 // per 16-deep step (A_hi B_hi, A_hi B_lo, A_lo B_hi).  MSEG: K runs in
 // segments of seg_kb k-blocks, each into a fresh accumulator, added in FP32
 // registers by the epilogue in segment order.
-template <bool X3, bool MSEG>
+template <bool X3, bool MSEG, int KS>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(TC_THREADS, 1)
 gemm_tc2_kernel(const TcParams p, const __grid_constant__ CUtensorMap tm_ah, const __grid_constant__ CUtensorMap tm_al,
                 const __grid_constant__ CUtensorMap tm_bh, const __grid_constant__ CUtensorMap tm_bl,
@@ -362,7 +362,7 @@ gemm_tc2_kernel(const TcParams p, const __grid_constant__ CUtensorMap tm_ah, con
     using PC = P2Cfg<X3>;
     constexpr int NACC = 2;
     constexpr uint32_t kCols = 256u * NACC;
-    constexpr int S = P2_STAGES;
+    constexpr int S = P2_STAGES / KS;  // a stage holds KS consecutive k-blocks
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t full[S], empty[S], tfull[NACC], tempty[NACC], mma_done;
     __shared__ uint32_t tmem_base_sh;
@@ -372,8 +372,8 @@ gemm_tc2_kernel(const TcParams p, const __grid_constant__ CUtensorMap tm_ah, con
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t rank = cluster_rank();
     const bool leader = rank == 0;
-    const int nkb = (int)((p.K + PC::BK - 1) / PC::BK);
-    const int seg_kb = MSEG ? p.seg_kb : nkb;
+    const int nst = (int)((p.K + PC::BK * KS - 1) / (PC::BK * KS));  // stages along K
+    const int seg_st = MSEG ? p.seg_kb / KS : nst;                     // stages per K segment
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) {
@@ -410,9 +410,9 @@ gemm_tc2_kernel(const TcParams p, const __grid_constant__ CUtensorMap tm_ah, con
     const bool pair_bad = peer_base != tmem_base;
     if (pair_bad && threadIdx.x == 0) atomicCAS(p.err_word, 0, UPIR_ERR_WAIT_TIMEOUT);
 
-    // stage layout: A_hi [, A_lo], B_hi [, B_lo]
-    auto stage_a = [&](int s) { return ring + (size_t)s * P2_STAGE_BYTES; };
-    auto stage_b = [&](int s) { return ring + (size_t)s * P2_STAGE_BYTES + PC::A_BYTES * (X3 ? 2 : 1); };
+    // stage layout: KS slices of A_hi [, A_lo], B_hi [, B_lo], one k-block each
+    auto stage_a = [&](int s, int j) { return ring + ((size_t)s * KS + j) * P2_STAGE_BYTES; };
+    auto stage_b = [&](int s, int j) { return stage_a(s, j) + PC::A_BYTES * (X3 ? 2 : 1); };
 
     if (pair_bad) {
         // nothing to do: both CTAs go straight to the teardown
@@ -433,19 +433,22 @@ gemm_tc2_kernel(const TcParams p, const __grid_constant__ CUtensorMap tm_ah, con
                 const CUtensorMap* mbh = w.half ? &tm_bh64 : &tm_bh;
                 const CUtensorMap* mbl = w.half ? &tm_bl64 : &tm_bl;
                 const uint32_t bytes =
-                    2u * (uint32_t)((X3 ? 2 : 1) * (PC::A_BYTES + (w.half ? PC::B_BYTES / 2 : PC::B_BYTES)));
-                for (int kb = 0; kb < nkb; ++kb) {
+                    2u * KS * (uint32_t)((X3 ? 2 : 1) * (PC::A_BYTES + (w.half ? PC::B_BYTES / 2 : PC::B_BYTES)));
+                for (int kst = 0; kst < nst; ++kst) {
                     if (!p2_wait(&empty[s], ph ^ 1u, p, &abort_flag)) break;
                     const uint32_t fb = pair_addr(&full[s], 0);
                     if (leader) mbar_arrive_expect_tx(&full[s], bytes);
-                    const int32_t k0 = kb * PC::BK;
-                    unsigned char* a = stage_a(s);
-                    unsigned char* b = stage_b(s);
-                    tma_load_2d_pair(a, &tm_ah, fb, k0, m0);
-                    tma_load_2d_pair(b, mbh, fb, k0, n0);
-                    if (X3) {
-                        tma_load_2d_pair(a + PC::A_BYTES, &tm_al, fb, k0, m0);
-                        tma_load_2d_pair(b + PC::B_BYTES, mbl, fb, k0, n0);
+#pragma unroll
+                    for (int j = 0; j < KS; ++j) {
+                        const int32_t k0 = (kst * KS + j) * PC::BK;
+                        unsigned char* a = stage_a(s, j);
+                        unsigned char* b = stage_b(s, j);
+                        tma_load_2d_pair(a, &tm_ah, fb, k0, m0);
+                        tma_load_2d_pair(b, mbh, fb, k0, n0);
+                        if (X3) {
+                            tma_load_2d_pair(a + PC::A_BYTES, &tm_al, fb, k0, m0);
+                            tma_load_2d_pair(b + PC::B_BYTES, mbl, fb, k0, n0);
+                        }
                     }
                     issued[s] = true;
                     issued_parity[s] = ph;
@@ -467,7 +470,7 @@ gemm_tc2_kernel(const TcParams p, const __grid_constant__ CUtensorMap tm_ah, con
             bool issued_any = false, ok = true;
             for (int64_t u = blockIdx.x >> 1; u < p.nunits && ok && !abort_flag; u += gridDim.x >> 1) {
                 const uint32_t idesc = p2_unit(u, p).half ? idesc_half : idesc_full;
-                for (int kb0 = 0; kb0 < nkb && ok; kb0 += seg_kb) {
+                for (int kb0 = 0; kb0 < nst && ok; kb0 += seg_st) {
                     // one K segment into a fresh accumulator buffer
                     if (!p2_wait(&tempty[acc], aph ^ 1u, p, &abort_flag, true)) {
                         ok = false;
@@ -475,24 +478,27 @@ gemm_tc2_kernel(const TcParams p, const __grid_constant__ CUtensorMap tm_ah, con
                     }
                     tc_fence_after();
                     const uint32_t d_tmem = tmem_base + (uint32_t)(acc * TC_BN);
-                    const int kb1 = min(kb0 + seg_kb, nkb);
+                    const int kb1 = min(kb0 + seg_st, nst);
                     for (int kb = kb0; kb < kb1; ++kb) {
                         if (!p2_wait(&full[s], ph, p, &abort_flag, true)) {
                             ok = false;
                             break;
                         }
                         tc_fence_after();
-                        const uint32_t a = smem_u32(stage_a(s)), b = smem_u32(stage_b(s));
 #pragma unroll
-                        for (int k = 0; k < PC::BK / 16; ++k) {
-                            const uint32_t koff = (uint32_t)k * 32u;  // 16 bfloat16 along K
-                            mma_pair(d_tmem, smem_desc<Cfg>(a + koff), smem_desc<Cfg>(b + koff), idesc,
-                                     (kb > kb0 || k > 0) ? 1u : 0u);
-                            if (X3) {
-                                mma_pair(d_tmem, smem_desc<Cfg>(a + koff), smem_desc<Cfg>(b + PC::B_BYTES + koff),
-                                         idesc, 1u);
-                                mma_pair(d_tmem, smem_desc<Cfg>(a + PC::A_BYTES + koff), smem_desc<Cfg>(b + koff),
-                                         idesc, 1u);
+                        for (int j = 0; j < KS; ++j) {
+                            const uint32_t a = smem_u32(stage_a(s, j)), b = smem_u32(stage_b(s, j));
+#pragma unroll
+                            for (int k = 0; k < PC::BK / 16; ++k) {
+                                const uint32_t koff = (uint32_t)k * 32u;  // 16 bfloat16 along K
+                                mma_pair(d_tmem, smem_desc<Cfg>(a + koff), smem_desc<Cfg>(b + koff), idesc,
+                                         (kb > kb0 || j > 0 || k > 0) ? 1u : 0u);
+                                if (X3) {
+                                    mma_pair(d_tmem, smem_desc<Cfg>(a + koff),
+                                             smem_desc<Cfg>(b + PC::B_BYTES + koff), idesc, 1u);
+                                    mma_pair(d_tmem, smem_desc<Cfg>(a + PC::A_BYTES + koff),
+                                             smem_desc<Cfg>(b + koff), idesc, 1u);
+                                }
                             }
                         }
                         issued_any = true;
@@ -518,7 +524,7 @@ gemm_tc2_kernel(const TcParams p, const __grid_constant__ CUtensorMap tm_ah, con
         uint32_t aph = 0;
         const bool v8_ok = (p.N % 8) == 0 && (reinterpret_cast<uintptr_t>(p.C) & 31) == 0;
         const uint32_t te0 = pair_addr(&tempty[0], 0), te1 = pair_addr(&tempty[NACC - 1], 0);
-        const int nseg = (nkb + seg_kb - 1) / seg_kb;
+        const int nseg = (nst + seg_st - 1) / seg_st;
         bool ok = true;
         for (int64_t u = blockIdx.x >> 1; u < p.nunits && ok && !abort_flag; u += gridDim.x >> 1) {
             const P2Unit w = p2_unit(u, p);
@@ -585,18 +591,26 @@ gemm_tc2_kernel(const TcParams p, const __grid_constant__ CUtensorMap tm_ah, con
 
 // The large shared-memory window, set once per instantiation; returns the
 // result of that one call.
-template <bool X3, bool MSEG>
+template <bool X3, bool MSEG, int KS>
 cudaError_t p2_configure() {
-    static cudaError_t state = cudaFuncSetAttribute(gemm_tc2_kernel<X3, MSEG>,
+    static cudaError_t state = cudaFuncSetAttribute(gemm_tc2_kernel<X3, MSEG, KS>,
                                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P2_SMEM);
     return state;
 }
 
+// Two k-blocks per stage unless K segments of an odd number of k-blocks
+// would split a stage.
 template <bool X3, bool MSEG>
 cudaError_t p2_launch(const TcParams& tp, int ctas, const CUtensorMap* m, cudaStream_t s) {
-    const cudaError_t e = p2_configure<X3, MSEG>();
-    if (e != cudaSuccess) return e;
-    gemm_tc2_kernel<X3, MSEG><<<ctas, TC_THREADS, P2_SMEM, s>>>(tp, m[0], m[1], m[2], m[3], m[4], m[5]);
+    if (MSEG && tp.seg_kb % 2) {
+        const cudaError_t e = p2_configure<X3, MSEG, 1>();
+        if (e != cudaSuccess) return e;
+        gemm_tc2_kernel<X3, MSEG, 1><<<ctas, TC_THREADS, P2_SMEM, s>>>(tp, m[0], m[1], m[2], m[3], m[4], m[5]);
+    } else {
+        const cudaError_t e = p2_configure<X3, MSEG, 2>();
+        if (e != cudaSuccess) return e;
+        gemm_tc2_kernel<X3, MSEG, 2><<<ctas, TC_THREADS, P2_SMEM, s>>>(tp, m[0], m[1], m[2], m[3], m[4], m[5]);
+    }
     return cudaGetLastError();
 }
 
