@@ -48,7 +48,7 @@ typedef int32_t upir_status;
 #define UPIR_ENOMEM       (-4) /* the allocator returned NULL                                  */
 #define UPIR_ECUDA        (-5) /* a CUDA runtime call failed                                   */
 #define UPIR_ETIMEDOUT    (-6) /* a bounded device-side wait ran out (device error word set)  */
-#define UPIR_EUNSUPPORTED (-7) /* valid request this build does not execute (e.g. K % 8 != 0 on tensor cores) */
+#define UPIR_EUNSUPPORTED (-7) /* valid request this library does not execute (e.g. K % 8 != 0 on tensor cores) */
 
 /* Static text for a status code; never NULL. */
 const char* upir_status_string(upir_status s);

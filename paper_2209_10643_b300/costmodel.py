@@ -5,7 +5,8 @@ units per team, teams) from 12 features and picks the one it predicts
 fastest.  Its training data are timings the runtime measures itself
 (exhaustive autotuning of candidate schedules with CUDA events); training runs
 on the GPU through the library's MLP forward/backward/SGD kernels.  The
-exhaustive autotuner remains the fallback and the judge of the model's regret.
+exhaustive autotuner remains the fallback and the reference the model's regret
+is measured against.
 
 Features (12): op one-hot (AXPY, JACOBI5, MATVEC, GEMM), log2 trip count,
 bytes per iteration, flops per iteration, schedule one-hot (static, dynamic),

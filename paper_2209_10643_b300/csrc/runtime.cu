@@ -66,7 +66,7 @@ extern "C" const char* upir_status_string(upir_status s) {
         case UPIR_ENOMEM: return "UPIR_ENOMEM: device allocation failed";
         case UPIR_ECUDA: return "UPIR_ECUDA: CUDA runtime error";
         case UPIR_ETIMEDOUT: return "UPIR_ETIMEDOUT: a bounded device wait ran out";
-        case UPIR_EUNSUPPORTED: return "UPIR_EUNSUPPORTED: not supported by this build";
+        case UPIR_EUNSUPPORTED: return "UPIR_EUNSUPPORTED: not supported by this library";
         default: return "unknown upir_status";
     }
 }
