@@ -640,6 +640,7 @@ def cpu_baseline_jacobi(budget_s: float = 12.0) -> dict:
 
 def extra_workloads(rt: Runtime, pk: dict) -> dict:
     return {"axpy_2^20": lambda: extra_axpy(rt, 1 << 20, pk),
+            "axpy_2^26": lambda: extra_axpy(rt, 1 << 26, pk),
             "axpy_2^28": lambda: extra_axpy(rt, 1 << 28, pk),
             "matvec_16384": lambda: extra_matvec(rt, pk),
             "jacobi_tb4_4096": lambda: extra_jacobi_tb(rt, pk, 4),

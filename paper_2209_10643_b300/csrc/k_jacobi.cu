@@ -78,7 +78,7 @@ __global__ void __launch_bounds__(1024) jacobi_tma_kernel(const JacobiParams p,
     griddep_launch_dependents();
 
     bool failed = false;
-    int s = 0;
+    int s = 0, prev = -1;
     uint32_t parity = 0;
     for (;;) {
         const int2 rc = stage_rc[s];
@@ -87,6 +87,10 @@ __global__ void __launch_bounds__(1024) jacobi_tma_kernel(const JacobiParams p,
             failed = true;
             break;
         }
+        // with three or more stages, every thread has finished the previous
+        // stage once it passes this barrier: its refill goes out now, and its
+        // stage_rc entry is next read two barriers later
+        if (S >= 3 && threadIdx.x == 0 && prev >= 0) issue_next(prev);
         if (active) {
             const float* cen = ring + s * stage_floats + (ty + 1) * SW + 4 + 4 * tx;
             const int c = rc.y + 4 * tx;
@@ -126,9 +130,12 @@ __global__ void __launch_bounds__(1024) jacobi_tma_kernel(const JacobiParams p,
                 }
             }
         }
-        __syncthreads();  // every thread is done with stage s
-        if (threadIdx.x == 0) issue_next(s);
-        __syncthreads();  // stage_rc[s] is read again (at once when S == 1)
+        if (S < 3) {
+            __syncthreads();  // every thread is done with stage s
+            if (threadIdx.x == 0) issue_next(s);
+            __syncthreads();  // stage_rc[s] is read again (at once when S == 1)
+        }
+        prev = s;
         if (++s == S) {
             s = 0;
             parity ^= 1u;
