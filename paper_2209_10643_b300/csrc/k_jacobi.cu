@@ -160,9 +160,10 @@ __global__ void __launch_bounds__(1024) jacobi_tma_kernel(const JacobiParams p,
 
 // The row-copy variant (widths that are not a multiple of 4).  Per stage,
 // thread 0 takes the next tile and arms the stage's barrier while the team
-// computes; once the team has finished with the stage, threads 0 .. TM + 1
-// issue one halo-row copy each, so the copies cost every thread at most one
-// instruction.
+// computes; after the barrier that opens the following stage (the team is
+// then done with this one), threads 0 .. TM + 1 issue one halo-row copy each,
+// so the copies cost every thread at most one instruction and a tile costs
+// one team barrier.
 template <int S, int ROP>
 __global__ void __launch_bounds__(1024) jacobi_rows_kernel(const JacobiParams p,
                                                           const __grid_constant__ CUtensorMap tmap) {
@@ -224,7 +225,7 @@ __global__ void __launch_bounds__(1024) jacobi_rows_kernel(const JacobiParams p,
     griddep_launch_dependents();
 
     bool failed = false;
-    int s = 0;
+    int s = 0, prev = -1;
     uint32_t parity = 0;
     for (;;) {
         const int2 rc = stage_rc[s];
@@ -233,6 +234,9 @@ __global__ void __launch_bounds__(1024) jacobi_rows_kernel(const JacobiParams p,
             failed = true;
             break;
         }
+        // past this barrier every thread has left the previous stage, whose
+        // next tile thread 0 took an iteration ago: its row copies go out
+        if (prev >= 0) copy_rows(prev);
         // every thread has read stage_rc[s] and the stage's phase is complete:
         // the stage's next tile can be taken and its barrier re-armed
         if (threadIdx.x == 0) take_next(s);
@@ -260,8 +264,7 @@ __global__ void __launch_bounds__(1024) jacobi_rows_kernel(const JacobiParams p,
                 }
             }
         }
-        __syncthreads();  // every thread is done with stage s; stage_rc[s] holds its next tile
-        copy_rows(s);
+        prev = s;
         if (++s == S) {
             s = 0;
             parity ^= 1u;
