@@ -262,7 +262,9 @@ __global__ void __launch_bounds__(1024, 1) jacobi_tb_kernel(const JacobiTBParams
                 }
             }
         }
-        __syncthreads();  // ring(s) and the scratch plane are free again
+        // no barrier here: the next tile's opening barrier orders these reads
+        // of ring(s) and the scratch plane before the copy into ring(s) and
+        // the next sweeps' writes
         s ^= 1;
     }
 
