@@ -295,7 +295,9 @@ typedef struct {
  * tile, 2 = CTA pairs (tcgen05 cta_group::2, 256 x 256 tiles; EUNSUPPORTED
  * with explicit teams, a chunk, a TILE_M hint or when no two-CTA cluster
  * fits), 0 = the planner's choice (pairs when every resident cluster gets a
- * tile). */
+ * tile); GEMM_F32 1 = the kernel that stages loads through registers (the
+ * default, TMA-fed kernel needs K and N multiples of 4 and 16-byte aligned
+ * buffers, and gives the same result bit for bit). */
 typedef enum {
     UPIR_HINT_VARIANT   = 1, /* kernel variant of the body (body-specific, 0 = default)       */
     UPIR_HINT_TILE_M    = 2, /* tile rows (JACOBI5 tiled variant, GEMM)                       */

@@ -734,15 +734,47 @@ upir_status plan_loop(upir_region r, const upir_loop_desc* d, LoopRec& lp) {
                 gp.chunk = lp.chunk;
                 gp.sched = kernel_sched(lp.sched);
                 const int64_t ntiles = ceil_div(lp.trip, 128) * ceil_div(N, 128);
+                gp.whole = ntiles;
+                gp.kparts = 1;
                 if (T0) lp.teams = T0;
-                else if (lp.sched == UPIR_SCHED_STATIC && lp.chunk == 0)
-                    lp.teams = (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, 0x7fffffff));
-                else
+                else if (lp.sched == UPIR_SCHED_STATIC && lp.chunk == 0) {
+                    // one tile per team; when the last wave of resident teams
+                    // (two per SM) would be at most half full, its tiles are
+                    // split in k over the idle slots, each share at least 8 k tiles
+                    const int64_t slots = 2 * kNumSMs, rem = ntiles % slots;
+                    const int64_t q = rem ? std::min<int64_t>(std::min<int64_t>(slots / rem, 4), ceil_div(K, 16) / 8) : 1;
+                    if (ntiles > slots && q >= 2) {
+                        gp.whole = ntiles - rem;
+                        gp.kparts = (int)q;
+                        upir_status st = alloc_scratch(ctx, lp, rem, rem * q * 128 * 128 / 4, &gp.sc);
+                        if (st != UPIR_OK) return st;
+                        gp.tile_tickets = gp.sc.group_tickets;
+                        gp.work = reinterpret_cast<float*>(gp.sc.partials);
+                    }
+                    lp.teams = (int)std::max<int64_t>(1, std::min<int64_t>(gp.whole + (ntiles - gp.whole) * gp.kparts,
+                                                                           0x7fffffff));
+                } else
                     lp.teams = (int)std::max<int64_t>(1, std::min<int64_t>(dyn_estimate(lp, ntiles), kNumSMs * 2));
                 gp.sk = make_sched_const(ntiles, lp.chunk, lp.teams);
                 if (is_dyn(lp.sched)) {
                     build_chunk_table(lp, ntiles, lp.teams);
                     upir_status st = alloc_scratch(ctx, lp, 0, 0, &gp.sc);
+                    if (st != UPIR_OK) return st;
+                }
+                // TMA boxes need rows of A and B (and C's float4 stores) that
+                // start on 16-byte boundaries; VARIANT 1 keeps the register-
+                // staged kernel
+                const auto al16 = [](const void* q) { return (reinterpret_cast<uintptr_t>(q) & 15) == 0; };
+                lp.gemm_tma = lp.variant != 1 && lp.trip > 0 && N > 0 && K > 0 && K % 4 == 0 && N % 4 == 0 &&
+                              al16(gp.A) && al16(gp.B) && al16(gp.C);
+                if (lp.gemm_tma) {
+                    gp.spin_limit = ctx->spin_limit;
+                    gp.err_word = ctx->err_word;
+                    upir_status st = encode_tmap_2d(ctx, &lp.tmap[0], gp.A, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4,
+                                                    (uint64_t)K, (uint64_t)M, 16, 128, 0);
+                    if (st == UPIR_OK)
+                        st = encode_tmap_2d(ctx, &lp.tmap[1], gp.B, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4,
+                                            (uint64_t)N, (uint64_t)K, 128, 16, 0);
                     if (st != UPIR_OK) return st;
                 }
                 lp.skip = lp.trip == 0 || N == 0;
@@ -841,7 +873,9 @@ cudaError_t launch_loop(upir_ctx ctx, LoopRec& lp, cudaStream_t s) {
                                lp.ep.rv.ivar ? lp.ep.rv.iop : 0, lp.teams, lp.units, lp.ep, s);
         case LK_JACOBI_TMA: return launch_jacobi_tma(lp.teams, lp.units, lp.jp, &lp.tmap[0], s);
         case LK_MATVEC: return launch_matvec(lp.teams, lp.units, lp.mp, s);
-        case LK_GEMM_F32: return launch_gemm_f32(lp.teams, lp.units, lp.gp, s);
+        case LK_GEMM_F32:
+            return lp.gemm_tma ? launch_gemm_f32_tma(lp.teams, lp.gp, &lp.tmap[0], s)
+                               : launch_gemm_f32(lp.teams, lp.units, lp.gp, s);
         case LK_SPLIT: return launch_split_bf16(lp.teams, lp.units, lp.sp, s);
         case LK_GEMM_TC: return launch_gemm_tc_loop(ctx, lp, s);
         case LK_JACOBI_TB: return launch_jacobi_tb(lp.teams, lp.units, lp.tb, &lp.tmap[0], s);

@@ -158,6 +158,16 @@ struct GemmParams {
     int sched;
     SchedConst sk;
     Scratch sc;
+    // tail split (static default plan only, kparts > 1): teams [0, whole) take
+    // whole tiles; the tiles from `whole` on are each taken by kparts teams,
+    // one share of the k tiles each, whose sums meet in `work` (kparts 128 x
+    // 128 partial tiles per split tile) and are added by the last to finish
+    int64_t whole;
+    int kparts;
+    float* work;
+    unsigned* tile_tickets;
+    long long spin_limit;  // TMA-fed kernel: bound of each wait for a k tile
+    int* err_word;
 };
 
 struct SplitParams {
@@ -235,6 +245,8 @@ cudaError_t launch_filter7(int teams, const Filter7Params& p, const void* tmap, 
 int jacobi_tma_max_teams_per_sm(int units, int tile_m, int tile_n, int stages, bool rows);
 cudaError_t launch_matvec(int teams, int units, const MatvecParams& p, cudaStream_t s);
 cudaError_t launch_gemm_f32(int teams, int units, const GemmParams& p, cudaStream_t s);
+// tm: the A (K x M, 16 x 128 boxes) and B (N x K, 128 x 16 boxes) tensor maps
+cudaError_t launch_gemm_f32_tma(int teams, const GemmParams& p, const CUtensorMap* tm, cudaStream_t s);
 cudaError_t launch_split_bf16(int teams, int units, const SplitParams& p, cudaStream_t s);
 cudaError_t launch_bounded_wait_selftest(long long spin_limit, int* err_word, cudaStream_t s);
 cudaError_t launch_batch_persistent(int teams, const BatchParams& p, cudaStream_t s);

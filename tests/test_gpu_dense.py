@@ -75,13 +75,14 @@ def test_matvec_full_workload_16384(s):
     check_matvec(a, x, run_matvec(s, a, x))
 
 
-def run_gemm(s, a, b, teams=0, sched=0, chunk=0, lb=0, ub=None):
+def run_gemm(s, a, b, teams=0, sched=0, chunk=0, lb=0, ub=None, variant=0):
     m, k = a.shape
     n = b.shape[1]
     c = np.full((m, n), -3.0, np.float32)
     ha, hb, hc = s.map(a, U.UPIR_MAP_TO), s.map(b, U.UPIR_MAP_TO), s.map(c, U.UPIR_MAP_TOFROM)
     s.run([dict(lb=lb, ub=m if ub is None else ub, step=1, collapse=2, body=U.UPIR_BODY_GEMM_F32,
-                bufs=[ha, hb, hc], scalars=[m, n, k], sched=sched, chunk=chunk)], teams, 0)
+                bufs=[ha, hb, hc], scalars=[m, n, k], sched=sched, chunk=chunk,
+                hints=[(U.UPIR_HINT_VARIANT, variant)] if variant else [])], teams, 0)
     for h in (ha, hb, hc):
         s.unmap(h)
     return c
@@ -101,6 +102,65 @@ def test_gemm_f32_exact_integers_and_schedules(s):
     ref = O.gemm(a, b)
     for teams, sched, chunk in [(0, 0, 0), (3, 0, 1), (2, 1, 1)]:
         assert np.array_equal(run_gemm(s, a, b, teams, sched, chunk), ref)
+
+
+@pytest.mark.parametrize("n", [2250, 2252])
+def test_gemm_f32_split_tail_exact_and_close(s, n):
+    """A 2300 x n output has 18 x 18 = 324 tiles: 296 resident teams take
+    whole tiles and the last 28 tiles are split in four shares of k (520, a
+    ragged last k tile).  Small integers give the exact product whatever the
+    split; random inputs stay within the FP32 bound.  n = 2250 runs the
+    register-staged kernel, n = 2252 (rows on 16-byte boundaries) the TMA-fed
+    one."""
+    a = I.small_int_matrix(2300, 520, -8, 8, seed=3)
+    b = I.small_int_matrix(520, n, -8, 8, seed=4)
+    assert np.array_equal(run_gemm(s, a, b), O.gemm(a, b))
+    a, b = I.gemm_inputs(2300, n, 520)
+    c = run_gemm(s, a, b)
+    ref = O.gemm(a, b)
+    assert np.linalg.norm(c - ref) <= 1e-5 * np.linalg.norm(ref)
+    tail = slice(2048, 2300)
+    assert np.linalg.norm(c[tail] - ref[tail]) <= 1e-5 * np.linalg.norm(ref[tail])
+
+
+@pytest.mark.parametrize("m,n,k,teams,sched,chunk", [
+    (300, 260, 96, 0, 0, 0), (1000, 1004, 520, 0, 0, 0), (129, 132, 20, 0, 0, 0), (2300, 2252, 520, 0, 0, 0),
+    (700, 516, 64, 5, 0, 2), (700, 516, 64, 0, 1, 3), (4, 4, 4, 0, 0, 0)])
+def test_gemm_f32_tma_and_register_kernels_agree(s, m, n, k, teams, sched, chunk):
+    """Both FP32 kernels run every element as one FMA chain in increasing k
+    (and split the same tiles the same way): their results agree bit for bit,
+    and match the FP64 product within the FP32 bound."""
+    a, b = I.gemm_inputs(m, n, k)
+    c_tma = run_gemm(s, a, b, teams, sched, chunk)
+    c_reg = run_gemm(s, a, b, teams, sched, chunk, variant=1)
+    assert np.array_equal(c_tma, c_reg)
+    ref = O.gemm(a, b)
+    assert np.linalg.norm(c_tma - ref) <= 1e-5 * np.linalg.norm(ref)
+
+
+def test_gemm_f32_split_tail_resubmitted(s):
+    """Each submission of a recorded split GEMM writes every tile: the shares'
+    tickets are ready again for the next one (C is changed in between by an
+    AXPY loop of the same region, C += 1 in place)."""
+    m, n, k = 2300, 2250, 520
+    a = I.small_int_matrix(m, k, -8, 8, seed=5)
+    b = I.small_int_matrix(k, n, -8, 8, seed=6)
+    c = np.zeros((m, n), np.float32)
+    ones = np.ones(m * n, np.float32)
+    ha, hb, hc, ho = (s.map(a, U.UPIR_MAP_TO), s.map(b, U.UPIR_MAP_TO), s.map(c, U.UPIR_MAP_TOFROM),
+                      s.map(ones, U.UPIR_MAP_TO))
+    r = U.upir_spmd_region(s.ctx, 0, 0)
+    U.upir_loop_checked(s.ctx, r, U.make_loop_desc(lb=0, ub=m, step=1, collapse=2, body=U.UPIR_BODY_GEMM_F32,
+                                                   bufs=[ha, hb, hc], scalars=[m, n, k]))
+    U.upir_loop_checked(s.ctx, r, U.make_loop_desc(lb=0, ub=m * n, step=1, body=U.UPIR_BODY_AXPY,
+                                                   bufs=[ho, hc], scalars=[1.0, 3, 1000]))
+    for _ in range(3):
+        U.upir_region_submit(r, 0)
+    U.upir_ctx_wait(s.ctx)
+    U.upir_region_destroy(r)
+    for h in (ha, hb, hc, ho):
+        s.unmap(h)
+    assert np.array_equal(c, O.gemm(a, b) + 1.0)
 
 
 def test_gemm_f32_full_size_sampled_and_freivalds(s):
