@@ -138,6 +138,26 @@ def test_gemm_f32_tma_and_register_kernels_agree(s, m, n, k, teams, sched, chunk
     assert np.linalg.norm(c_tma - ref) <= 1e-5 * np.linalg.norm(ref)
 
 
+@pytest.mark.parametrize("variant", [0, 1])
+def test_gemm_f32_row_subrange_touches_only_its_rows(s, variant):
+    """Rows [70, 1030) of a 1100 x 5120 product, both kernels (the TMA boxes
+    of the first and last tile rows cover rows outside the range, which are
+    read but not written); the range's 8 x 40 tiles outnumber the 296
+    resident teams, so the default plan splits the last 24 in k."""
+    a, b = I.gemm_inputs(1100, 5120, 256)
+    c = run_gemm(s, a, b, lb=70, ub=1030, variant=variant)
+    ref = O.gemm(a, b)
+    inside = slice(70, 1030)
+    assert np.linalg.norm(c[inside] - ref[inside]) <= 1e-5 * np.linalg.norm(ref[inside])
+    assert np.all(c[:70] == -3.0) and np.all(c[1030:] == -3.0)
+
+
+def test_gemm_f32_empty_k_writes_zeros(s):
+    a = np.zeros((40, 0), np.float32)
+    b = np.zeros((0, 36), np.float32)
+    assert np.all(run_gemm(s, a, b) == 0.0)
+
+
 def test_gemm_f32_split_tail_resubmitted(s):
     """Each submission of a recorded split GEMM writes every tile: the shares'
     tickets are ready again for the next one (C is changed in between by an
