@@ -124,8 +124,8 @@ upir_status upir_data_unmap(upir_ctx ctx, upir_buf buf);
 upir_status upir_buf_device_ptr(upir_buf buf, void** device_ptr, size_t* bytes);
 
 /* ----------------------------------------------- asynchronous data movement --
- * §4 leaves data movement to the runtime "for the purpose of achieving maximum
- * overlapping and pipelining of computation and data movement".  These calls
+ * §4 leaves data movement to the runtime so that copies can overlap and be
+ * pipelined with the computation.  These calls
  * put the copies on the context's copy stream, ordered after the work already
  * submitted, and return at once; a later submission that uses the buffer
  * waits (on the device) for the copy.  Overlap with computation needs
@@ -145,6 +145,16 @@ upir_status upir_buf_device_ptr(upir_buf buf, void** device_ptr, size_t* bytes);
 upir_status upir_data_map_async(upir_ctx ctx, void* host, size_t bytes, int32_t kind, upir_buf* out);
 upir_status upir_data_update_async(upir_ctx ctx, upir_buf buf, int32_t direction);
 upir_status upir_buf_wait(upir_ctx ctx, upir_buf buf);
+
+/* Device-side copy between mapped buffers (the device-to-device case of the
+ * data movement of §4.2): the first src->bytes bytes of dst become those of
+ * src, on the context's compute stream, after both buffers' pending
+ * asynchronous copies and the work submitted so far; later submissions and
+ * copies see the result.  Returns at once.  Use: one host array that seeds
+ * two device buffers (the two grids of a Jacobi iteration) crosses the host
+ * link once.  EINVAL if dst is smaller than src; ENOTMAPPED for a stale
+ * handle; dst == src or an empty src does nothing. */
+upir_status upir_buf_copy(upir_ctx ctx, upir_buf dst, upir_buf src);
 
 /* ------------------------------------------------------ two-step sync steps --
  * §5: a sync is an arrive-compute step (a unit reaches the sync point and its

@@ -93,6 +93,7 @@ _SIGS = {
     "upir_data_map_async": (_i32, [_vp, _vp, _sz, _i32, _P(_vp)]),
     "upir_data_update_async": (_i32, [_vp, _vp, _i32]),
     "upir_buf_wait": (_i32, [_vp, _vp]),
+    "upir_buf_copy": (_i32, [_vp, _vp, _vp]),
     "upir_ctx_arrive": (_i32, [_vp, _P(_vp)]),
     "upir_event_query": (_i32, [_vp]),
     "upir_event_wait": (_i32, [_vp]),
@@ -284,6 +285,12 @@ def upir_data_update_async(ctx: int, buf: int, direction: int) -> None:
 
 def upir_buf_wait(ctx: int, buf: int) -> None:
     _chk(ctx, lib.upir_buf_wait(ctx, buf), "upir_buf_wait")
+
+
+def upir_buf_copy(ctx: int, dst: int, src: int) -> None:
+    """Device-side copy of ``src`` into the first bytes of ``dst`` (ordered
+    on the context's compute stream)."""
+    _chk(ctx, lib.upir_buf_copy(ctx, dst, src), "upir_buf_copy")
 
 
 def upir_ctx_arrive(ctx: int) -> int:

@@ -420,6 +420,25 @@ extern "C" upir_status upir_buf_wait(upir_ctx ctx, upir_buf b) {
     return e == cudaSuccess ? UPIR_OK : cuda_fail(ctx, e, "upir_buf_wait");
 }
 
+extern "C" upir_status upir_buf_copy(upir_ctx ctx, upir_buf dst, upir_buf src) {
+    if (!ctx) return UPIR_EINVAL;
+    if (!buf_ok(ctx, dst) || !buf_ok(ctx, src)) return fail(ctx, UPIR_ENOTMAPPED, "upir_buf_copy: buffer not mapped");
+    if (dst->bytes < src->bytes)
+        return fail(ctx, UPIR_EINVAL, "upir_buf_copy: destination (%zu bytes) smaller than the source (%zu bytes)",
+                    dst->bytes, src->bytes);
+    if (src->bytes == 0 || dst == src) return UPIR_OK;
+    // a pending copy into src (or out of dst) finishes first; the compute
+    // stream orders everything after this copy behind it
+    for (upir_buf b : {src, dst}) {
+        if (!b->pending) continue;
+        const cudaError_t e = cudaStreamWaitEvent(ctx->stream, b->ready, 0);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "upir_buf_copy: waiting for a buffer's copy");
+        b->pending = false;
+    }
+    const cudaError_t e = cudaMemcpyAsync(dst->dev, src->dev, src->bytes, cudaMemcpyDeviceToDevice, ctx->stream);
+    return e == cudaSuccess ? UPIR_OK : cuda_fail(ctx, e, "upir_buf_copy");
+}
+
 // ------------------------------------------------------- two-step sync steps --
 
 extern "C" upir_status upir_ctx_arrive(upir_ctx ctx, upir_event* out) {

@@ -168,3 +168,41 @@ def test_async_argument_errors(ctx):
     with pytest.raises(U.UpirError) as e:
         U.upir_buf_wait(ctx, h)
     assert e.value.status == U.UPIR_ENOTMAPPED
+
+
+def test_buf_copy_seeds_a_second_buffer_on_the_device(ctx):
+    """One host grid mapped asynchronously, copied on the device into a
+    buffer mapped FROM, then one Jacobi sweep from the copy: the copy waits
+    for the host->device transfer, and the sweep for the copy."""
+    u0 = I.jacobi_grid(96, seed=2)
+    host = pinned(u0)
+    back = np.full_like(u0, -1.0)
+    out = np.full_like(u0, -1.0)
+    ha = U.upir_data_map_async(ctx, host.data_ptr(), u0.nbytes, U.UPIR_MAP_TO)
+    hb = U.upir_data_map(ctx, back.ctypes.data, u0.nbytes, U.UPIR_MAP_FROM)
+    ho = U.upir_data_map(ctx, out.ctypes.data, u0.nbytes, U.UPIR_MAP_FROM)
+    U.upir_buf_copy(ctx, hb, ha)
+    U.upir_buf_copy(ctx, ho, hb)
+    run(ctx, [dict(lb=1, ub=95, step=1, collapse=2, body=U.UPIR_BODY_JACOBI5, bufs=[hb, ho], scalars=[96, 96])])
+    for h in (ha, hb, ho):
+        U.upir_data_unmap(ctx, h)
+    assert np.array_equal(back, u0)
+    want, _ = O.jacobi_run(u0, 1, mirror_f32=True)
+    assert np.array_equal(out, want)
+
+
+def test_buf_copy_argument_errors(ctx):
+    big = np.zeros(64, np.float32)
+    small = np.zeros(16, np.float32)
+    hbig = U.upir_data_map(ctx, big.ctypes.data, big.nbytes, U.UPIR_MAP_TO)
+    hsmall = U.upir_data_map(ctx, small.ctypes.data, small.nbytes, U.UPIR_MAP_TO)
+    with pytest.raises(U.UpirError) as e:
+        U.upir_buf_copy(ctx, hsmall, hbig)
+    assert e.value.status == U.UPIR_EINVAL
+    U.upir_buf_copy(ctx, hbig, hsmall)   # the first 64 bytes of big
+    U.upir_buf_copy(ctx, hbig, hbig)     # nothing to do
+    U.upir_data_unmap(ctx, hsmall)
+    with pytest.raises(U.UpirError) as e:
+        U.upir_buf_copy(ctx, hbig, hsmall)
+    assert e.value.status == U.UPIR_ENOTMAPPED
+    U.upir_data_unmap(ctx, hbig)
