@@ -27,7 +27,7 @@ from dataclasses import dataclass, field
 import numpy as np
 
 # ----------------------------------------------------------------------------
-# Data mapping — §4.1 (Fig. "UPIR MLIR dialect for data attributes"): the
+# Data mapping — §4.1 (the figure with the dialect of data attributes): the
 # data-mapping property is one of to / from / tofrom / allocate.
 # ----------------------------------------------------------------------------
 
@@ -78,7 +78,7 @@ class Device:
 
 
 # ----------------------------------------------------------------------------
-# Canonical loop — §3.2 (Fig. "UPIR MLIR dialect for data parallelism"):
+# Canonical loop — §3.2 (the figure with the dialect of data parallelism):
 # induction variable, lowerBound, upperBound, step.  The AXPY listings of §6
 # (``for (i = 0; i < n; i++)`` lowered to ``lowerBound(0) upperBound(n)``) fix
 # the upper bound as exclusive.
@@ -228,7 +228,7 @@ def check_dynamic_assignment(trip: int, chunk: int, owner: np.ndarray,
 
 
 # ----------------------------------------------------------------------------
-# Reductions — §5 (Fig. "UPIR MLIR dialect for synchronization"): a sync of
+# Reductions — §5 (the figure with the dialect of synchronization): a sync of
 # kind ``reduction`` carries an operation and the data it reduces.  Reading
 # (paper silent): identities + -> 0, * -> 1, max -> -inf, min -> +inf; the
 # variable's value before the loop is combined exactly once; max/min ignore a
