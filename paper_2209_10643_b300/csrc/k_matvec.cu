@@ -51,6 +51,15 @@ __global__ void __launch_bounds__(1024) matvec_kernel(const MatvecParams p) {
 
 }  // namespace
 
+int matvec_max_teams_per_sm(int units) {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, matvec_kernel, units, 0) != cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    return n > 0 ? n : 1;
+}
+
 cudaError_t launch_matvec(int teams, int units, const MatvecParams& p, cudaStream_t s) {
     return launch_pdl(matvec_kernel, teams, units, 0, s, p);
 }

@@ -678,7 +678,10 @@ upir_status plan_loop(upir_region r, const upir_loop_desc* d, LoopRec& lp) {
             mp.chunk = lp.chunk;
             mp.sched = kernel_sched(lp.sched);
             const int64_t wpb = lp.units / 32;
-            const int64_t resident_warps = (int64_t)kNumSMs * (kResidentThreadsPerSM / 32);
+            // the warps that fit at once (the kernel's registers, not the
+            // thread limit, bound them): a static plan gives each the same
+            // number of rows and launches no second wave
+            const int64_t resident_warps = (int64_t)kNumSMs * matvec_max_teams_per_sm(lp.units) * wpb;
             if (T0) lp.teams = T0;
             else if (lp.sched == UPIR_SCHED_STATIC && lp.chunk == 0) {
                 const int64_t per = std::max<int64_t>(1, ceil_div(lp.trip, resident_warps));

@@ -244,6 +244,7 @@ int filter7_max_teams_per_sm(int tile_m, int tile_n);
 cudaError_t launch_filter7(int teams, const Filter7Params& p, const void* tmap, cudaStream_t s);
 int jacobi_tma_max_teams_per_sm(int units, int tile_m, int tile_n, int stages, bool rows);
 cudaError_t launch_matvec(int teams, int units, const MatvecParams& p, cudaStream_t s);
+int matvec_max_teams_per_sm(int units);
 cudaError_t launch_gemm_f32(int teams, int units, const GemmParams& p, cudaStream_t s);
 // tm: the A (K x M, 16 x 128 boxes) and B (N x K, 128 x 16 boxes) tensor maps
 cudaError_t launch_gemm_f32_tma(int teams, const GemmParams& p, const CUtensorMap* tm, cudaStream_t s);
