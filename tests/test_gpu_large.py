@@ -115,3 +115,57 @@ def test_jacobi_sweep_past_2p31_points(s):
     assert res[0] == 0.0
     del u, out
     torch.cuda.empty_cache()
+
+
+def test_time_blocked_jacobi_past_2p31_points(s):
+    """Eight sweeps in one time-blocked loop over the same 46342 x 46344
+    harmonic field: the field comes back unchanged and all eight residuals
+    are 0."""
+    rows, cols = 46342, 46344
+    u = torch.empty((rows, cols), dtype=torch.float32, device="cuda")
+    cc = 2 * torch.arange(cols, device="cuda", dtype=torch.float32)[None, :]
+    for r0 in range(0, rows, 4096):
+        r1 = min(rows, r0 + 4096)
+        u[r0:r1] = torch.arange(r0, r1, device="cuda", dtype=torch.float32)[:, None] + cc
+    del cc
+    out = u.clone()
+    out[1:-1, 1:-1] = -1.0
+    res = np.full(8, -np.inf, np.float32)
+    torch.cuda.synchronize()
+    hu, ho = dev_map(s, u), dev_map(s, out)
+    hr = s.map(res, U.UPIR_MAP_TOFROM)
+    s.run([dict(lb=1, ub=rows - 1, step=1, collapse=2, body=U.UPIR_BODY_JACOBI5_TB, bufs=[hu, ho],
+                scalars=[rows, cols, 8], reductions=[(U.UPIR_RED_MAX, U.UPIR_F32, U.UPIR_TERM_RESID, hr, 0)])])
+    for h in (hu, ho, hr):
+        s.unmap(h)
+    assert bool(torch.equal(out, u))
+    assert np.all(res == 0.0)
+    del u, out
+    torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("variant", [0, 1])
+def test_gemm_f32_past_2p31_elements_of_a(s, variant):
+    """C = A B with A 65536 x 32772 (more than 2^31 elements), A[r][k] =
+    (r + k) mod 5 - 2 and B = 1 (32772 x 8): every C[r][j] is the exact
+    integer sum over k, which depends on r mod 5 only; both FP32 kernels."""
+    m, k, n = 65536, 32772, 8
+    a = torch.empty((m, k), dtype=torch.float32, device="cuda")
+    kk = torch.arange(k, device="cuda")[None, :]
+    for r0 in range(0, m, 4096):
+        rr = torch.arange(r0, r0 + 4096, device="cuda")[:, None]
+        a[r0:r0 + 4096] = ((rr + kk) % 5 - 2).to(torch.float32)
+    del kk
+    b = torch.ones((k, n), dtype=torch.float32, device="cuda")
+    c = torch.full((m, n), -3.0, dtype=torch.float32, device="cuda")
+    torch.cuda.synchronize()
+    ha, hb, hc = dev_map(s, a), dev_map(s, b), dev_map(s, c)
+    s.run([dict(lb=0, ub=m, step=1, collapse=2, body=U.UPIR_BODY_GEMM_F32, bufs=[ha, hb, hc], scalars=[m, n, k],
+                hints=[(U.UPIR_HINT_VARIANT, variant)] if variant else [])])
+    for h in (ha, hb, hc):
+        s.unmap(h)
+    per_residue = np.array([np.sum((q + np.arange(k)) % 5 - 2) for q in range(5)], np.float32)
+    want = np.repeat(per_residue[np.arange(m) % 5][:, None], n, axis=1)
+    assert np.array_equal(c.cpu().numpy(), want)
+    del a, b, c
+    torch.cuda.empty_cache()
