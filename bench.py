@@ -36,9 +36,9 @@ N_GRID = 4096
 SWEEPS = 100
 JACOBI_BYTES_PER_SWEEP = 8 * (N_GRID - 2) ** 2
 # DRAM bytes (read + write) of one launch of the sweep kernel on this grid, from
-# an ncu capture of the current kernel (cold launch, 3-stage ring, 64 x 128
-# tiles, one team barrier per tile)
-JACOBI_TRAFFIC_BYTES = 70_771_712 + 12_221_952
+# an ncu capture of the current kernel and launch (cold launch, 3-stage ring,
+# 64 x 128 tiles, one team barrier per tile, 512-unit teams)
+JACOBI_TRAFFIC_BYTES = 70_514_688 + 11_719_168
 L2_FLUSH_BYTES = 256 << 20
 
 

@@ -403,10 +403,12 @@ upir_status plan_loop(upir_region r, const upir_loop_desc* d, LoopRec& lp) {
                 JacobiParams& jp = lp.jp;
                 memset(&jp, 0, sizeof(jp));
                 jp.rows_tma = rows_tma ? 1 : 0;
-                // row copies: teams of 512 units on 64-row tiles, two stages
-                // (4095^2 grid: 28.9 us per sweep; 256 units, 32 rows and
-                // three stages 32.0 us)
-                if (rows_tma && !U0 && !auto_units) lp.units = 512;
+                // teams of 512 units on 64 x 128 tiles: four rows per thread
+                // and 1024 threads per SM (4096^2 grid, 100 sweeps: 2.139 ms;
+                // 256 units 2.157 ms, 1024 units 2.616 ms).  Row copies: two
+                // stages (4095^2 grid: 28.9 us per sweep; 256 units, 32 rows
+                // and three stages 32.0 us)
+                if (!U0 && !auto_units) lp.units = 512;
                 lp.tile_m = lp.tile_m ? lp.tile_m : 64;
                 lp.tile_n = lp.tile_n ? lp.tile_n : 128;
                 lp.tile_n = (int)std::min<int64_t>(lp.tile_n, 4 * (int64_t)lp.units);
