@@ -186,11 +186,10 @@ def make_loop_desc(lb: int, ub: int, step: int = 1, *, body: int, bufs=(), scala
                                             for (op, dt, term, var, idx) in reductions])
     flat = [v for kv in hints for v in kv]
     h_arr = (C.c_int64 * max(len(flat), 1))(*flat)
-    d = upir_loop_desc(lb, ub, step, collapse, sched, chunk, body, nb,
-                       C.cast(b_arr, C.POINTER(C.c_void_p)), ns, nr,
-                       C.cast(s_arr, C.POINTER(C.c_double)),
-                       C.cast(r_arr, C.POINTER(upir_reduction)), nowait, len(hints),
-                       C.cast(h_arr, C.POINTER(C.c_int64)))
+    # ctypes stores an array assigned to a pointer field as the address of
+    # its first element (no cast objects: this runs once per recorded loop)
+    d = upir_loop_desc(lb, ub, step, collapse, sched, chunk, body, nb, b_arr, ns, nr, s_arr, r_arr,
+                       nowait, len(hints), h_arr)
     return d, (b_arr, s_arr, r_arr, h_arr)
 
 
