@@ -125,10 +125,12 @@ upir_status upir_buf_device_ptr(upir_buf buf, void** device_ptr, size_t* bytes);
 
 /* ----------------------------------------------- asynchronous data movement --
  * §4 leaves data movement to the runtime so that copies can overlap and be
- * pipelined with the computation.  These calls
- * put the copies on the context's copy stream, ordered after the work already
- * submitted, and return at once; a later submission that uses the buffer
- * waits (on the device) for the copy.  Overlap with computation needs
+ * pipelined with the computation.  These calls put the copies on the
+ * context's copy streams and return at once.  A buffer's copy is ordered
+ * after the buffer's previous copies and after the submitted work that uses
+ * the buffer (the regions and batches submitted with it, device-side copies,
+ * synchronous copies to it), not after unrelated work; a later submission
+ * that uses the buffer waits (on the device) for the copy.  Overlap with computation needs
  * page-locked host memory (pageable memory still works, without overlap).
  *
  * Host->device and device->host copies use separate streams, so both copy

@@ -146,6 +146,7 @@ extern "C" upir_status upir_finalize(upir_ctx ctx) {
     for (upir_buf b : ctx->all_bufs) {
         if (b->live && !b->wrapped) dev_free(ctx, b->dev, b->bytes);
         if (b->ready) cudaEventDestroy(b->ready);
+        if (b->used) cudaEventDestroy(b->used);
         delete b;
     }
     ctx->all_bufs.clear();
@@ -229,6 +230,13 @@ extern "C" upir_status upir_data_map(upir_ctx ctx, void* host, size_t bytes, int
     b->bytes = bytes;
     b->kind = kind;
     ctx->all_bufs.insert(b);
+    if (bytes > 0 && (kind == UPIR_MAP_TO || kind == UPIR_MAP_TOFROM)) {
+        // the copy went out on the compute stream
+        if (upir_status st = mark_buffer_use(ctx, b)) {
+            *out = b;
+            return st;
+        }
+    }
     *out = b;
     return UPIR_OK;
 }
@@ -257,6 +265,7 @@ extern "C" upir_status upir_data_update(upir_ctx ctx, upir_buf b, int32_t direct
     cudaError_t e;
     if (direction == UPIR_MAP_TO) {
         e = cudaMemcpyAsync(b->dev, b->host, b->bytes, cudaMemcpyHostToDevice, ctx->stream);
+        if (e == cudaSuccess) return mark_buffer_use(ctx, b);
     } else if (direction == UPIR_MAP_FROM) {
         e = cudaMemcpyAsync(b->host, b->dev, b->bytes, cudaMemcpyDeviceToHost, ctx->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
@@ -285,7 +294,9 @@ extern "C" upir_status upir_data_unmap(upir_ctx ctx, upir_buf b) {
     if (e == cudaSuccess) e = e2;
     if (!b->wrapped) dev_free(ctx, b->dev, b->bytes);
     if (b->ready) cudaEventDestroy(b->ready);
+    if (b->used) cudaEventDestroy(b->used);
     b->ready = nullptr;
+    b->used = nullptr;
     b->live = false;
     b->dev = nullptr;
     if (e != cudaSuccess) return cuda_fail(ctx, e, "upir_data_unmap: device->host copy");
@@ -304,20 +315,16 @@ extern "C" upir_status upir_buf_device_ptr(upir_buf b, void** device_ptr, size_t
 namespace {
 
 // The copy stream of one direction, created on first use, ordered after the
-// buffer's previous copy and, with after_compute, after the work already
-// submitted to the context.
+// buffer's previous copy and, with after_compute, after the submitted work
+// that uses the buffer (its last use on the compute stream: region and batch
+// submissions, device-side copies and copies issued on the compute stream
+// record it; work that does not touch the buffer is not waited for).
 upir_status copy_stream_for(upir_ctx ctx, upir_buf b, bool to_device, bool after_compute, cudaStream_t* out) {
     cudaStream_t& cs = to_device ? ctx->copy_stream : ctx->d2h_stream;
     if (!cs && cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess)
         return cuda_fail(ctx, cudaGetLastError(), "creating a copy stream");
     cudaError_t e = cudaSuccess;
-    if (after_compute) {
-        cudaEvent_t ev;
-        e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
-        if (e == cudaSuccess) e = cudaEventRecord(ev, ctx->stream);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ev, 0);
-        cudaEventDestroy(ev);  // released once the wait has consumed it
-    }
+    if (after_compute && b->used) e = cudaStreamWaitEvent(cs, b->used, 0);
     if (e == cudaSuccess && b->ready) e = cudaStreamWaitEvent(cs, b->ready, 0);
     *out = cs;
     return e == cudaSuccess ? UPIR_OK : cuda_fail(ctx, e, "ordering a copy stream");
@@ -334,6 +341,29 @@ upir_status mark_pending(upir_ctx ctx, upir_buf b, cudaStream_t cs) {
 }
 
 }  // namespace
+
+upir_status upir::mark_buffer_use(upir_ctx ctx, upir_buf b) {
+    cudaError_t e = cudaSuccess;
+    if (!b->used) e = cudaEventCreateWithFlags(&b->used, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(b->used, ctx->stream);
+    return e == cudaSuccess ? UPIR_OK : cuda_fail(ctx, e, "recording a buffer's last use");
+}
+
+upir_status upir::mark_region_buffers(upir_region r) {
+    std::vector<upir_buf> seen;
+    auto add = [&](upir_buf b) {
+        for (upir_buf q : seen)
+            if (q == b) return;
+        seen.push_back(b);
+    };
+    for (auto& lp : r->loops) {
+        for (upir_buf b : lp->bufs) add(b);
+        for (auto& red : lp->reds) add(red.var);
+    }
+    for (upir_buf b : seen)
+        if (upir_status st = mark_buffer_use(r->ctx, b)) return st;
+    return UPIR_OK;
+}
 
 upir_status upir::wait_region_buffers(upir_region r) {
     upir_ctx ctx = r->ctx;
@@ -384,6 +414,7 @@ extern "C" upir_status upir_data_map_async(upir_ctx ctx, void* host, size_t byte
             if (ctx->copy_stream) cudaStreamSynchronize(ctx->copy_stream);
             dev_free(ctx, dev, bytes);
             if (b->ready) cudaEventDestroy(b->ready);
+            if (b->used) cudaEventDestroy(b->used);
             ctx->all_bufs.erase(b);
             delete b;
             return st;
@@ -436,7 +467,9 @@ extern "C" upir_status upir_buf_copy(upir_ctx ctx, upir_buf dst, upir_buf src) {
         b->pending = false;
     }
     const cudaError_t e = cudaMemcpyAsync(dst->dev, src->dev, src->bytes, cudaMemcpyDeviceToDevice, ctx->stream);
-    return e == cudaSuccess ? UPIR_OK : cuda_fail(ctx, e, "upir_buf_copy");
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "upir_buf_copy");
+    upir_status st = mark_buffer_use(ctx, src);
+    return st == UPIR_OK ? mark_buffer_use(ctx, dst) : st;
 }
 
 // ------------------------------------------------------- two-step sync steps --
@@ -656,12 +689,14 @@ extern "C" upir_status upir_region_submit(upir_region r, int32_t flags) {
     upir_ctx ctx = r->ctx;
     if (flags & ~UPIR_SUBMIT_GRAPH) return fail(ctx, UPIR_EINVAL, "upir_region_submit: unknown flags");
     if (upir_status st = wait_region_buffers(r)) return st;
-    if (!(flags & UPIR_SUBMIT_GRAPH)) return launch_region_loops(r, ctx->timing);
-    if (!r->gexec) {
-        upir_status st = capture_graph(ctx, {r}, &r->gexec);
-        if (st != UPIR_OK) return st;
+    upir_status st = UPIR_OK;
+    if (!(flags & UPIR_SUBMIT_GRAPH)) {
+        st = launch_region_loops(r, ctx->timing);
+    } else {
+        if (!r->gexec) st = capture_graph(ctx, {r}, &r->gexec);
+        if (st == UPIR_OK) st = launch_graph_timed(ctx, r->gexec, -1);
     }
-    return launch_graph_timed(ctx, r->gexec, -1);
+    return st == UPIR_OK ? mark_region_buffers(r) : st;
 }
 
 // ------------------------------------------------------------------ timing --

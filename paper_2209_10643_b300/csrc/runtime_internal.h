@@ -20,6 +20,7 @@ struct upir_buf_s {
     int refs = 0;          // loops of live regions that use this buffer
     cudaEvent_t ready = nullptr;  // end of the last asynchronous copy
     bool pending = false;         // the compute stream has not waited for it yet
+    cudaEvent_t used = nullptr;   // end of the last compute-stream work that uses it
 };
 
 struct upir_event_s {
@@ -133,6 +134,11 @@ void destroy_batch(upir_batch b);
 // make the compute stream wait for pending asynchronous copies of the
 // buffers a region's loops use
 upir_status wait_region_buffers(upir_region r);
+// Record, on the compute stream, the end of the work submitted so far that
+// uses the buffer (or every buffer of the region): asynchronous copies of a
+// buffer are ordered after that point, not after all submitted work.
+upir_status mark_buffer_use(upir_ctx ctx, upir_buf b);
+upir_status mark_region_buffers(upir_region r);
 
 // Encode a 2D tiled TMA descriptor (row-major [rows][cols] of `elem_bytes`);
 // swizzle_bytes is 0 (none), 32, 64 or 128.

@@ -206,3 +206,51 @@ def test_buf_copy_argument_errors(ctx):
         U.upir_buf_copy(ctx, hbig, hsmall)
     assert e.value.status == U.UPIR_ENOTMAPPED
     U.upir_data_unmap(ctx, hbig)
+
+
+def test_stream_of_recorded_regions_with_async_copies(ctx):
+    """Three slots, each with buffers mapped once (bound to pinned host
+    arrays) and a recorded two-sweep Jacobi region; two passes of: upload the
+    grid and residual start values, seed the second grid on the device, run
+    the region as a graph, download the field and residuals.  Each copy waits
+    only for the work that uses its buffer, yet every result is the oracle's;
+    the second pass, with other grids, reuses the slots behind the first
+    pass's downloads."""
+    side = 72
+    slots = []
+    for k in range(3):
+        pa = pinned(np.zeros((side, side), np.float32))
+        pr = pinned(np.zeros(2, np.float32))
+        ha = U.upir_data_map(ctx, pa.data_ptr(), pa.numel() * 4, U.UPIR_MAP_ALLOC)
+        hb = U.upir_data_map(ctx, 0, pa.numel() * 4, U.UPIR_MAP_ALLOC)
+        hr = U.upir_data_map(ctx, pr.data_ptr(), 8, U.UPIR_MAP_ALLOC)
+        loops = [dict(lb=1, ub=side - 1, step=1, collapse=2, body=U.UPIR_BODY_JACOBI5, bufs=[src, dst],
+                      scalars=[side, side], reductions=[(U.UPIR_RED_MAX, U.UPIR_F32, U.UPIR_TERM_RESID, hr, s)])
+                 for s, (src, dst) in enumerate([(ha, hb), (hb, ha)])]
+        r = U.upir_spmd_region(ctx, 0, 0)
+        for lp in loops:
+            U.upir_loop_checked(ctx, r, U.make_loop_desc(**lp))
+        slots.append((pa, pr, ha, hb, hr, r))
+    for p in range(2):
+        grids = [I.jacobi_grid(side, seed=10 * p + k) for k in range(3)]
+        for (pa, pr, ha, hb, hr, r), g in zip(slots, grids):
+            U.upir_buf_wait(ctx, ha)  # the previous pass's download has left pa
+            U.upir_buf_wait(ctx, hr)
+            pa.numpy()[...] = g
+            pr.numpy()[...] = -np.inf
+            U.upir_data_update_async(ctx, ha, U.UPIR_MAP_TO)
+            U.upir_data_update_async(ctx, hr, U.UPIR_MAP_TO)
+            U.upir_buf_copy(ctx, hb, ha)
+            U.upir_region_submit(r, U.UPIR_SUBMIT_GRAPH)
+            U.upir_data_update_async(ctx, ha, U.UPIR_MAP_FROM)
+            U.upir_data_update_async(ctx, hr, U.UPIR_MAP_FROM)
+        for (pa, pr, ha, hb, hr, r), g in zip(slots, grids):
+            U.upir_buf_wait(ctx, ha)
+            U.upir_buf_wait(ctx, hr)
+            want, res = O.jacobi_run(g, 2, mirror_f32=True)
+            assert np.array_equal(pa.numpy(), want)
+            assert np.array_equal(pr.numpy(), np.asarray(res, np.float32))
+    for pa, pr, ha, hb, hr, r in slots:
+        U.upir_region_destroy(r)
+        for h in (ha, hb, hr):
+            U.upir_data_unmap(ctx, h)
