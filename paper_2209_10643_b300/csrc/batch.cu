@@ -253,9 +253,7 @@ extern "C" upir_status upir_batch_submit(upir_batch b) {
     } else if (upir_status st = launch_graph_timed(ctx, b->gexec, b->mode == UPIR_BATCH_GRAPH ? -2 : -3)) {
         return st;
     }
-    for (upir_region r : b->regions)
-        if (upir_status st = mark_region_buffers(r)) return st;
-    return UPIR_OK;
+    return mark_regions_buffers(b->regions.data(), b->regions.size());
 }
 
 extern "C" upir_status upir_batch_destroy(upir_batch b) {
@@ -318,8 +316,7 @@ done:
     upir_status st2 = build_persistent(b);
     if (st == UPIR_OK) st = st2;
     // the timing runs used every region's buffers
-    for (upir_region r : b->regions)
-        if (upir_status st3 = mark_region_buffers(r); st == UPIR_OK) st = st3;
+    if (upir_status st3 = mark_regions_buffers(b->regions.data(), b->regions.size()); st == UPIR_OK) st = st3;
     if (tiles_out) {
         tiles_out[0] = b->axpy_tile;
         tiles_out[1] = b->jac_rows;

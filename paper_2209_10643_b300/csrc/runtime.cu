@@ -146,7 +146,6 @@ extern "C" upir_status upir_finalize(upir_ctx ctx) {
     for (upir_buf b : ctx->all_bufs) {
         if (b->live && !b->wrapped) dev_free(ctx, b->dev, b->bytes);
         if (b->ready) cudaEventDestroy(b->ready);
-        if (b->used) cudaEventDestroy(b->used);
         delete b;
     }
     ctx->all_bufs.clear();
@@ -155,6 +154,7 @@ extern "C" upir_status upir_finalize(upir_ctx ctx) {
         cudaEventDestroy(t.b);
     }
     for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
+    for (cudaEvent_t e : ctx->use_ring) cudaEventDestroy(e);
     dev_free(ctx, ctx->mlp_scratch, ctx->mlp_scratch_bytes);
     dev_free(ctx, ctx->err_word, 256);
     cudaStreamSynchronize(ctx->stream);
@@ -294,9 +294,8 @@ extern "C" upir_status upir_data_unmap(upir_ctx ctx, upir_buf b) {
     if (e == cudaSuccess) e = e2;
     if (!b->wrapped) dev_free(ctx, b->dev, b->bytes);
     if (b->ready) cudaEventDestroy(b->ready);
-    if (b->used) cudaEventDestroy(b->used);
     b->ready = nullptr;
-    b->used = nullptr;
+    b->last_use = 0;
     b->live = false;
     b->dev = nullptr;
     if (e != cudaSuccess) return cuda_fail(ctx, e, "upir_data_unmap: device->host copy");
@@ -324,7 +323,8 @@ upir_status copy_stream_for(upir_ctx ctx, upir_buf b, bool to_device, bool after
     if (!cs && cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess)
         return cuda_fail(ctx, cudaGetLastError(), "creating a copy stream");
     cudaError_t e = cudaSuccess;
-    if (after_compute && b->used) e = cudaStreamWaitEvent(cs, b->used, 0);
+    if (after_compute && b->last_use > 0)
+        e = cudaStreamWaitEvent(cs, ctx->use_ring[(size_t)(b->last_use % (int64_t)ctx->use_ring.size())], 0);
     if (e == cudaSuccess && b->ready) e = cudaStreamWaitEvent(cs, b->ready, 0);
     *out = cs;
     return e == cudaSuccess ? UPIR_OK : cuda_fail(ctx, e, "ordering a copy stream");
@@ -342,28 +342,44 @@ upir_status mark_pending(upir_ctx ctx, upir_buf b, cudaStream_t cs) {
 
 }  // namespace
 
-upir_status upir::mark_buffer_use(upir_ctx ctx, upir_buf b) {
-    cudaError_t e = cudaSuccess;
-    if (!b->used) e = cudaEventCreateWithFlags(&b->used, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventRecord(b->used, ctx->stream);
-    return e == cudaSuccess ? UPIR_OK : cuda_fail(ctx, e, "recording a buffer's last use");
+namespace {
+
+// Number a new submission and record its ring event on the compute stream.
+upir_status record_submission(upir_ctx ctx, int64_t* k) {
+    constexpr size_t kRing = 64;
+    if (ctx->use_ring.empty()) {
+        ctx->use_ring.assign(kRing, nullptr);
+        for (cudaEvent_t& e : ctx->use_ring)
+            if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
+                return cuda_fail(ctx, cudaGetLastError(), "creating the buffer-use events");
+    }
+    *k = ++ctx->submissions;
+    const cudaError_t e = cudaEventRecord(ctx->use_ring[(size_t)(*k % (int64_t)kRing)], ctx->stream);
+    return e == cudaSuccess ? UPIR_OK : cuda_fail(ctx, e, "recording a submission's end");
 }
 
-upir_status upir::mark_region_buffers(upir_region r) {
-    std::vector<upir_buf> seen;
-    auto add = [&](upir_buf b) {
-        for (upir_buf q : seen)
-            if (q == b) return;
-        seen.push_back(b);
-    };
-    for (auto& lp : r->loops) {
-        for (upir_buf b : lp->bufs) add(b);
-        for (auto& red : lp->reds) add(red.var);
-    }
-    for (upir_buf b : seen)
-        if (upir_status st = mark_buffer_use(r->ctx, b)) return st;
+}  // namespace
+
+upir_status upir::mark_buffer_use(upir_ctx ctx, upir_buf b) {
+    int64_t k = 0;
+    if (upir_status st = record_submission(ctx, &k)) return st;
+    b->last_use = k;
     return UPIR_OK;
 }
+
+upir_status upir::mark_regions_buffers(const upir_region* rs, size_t n) {
+    if (n == 0) return UPIR_OK;
+    int64_t k = 0;
+    if (upir_status st = record_submission(rs[0]->ctx, &k)) return st;
+    for (size_t i = 0; i < n; ++i)
+        for (auto& lp : rs[i]->loops) {
+            for (upir_buf b : lp->bufs) b->last_use = k;
+            for (auto& red : lp->reds) red.var->last_use = k;
+        }
+    return UPIR_OK;
+}
+
+upir_status upir::mark_region_buffers(upir_region r) { return mark_regions_buffers(&r, 1); }
 
 upir_status upir::wait_region_buffers(upir_region r) {
     upir_ctx ctx = r->ctx;
@@ -414,8 +430,7 @@ extern "C" upir_status upir_data_map_async(upir_ctx ctx, void* host, size_t byte
             if (ctx->copy_stream) cudaStreamSynchronize(ctx->copy_stream);
             dev_free(ctx, dev, bytes);
             if (b->ready) cudaEventDestroy(b->ready);
-            if (b->used) cudaEventDestroy(b->used);
-            ctx->all_bufs.erase(b);
+                ctx->all_bufs.erase(b);
             delete b;
             return st;
         }
@@ -468,8 +483,9 @@ extern "C" upir_status upir_buf_copy(upir_ctx ctx, upir_buf dst, upir_buf src) {
     }
     const cudaError_t e = cudaMemcpyAsync(dst->dev, src->dev, src->bytes, cudaMemcpyDeviceToDevice, ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "upir_buf_copy");
-    upir_status st = mark_buffer_use(ctx, src);
-    return st == UPIR_OK ? mark_buffer_use(ctx, dst) : st;
+    upir_status st = mark_buffer_use(ctx, dst);
+    src->last_use = dst->last_use;
+    return st;
 }
 
 // ------------------------------------------------------- two-step sync steps --

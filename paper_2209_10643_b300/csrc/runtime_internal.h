@@ -20,7 +20,7 @@ struct upir_buf_s {
     int refs = 0;          // loops of live regions that use this buffer
     cudaEvent_t ready = nullptr;  // end of the last asynchronous copy
     bool pending = false;         // the compute stream has not waited for it yet
-    cudaEvent_t used = nullptr;   // end of the last compute-stream work that uses it
+    int64_t last_use = 0;         // the compute-stream submission that last used it (0: none)
 };
 
 struct upir_event_s {
@@ -105,6 +105,12 @@ struct upir_ctx_s {
     // so that both copy directions and the computation overlap (created on
     // first use)
     cudaStream_t copy_stream = nullptr, d2h_stream = nullptr;
+    // submissions that use buffers, numbered; submission k records use_ring[k
+    // % size] on the compute stream.  A slot re-recorded by a later
+    // submission marks a later point of the same stream, so waiting on it
+    // stays correct (it only waits for more).
+    std::vector<cudaEvent_t> use_ring;
+    int64_t submissions = 0;
     int run_sched = UPIR_SCHED_STATIC;  // what UPIR_SCHED_RUNTIME loops take
     int64_t run_chunk = 0;
     std::vector<float> cm_params, cm_mean, cm_std;  // cost model for UPIR_SCHED_AUTO (empty: none)
@@ -139,6 +145,7 @@ upir_status wait_region_buffers(upir_region r);
 // buffer are ordered after that point, not after all submitted work.
 upir_status mark_buffer_use(upir_ctx ctx, upir_buf b);
 upir_status mark_region_buffers(upir_region r);
+upir_status mark_regions_buffers(const upir_region* rs, size_t n);
 
 // Encode a 2D tiled TMA descriptor (row-major [rows][cols] of `elem_bytes`);
 // swizzle_bytes is 0 (none), 32, 64 or 128.
