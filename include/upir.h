@@ -508,7 +508,10 @@ upir_status upir_auto_pick(const float* params, const float* feat_mean, const fl
  * |imod_mul| * (n - 1) < 2^62, else UPIR_EINVAL; NULL pointers: UPIR_EINVAL;
  * n == 0 leaves the variables unchanged.  The first call on a device looks up
  * the array's device address (once per device, with that device current), so
- * make that first call before any stream capture.  Every call shares the one
+ * make that first call before any stream capture.  That address is kept for
+ * the life of the process, so do not use this call across a device reset
+ * (cudaDeviceReset or a reset of the primary context), which moves the
+ * array.  Every call shares the one
  * array: calls whose work overlaps on the GPU (other streams, other threads)
  * race and give wrong results; serialize them. */
 upir_status upir_axpy_reduce_noalloc(const float* x, float* y, int64_t n, float a,

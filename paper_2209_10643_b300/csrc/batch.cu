@@ -245,15 +245,19 @@ extern "C" upir_status upir_batch_submit(upir_batch b) {
     upir_ctx ctx = b->ctx;
     for (upir_region r : b->regions)
         if (upir_status st = wait_region_buffers(r)) return st;
+    upir_status st = UPIR_OK;
     if (b->mode == UPIR_BATCH_LAUNCHES) {
         for (upir_region r : b->regions) {
-            upir_status st = launch_region_loops(r, ctx->timing);
-            if (st != UPIR_OK) return st;
+            st = launch_region_loops(r, ctx->timing);
+            if (st != UPIR_OK) break;
         }
-    } else if (upir_status st = launch_graph_timed(ctx, b->gexec, b->mode == UPIR_BATCH_GRAPH ? -2 : -3)) {
-        return st;
+    } else {
+        st = launch_graph_timed(ctx, b->gexec, b->mode == UPIR_BATCH_GRAPH ? -2 : -3);
     }
-    return mark_regions_buffers(b->regions.data(), b->regions.size());
+    // record the buffers' last use even after a failed launch: the launches
+    // that went out before it still use them (the first error is returned)
+    upir_status mst = mark_regions_buffers(b->regions.data(), b->regions.size());
+    return st == UPIR_OK ? mst : st;
 }
 
 extern "C" upir_status upir_batch_destroy(upir_batch b) {

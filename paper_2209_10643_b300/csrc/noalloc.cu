@@ -1,8 +1,9 @@
 // AXPY with its FP32 sum and int64 (mul*i mod m) reductions for callers that
 // cannot allocate device memory.  It runs the same kernels as an AXPY loop
-// recorded through upir_loop (static schedule, planner geometry), but takes
-// its reduction scratch from one fixed array that lives in the library's
-// device image instead of from an allocator.
+// recorded through upir_loop with a static schedule, on teams of 256 units
+// with 8 iterations per unit, but takes its reduction scratch from one fixed
+// array that lives in the library's device image instead of from an
+// allocator.
 #include <cstring>
 #include <mutex>
 
@@ -17,19 +18,23 @@ constexpr int64_t kNoAllocPerWorker = 8;             // iterations per thread (p
 constexpr int64_t kNoAllocMaxTeams = 32768;          // one partial slot per team
 constexpr int64_t kNoAllocMaxGroups = (kNoAllocMaxTeams + kFinSeg - 1) / kFinSeg;
 constexpr int64_t kNoAllocMaxN = kNoAllocMaxTeams * kNoAllocUnits * kNoAllocPerWorker;  // 2^26
-constexpr int kMaxDevices = 64;
 
 // Slot 0 holds the finalize ticket and the (unused) chunk counter, then the
 // group partials, then one partial per team: (1 + 16 + 32768) x 16 B, about
 // 512 KiB, present on every device that loads the library.
 static __device__ __align__(256) Partial g_noalloc_scratch[1 + kNoAllocMaxGroups + kNoAllocMaxTeams];
 
+constexpr int kMaxDevices = 64;
+
 std::mutex g_noalloc_mu;
 void* g_noalloc_addr[kMaxDevices] = {};
 
 // Device address of the scratch array on the current device.  The array's name
 // is only a host-side stand-in, so the address is looked up once per device
-// (with that device current) and cached.
+// (with that device current) and cached.  The cache lives as long as the
+// process: a device reset (cudaDeviceReset, or a reset of the primary
+// context) reloads the module elsewhere and leaves the cached address
+// dangling, so this entry point must not be used across such a reset.
 upir_status noalloc_scratch(Partial** out) {
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess) {

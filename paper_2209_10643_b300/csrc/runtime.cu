@@ -430,7 +430,7 @@ extern "C" upir_status upir_data_map_async(upir_ctx ctx, void* host, size_t byte
             if (ctx->copy_stream) cudaStreamSynchronize(ctx->copy_stream);
             dev_free(ctx, dev, bytes);
             if (b->ready) cudaEventDestroy(b->ready);
-                ctx->all_bufs.erase(b);
+            ctx->all_bufs.erase(b);
             delete b;
             return st;
         }
@@ -712,7 +712,11 @@ extern "C" upir_status upir_region_submit(upir_region r, int32_t flags) {
         if (!r->gexec) st = capture_graph(ctx, {r}, &r->gexec);
         if (st == UPIR_OK) st = launch_graph_timed(ctx, r->gexec, -1);
     }
-    return st == UPIR_OK ? mark_region_buffers(r) : st;
+    // The loops that did launch still use the buffers even when a later one
+    // failed: record their last use whatever the status, so that an
+    // asynchronous copy waits for them; the first error is returned.
+    upir_status mst = mark_region_buffers(r);
+    return st == UPIR_OK ? mst : st;
 }
 
 // ------------------------------------------------------------------ timing --

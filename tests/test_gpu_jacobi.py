@@ -141,3 +141,13 @@ def test_min_reduction_and_partial_row_range(s):
     want[10:50, 1:-1] = v[10:50, 1:-1]
     assert np.array_equal(b, want)
     assert res[0] == np.min(np.abs(v[10:50, 1:-1] - u0[10:50, 1:-1]))
+
+
+def test_grid_8192_beyond_l2(s):
+    """8192^2 (a 537 MB ping-pong set, four times the L2): the sweep kernel
+    streams from HBM; field and residuals bit-exact against the FP32 mirror."""
+    u0 = I.jacobi_grid(8192, seed=1)
+    u, res = run_sweeps(s, u0, 4)
+    um, rm = O.jacobi_run(u0, 4, mirror_f32=True)
+    assert np.array_equal(u.view(np.uint32), um.view(np.uint32))
+    assert np.array_equal(res.view(np.uint32), rm.view(np.uint32))

@@ -65,7 +65,10 @@ def _noalloc_twice(x, y0, n, a, mul, mod):
     return outs
 
 
-@pytest.mark.parametrize("n", [1, 4099, 1_000_003, 1 << 20])
+# 2^20 folds the partials in the loop's last team; past 2048 teams (n > 2^22)
+# a separate finalize kernel folds them in groups, using the array's group
+# partials and its ticket; 2^26 is the documented maximum (32768 teams).
+@pytest.mark.parametrize("n", [1, 4099, 1_000_003, 1 << 20, (1 << 22) + 1, (1 << 24) + 3, MAX_N])
 def test_noalloc_matches_region_api_on_two_calls(n):
     x, y0 = I.axpy_inputs(n, seed=5)
     a, mul, mod = 2.5, 3, 1000
