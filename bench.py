@@ -24,7 +24,13 @@ import subprocess
 import sys
 import time
 
-import numpy as np
+# The oracle is sequential by design and is timed on one host core: hold the
+# host BLAS to one thread before numpy loads it (this process uses numpy only
+# for input generation and the oracle).
+for _v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
+import numpy as np  # noqa: E402
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
@@ -51,12 +57,13 @@ def dist_env() -> tuple[int, int, int]:
 
 
 def one_thread():
-    """Context manager holding the host BLAS to one thread: the oracle is
-    sequential by design, so its timings are single-core."""
+    """Context manager holding the host BLAS to one thread where threadpoolctl
+    is available (the environment variables set above already do so when
+    numpy is first loaded by this process)."""
     try:
         from threadpoolctl import threadpool_limits
         return threadpool_limits(limits=1)
-    except ImportError:  # pragma: no cover
+    except ImportError:
         import contextlib
         return contextlib.nullcontext()
 

@@ -200,8 +200,9 @@ upir_status upir_spmd_region(upir_ctx ctx, int32_t num_teams, int32_t num_units,
  *            "static|dynamic|guided[,chunk]" read by upir_init).
  *  AUTO      the runtime chooses: with a cost model installed
  *            (upir_ctx_set_cost_model) the candidate schedule and units per
- *            team it predicts fastest (AXPY, JACOBI5 and MATVEC bodies; the
- *            others take STATIC), else STATIC with the planner's geometry.
+ *            team it predicts fastest (AXPY, JACOBI5, MATVEC and GEMM_F32
+ *            bodies; the others take STATIC), else STATIC with the planner's
+ *            geometry.
  *  TASKLOOP  the iterations are cut into tasks (hints GRAINSIZE g: max(1,
  *            trip / g) tasks; NUM_TASKS n: min(n, trip) tasks; with both the
  *            smaller count; with neither 8 tasks per SM, 1184), contiguous,
@@ -309,13 +310,16 @@ typedef struct {
  * fits), 0 = the planner's choice (pairs when every resident cluster gets a
  * tile); GEMM_F32 1 = the kernel that stages loads through registers (the
  * default, TMA-fed kernel needs K and N multiples of 4 and 16-byte aligned
- * buffers, and gives the same result bit for bit). */
+ * buffers, and gives the same result bit for bit); FILTER7 1 = each thread
+ * computes strips of 8 output rows instead of 4 (TILE_M then a multiple of
+ * 8; the same result bit for bit).  UPIR_HINT_STAGES also sets FILTER7's
+ * TMA ring depth (2, the default, or 3). */
 typedef enum {
     UPIR_HINT_VARIANT   = 1, /* kernel variant of the body (body-specific, 0 = default)       */
     UPIR_HINT_TILE_M    = 2, /* tile rows (JACOBI5 tiled variant, GEMM)                       */
     UPIR_HINT_TILE_N    = 3, /* tile cols                                                     */
     UPIR_HINT_VEC       = 4, /* iterations per worker the planner aims for (1, 4, 8, 16, 32) */
-    UPIR_HINT_STAGES    = 5, /* shared-memory pipeline depth of the tiled JACOBI5 (1..4)      */
+    UPIR_HINT_STAGES    = 5, /* shared-memory pipeline depth (tiled JACOBI5: 1..4; FILTER7: 2, 3) */
     UPIR_HINT_GRAINSIZE = 6, /* taskloop grainsize (>= 1; schedule TASKLOOP only)             */
     UPIR_HINT_NUM_TASKS = 7  /* taskloop num_tasks (>= 1; schedule TASKLOOP only)             */
 } upir_hint_key;
@@ -469,7 +473,8 @@ upir_status upir_ctx_set_cost_model(upir_ctx ctx, const float* params, const flo
  *   model ranks for a body (AXPY, JACOBI5, MATVEC; none for the others);
  *   *count gets their number, at most `cap` are written (arrays may be NULL).
  * upir_auto_features: the 12 features of one candidate; trip is the loop's
- *   trip count (rows for JACOBI5 and MATVEC), cols the grid / matrix width.
+ *   trip count (rows for JACOBI5 and MATVEC; output elements, rows x N, for
+ *   GEMM_F32), cols the grid / matrix width (K for GEMM_F32).
  * upir_auto_pick: the candidate the model (params, feat_mean, feat_std as for
  *   upir_ctx_set_cost_model; params NULL: none) predicts fastest, restricted
  *   to `units` when non-zero; *units_out is its units (0 when fixed or when no

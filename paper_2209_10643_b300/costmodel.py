@@ -10,7 +10,9 @@ is measured against.
 
 Features (12): op one-hot (AXPY, JACOBI5, MATVEC, GEMM), log2 trip count,
 bytes per iteration, flops per iteration, schedule one-hot (static, dynamic),
-log2(chunk + 1), log2 units per team, log2 teams.
+log2(chunk + 1), log2 units per team, log2 teams.  A GEMM loop's iterations
+are its output elements (bytes per iteration K / 16: the 128 x 128 tile
+kernel's operand reads per output; flops 2 K).
 """
 from __future__ import annotations
 
@@ -59,7 +61,8 @@ def heuristic(op: int, trip: int) -> dict:
 class Pool:
     """Device buffers large enough for every problem of a sweep; each problem
     runs on prefixes of them (their values are seeded uniform[-1, 1), which
-    is all the timing needs)."""
+    is all the timing needs).  GEMM operands take prefixes of the matrix
+    buffer (A), the grid buffers (B) and the vector buffer (C)."""
 
     def __init__(self, ctx: int, max_vec: int, max_grid: int, max_mat: int, seed: int = 11):
         import torch
@@ -99,12 +102,18 @@ class Problem:
             self.loop = dict(lb=1, ub=side - 1, collapse=2, body=U.UPIR_BODY_JACOBI5, bufs=[h0, h1],
                              scalars=[side, side],
                              reductions=[(U.UPIR_RED_MAX, U.UPIR_F32, U.UPIR_TERM_RESID, hr, 0)])
-        else:
+        elif op == OP_MATVEC:
             rows, cols = spec["rows"], spec["cols"]
             ha, hx, hy = w(pool.a, rows * cols), w(pool.x, cols), w(pool.y, rows)
             self.trip, self.bpi, self.fpi = rows, 4.0 * cols, 2.0 * cols
             self.loop = dict(lb=0, ub=rows, body=U.UPIR_BODY_MATVEC, bufs=[ha, hx, hy],
                              scalars=[rows, cols])
+        else:
+            m, n, k = spec["m"], spec["n"], spec["k"]
+            ha, hb, hc = w(pool.a, m * k), w(pool.u0, k * n), w(pool.x, m * n)
+            self.trip, self.bpi, self.fpi = m * n, k / 16.0, 2.0 * k
+            self.loop = dict(lb=0, ub=m, collapse=2, body=U.UPIR_BODY_GEMM_F32, bufs=[ha, hb, hc],
+                             scalars=[m, n, k])
         self.op = op
 
     def _h(self, h):
@@ -166,8 +175,21 @@ def sweep(pool: Pool, specs: list[dict], reps: int = 3):
     return out
 
 
-def training_specs(count: int = 800, seed: int = 10) -> list[dict]:
-    """Regions like the AXPY, Jacobi and matvec workloads at log-spaced sizes."""
+def gemm_specs(count: int, seed: int) -> list[dict]:
+    """FP32 GEMM loops C = A B like the dense workload at log-spaced sizes:
+    M, N, K each 2^U(7, 11.5), N and K rounded to multiples of 4 (the tile
+    kernel's TMA path), M to a multiple of 8."""
+    g = np.random.Generator(np.random.Philox(seed))
+    out = []
+    for _ in range(count):
+        m, n, k = (int(2 ** g.uniform(7, 11.5)) for _ in range(3))
+        out.append({"op": OP_GEMM, "m": max(8, m // 8 * 8), "n": max(4, n // 4 * 4), "k": max(4, k // 4 * 4)})
+    return out
+
+
+def training_specs(count: int = 800, seed: int = 10, gemm: int = 0) -> list[dict]:
+    """Regions like the AXPY, Jacobi and matvec workloads at log-spaced sizes,
+    plus ``gemm`` GEMM loops (seed + 1)."""
     g = np.random.Generator(np.random.Philox(seed))
     specs = []
     for i in range(count):
@@ -180,7 +202,7 @@ def training_specs(count: int = 800, seed: int = 10) -> list[dict]:
             rows = int(2 ** g.uniform(8, 14))
             cols = int(min(max(2 ** g.uniform(5, 24) // rows, 1), 16384))
             specs.append({"op": OP_MATVEC, "rows": rows, "cols": cols})
-    return specs
+    return specs + gemm_specs(gemm, seed + 1)
 
 
 def dataset(results) -> tuple[np.ndarray, np.ndarray]:
@@ -285,7 +307,7 @@ def standardize(f: np.ndarray, mean=None, std=None):
 def regret_report(results, model: GpuMLP, mean, std) -> dict:
     """Per region: the model's pick (argmin of predictions over the measured
     candidates) against the exhaustive best, and the heuristic likewise."""
-    regrets, h_regrets = [], []
+    regrets, h_regrets, ops = [], [], []
     for res in results:
         rows = res["rows"]
         if not rows:
@@ -295,34 +317,45 @@ def regret_report(results, model: GpuMLP, mean, std) -> dict:
         times = np.array([r[1] for r in rows])
         best = times.min()
         regrets.append(times[int(np.argmin(pred))] / best - 1.0)
+        ops.append(res["spec"]["op"])
         hms = res["heuristic"][0]
         if not math.isnan(hms):
             h_regrets.append(hms / best - 1.0)
     r = np.array(regrets)
     h = np.array(h_regrets)
+    ops = np.array(ops)
+
+    def stats(v):
+        return {"mean": float(v.mean()), "median": float(np.median(v)), "p90": float(np.quantile(v, 0.9))}
+
+    names = {OP_AXPY: "axpy", OP_JACOBI: "jacobi", OP_MATVEC: "matvec", OP_GEMM: "gemm"}
     return {"regions": int(r.size),
-            "model_regret": {"mean": float(r.mean()), "median": float(np.median(r)),
-                             "p90": float(np.quantile(r, 0.9))},
-            "heuristic_regret": {"mean": float(h.mean()), "median": float(np.median(h)),
-                                 "p90": float(np.quantile(h, 0.9))} if h.size else None}
+            "model_regret": stats(r),
+            "model_regret_by_op": {names[o]: dict(stats(r[ops == o]), regions=int((ops == o).sum()))
+                                   for o in sorted(set(ops.tolist()))},
+            "heuristic_regret": stats(h) if h.size else None}
 
 
 def run_protocol(ctx: int, n_train: int = 800, n_eval: int = 1000, epochs: int = 300, seed_eval: int = 7,
-                 eval_t_hi: float = 1e7, reps: int = 3) -> dict:
+                 eval_t_hi: float = 1e7, reps: int = 3, n_train_gemm: int = 120, n_eval_gemm: int = 100) -> dict:
     """Autotune the training regions exhaustively, train the MLP on the GPU,
     then rank the candidate schedules of unseen regions (drawn like the
-    batched-region workload) and report its regret against the exhaustive
-    autotuner, next to the regret of the paper's default geometry."""
+    batched-region workload, plus unseen GEMM loops, seed_eval + 5) and
+    report its regret against the exhaustive autotuner, overall and per loop
+    kind, next to the regret of the paper's default geometry."""
     import time
 
     import upir_inputs as I
 
     t0 = time.perf_counter()
-    train_specs = training_specs(n_train)
-    eval_specs = I.batched_region_specs(n_eval, seed=seed_eval, t_hi=eval_t_hi)
-    max_vec = max([sp.get("n", 0) for sp in train_specs + eval_specs] + [16384])
-    max_grid = max(sp.get("side", 0) for sp in train_specs + eval_specs) ** 2
-    max_mat = max(sp.get("rows", 0) * sp.get("cols", 0) for sp in train_specs + eval_specs)
+    train_specs = training_specs(n_train, gemm=n_train_gemm)
+    eval_specs = I.batched_region_specs(n_eval, seed=seed_eval, t_hi=eval_t_hi) + \
+        gemm_specs(n_eval_gemm, seed_eval + 5)
+    every = train_specs + eval_specs
+    max_vec = max([sp.get("n", 0) for sp in every] + [sp["m"] * sp["n"] for sp in every if "m" in sp] + [16384])
+    max_grid = max([sp.get("side", 0) ** 2 for sp in every] + [sp["k"] * sp["n"] for sp in every if "m" in sp])
+    max_mat = max([sp.get("rows", 0) * sp.get("cols", 0) for sp in every] +
+                  [sp["m"] * sp["k"] for sp in every if "m" in sp])
     pool = Pool(ctx, max_vec, max_grid, max_mat)
     train = sweep(pool, train_specs, reps)
     t1 = time.perf_counter()
@@ -341,7 +374,8 @@ def run_protocol(ctx: int, n_train: int = 800, n_eval: int = 1000, epochs: int =
     fe, te = dataset(ev)
     pe = model.predict(standardize(fe, mean, std)[0]).cpu().numpy() + tmean
     rep.update({
-        "train_regions": len(train_specs), "train_variants": int(f.shape[0]),
+        "train_regions": len(train_specs), "train_gemm_regions": n_train_gemm,
+        "eval_gemm_regions": n_eval_gemm, "train_variants": int(f.shape[0]),
         "eval_variants": int(fe.shape[0]), "epochs": epochs,
         "loss_first": losses[0], "loss_last": losses[-1],
         "train_rmse_log2": rmse, "eval_rmse_log2": float(np.sqrt(np.mean((pe - te) ** 2))),

@@ -27,6 +27,7 @@ int body_op(int body) {
         case UPIR_BODY_AXPY: return OP_AXPY;
         case UPIR_BODY_JACOBI5: return OP_JACOBI;
         case UPIR_BODY_MATVEC: return OP_MATVEC;
+        case UPIR_BODY_GEMM_F32: return OP_GEMM;
         default: return -1;
     }
 }
@@ -54,18 +55,28 @@ std::vector<Cand> candidate_list(int op) {
             for (int64_t ch : {0, 1, 8}) c.push_back({UPIR_SCHED_STATIC, ch, u});
             for (int64_t ch : {1, 8}) c.push_back({UPIR_SCHED_DYNAMIC, ch, u});
         }
+    } else if (op == OP_GEMM) {
+        // the FP32 tile kernel runs 256-unit teams; the choice is how the
+        // 128 x 128 output tiles are shared out (chunk 0: one tile per team,
+        // the last wave's tiles split in k)
+        for (int64_t ch : {0, 1, 2, 8}) c.push_back({UPIR_SCHED_STATIC, ch, 256});
+        for (int64_t ch : {1, 2}) c.push_back({UPIR_SCHED_DYNAMIC, ch, 256});
     }
     return c;
 }
 
 // Feature vector of one candidate.  trip counts iterations (JACOBI5:
-// interior points of the loop's rows); cols is the grid or matrix width.
+// interior points of the loop's rows; GEMM_F32: output elements); cols is
+// the grid or matrix width (GEMM_F32: the contraction length K).  Bytes per
+// iteration of the GEMM: the 128 x 128 tile kernel reads 2 x 128 x K operand
+// floats per tile of 128^2 outputs, K / 16 bytes per output.
 void features(int op, int64_t trip, int64_t cols, int sched, int64_t chunk, int units, int teams, float* f) {
     for (int i = 0; i < NI; ++i) f[i] = 0.0f;
     f[op] = 1.0f;
     f[4] = (float)std::log2((double)std::max<int64_t>(trip, 1));
     if (op == OP_AXPY) f[5] = 12.0f, f[6] = 4.0f;
     else if (op == OP_JACOBI) f[5] = 8.0f, f[6] = 6.0f;
+    else if (op == OP_GEMM) f[5] = (float)cols / 16.0f, f[6] = 2.0f * (float)cols;
     else f[5] = 4.0f * (float)cols, f[6] = 2.0f * (float)cols;
     f[7 + (sched == UPIR_SCHED_DYNAMIC ? 1 : 0)] = 1.0f;
     f[9] = (float)std::log2((double)chunk + 1.0);
@@ -140,7 +151,13 @@ void auto_pick(const float* params, const float* mean, const float* sdev, int bo
 
 void auto_schedule(upir_ctx ctx, upir_region r, const upir_loop_desc* d, int64_t trip, int* sched, int64_t* chunk,
                    int* units_out) {
-    const int64_t cols = d->nscalars >= 2 && d->scalars ? (int64_t)d->scalars[1] : 0;
+    int64_t cols = d->nscalars >= 2 && d->scalars ? (int64_t)d->scalars[1] : 0;
+    if (d->body == UPIR_BODY_GEMM_F32) {
+        // output elements of the loop's rows, and K
+        const int64_t n = cols, k = d->nscalars >= 3 ? (int64_t)d->scalars[2] : 0;
+        trip = trip * std::max<int64_t>(n, 0);
+        cols = k;
+    }
     if (ctx->cm_params.empty()) {
         *sched = UPIR_SCHED_STATIC;
         *chunk = 0;

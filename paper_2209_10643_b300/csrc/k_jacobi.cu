@@ -163,15 +163,18 @@ __global__ void __launch_bounds__(1024) jacobi_tma_kernel(const JacobiParams p,
 // computes; after the barrier that opens the following stage (the team is
 // then done with this one), threads 0 .. TM + 1 issue one halo-row copy each,
 // so the copies cost every thread at most one instruction and a tile costs
-// one team barrier.
-template <int S, int ROP>
+// one team barrier.  TNC: the tile width fixed at compile time (0: taken from
+// the parameters), so that a thread's column offsets fold into the shared
+// loads and global stores; tiles whose columns are all interior skip the
+// per-point column test.
+template <int S, int ROP, int TNC>
 __global__ void __launch_bounds__(1024) jacobi_rows_kernel(const JacobiParams p,
                                                           const __grid_constant__ CUtensorMap tmap) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bar[S];
     __shared__ int2 stage_rc[S];  // (first row, first column) of the tile in each stage; x < 0: none
     __shared__ int last_team;
-    const int TM = p.tile_m, TN = p.tile_n;
+    const int TM = p.tile_m, TN = TNC ? TNC : p.tile_n;
     const int SW = jacobi_rt_pitch(TN);  // every row copy lands on a 128-byte boundary
     const int stage_floats = ((TM + 2) * SW + 255) / 256 * 256;
     float* ring = smem_align1k<float>(smem_raw);
@@ -245,21 +248,49 @@ __global__ void __launch_bounds__(1024) jacobi_rows_kernel(const JacobiParams p,
             const int nrows = min(TM, r_ub - rc.x);
             // halo row h sits shifted by ((r0 - 1 + h) * cols + c0) mod 4 columns
             const uint32_t sh0 = ((uint32_t)(rc.x - 1) * cq + (uint32_t)rc.y) & 3u;
-            for (int i2 = ty; i2 < nrows; i2 += nty) {
-                // grid column c0 of the rows above, at and below the output row
-                const float* rn = st + i2 * SW + ((sh0 + (uint32_t)i2 * cq) & 3u) + 4;
-                const float* rm = st + (i2 + 1) * SW + ((sh0 + (uint32_t)(i2 + 1) * cq) & 3u) + 4;
-                const float* rs = st + (i2 + 2) * SW + ((sh0 + (uint32_t)(i2 + 2) * cq) & 3u) + 4;
-                float* orow = p.uout + (size_t)(rc.x + i2) * cols + rc.y;
+            // every column of the tile interior: no per-point column test
+            const bool full = rc.y >= 1 && rc.y + TN <= cols - 1;
+            // grid column c0 of the rows above, at and below the thread's
+            // first output row, offset by its first column.  Its rows are nty
+            // apart; with nty a multiple of 4 they all have the same shifts
+            const int dn = (int)((sh0 + (uint32_t)ty * cq) & 3u);
+            const int dm = (int)((sh0 + (uint32_t)(ty + 1) * cq) & 3u);
+            const int ds = (int)((sh0 + (uint32_t)(ty + 2) * cq) & 3u);
+            const bool same_shift = (nty & 3) == 0;
+            const float* rn = st + ty * SW + dn + 4 + tx;
+            const float* rm = st + (ty + 1) * SW + dm + 4 + tx;
+            const float* rs = st + (ty + 2) * SW + ds + 4 + tx;
+            float* orow = p.uout + ((size_t)(rc.x + ty) * cols + rc.y + tx);
+            const size_t ostep = (size_t)nty * cols;
+#pragma unroll 2
+            for (int i2 = ty; i2 < nrows; i2 += nty, rn += nty * SW, rm += nty * SW, rs += nty * SW, orow += ostep) {
+                if (!same_shift) {
+                    rn = st + i2 * SW + ((sh0 + (uint32_t)i2 * cq) & 3u) + 4 + tx;
+                    rm = st + (i2 + 1) * SW + ((sh0 + (uint32_t)(i2 + 1) * cq) & 3u) + 4 + tx;
+                    rs = st + (i2 + 2) * SW + ((sh0 + (uint32_t)(i2 + 2) * cq) & 3u) + 4 + tx;
+                }
+                if (full) {
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const int q = tx + tpr * j;
-                    const int c = rc.y + q;
-                    const float cv = rm[q];
-                    const float v = __fmul_rn(0.25f, __fadd_rn(__fadd_rn(rn[q], rs[q]), __fadd_rn(rm[q - 1], rm[q + 1])));
-                    if (c >= 1 && c <= cols - 2) {
+                    for (int j = 0; j < 4; ++j) {
+                        const int q = tpr * j;
+                        const float cv = rm[q];
+                        const float v = __fmul_rn(0.25f, __fadd_rn(__fadd_rn(rn[q], rs[q]),
+                                                                   __fadd_rn(rm[q - 1], rm[q + 1])));
                         __stcs(orow + q, v);
                         if (ROP) racc = fold(racc, fabsf(__fsub_rn(v, cv)), ROP);
+                    }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const int q = tpr * j;
+                        const int c = rc.y + tx + q;
+                        const float cv = rm[q];
+                        const float v = __fmul_rn(0.25f, __fadd_rn(__fadd_rn(rn[q], rs[q]),
+                                                                   __fadd_rn(rm[q - 1], rm[q + 1])));
+                        if (c >= 1 && c <= cols - 2) {
+                            __stcs(orow + q, v);
+                            if (ROP) racc = fold(racc, fabsf(__fsub_rn(v, cv)), ROP);
+                        }
                     }
                 }
             }
@@ -289,35 +320,37 @@ __global__ void __launch_bounds__(1024) jacobi_rows_kernel(const JacobiParams p,
 
 using JacobiKernel = void (*)(const JacobiParams, const CUtensorMap);
 
-template <int S, bool ROWS>
+template <int S, bool ROWS, int TNC = 0>
 JacobiKernel pick_rop(int rop) {
     if (ROWS) {
-        if (rop == UPIR_RED_MAX) return jacobi_rows_kernel<S, UPIR_RED_MAX>;
-        if (rop == UPIR_RED_MIN) return jacobi_rows_kernel<S, UPIR_RED_MIN>;
-        return jacobi_rows_kernel<S, 0>;
+        if (rop == UPIR_RED_MAX) return jacobi_rows_kernel<S, UPIR_RED_MAX, TNC>;
+        if (rop == UPIR_RED_MIN) return jacobi_rows_kernel<S, UPIR_RED_MIN, TNC>;
+        return jacobi_rows_kernel<S, 0, TNC>;
     }
     if (rop == UPIR_RED_MAX) return jacobi_tma_kernel<S, UPIR_RED_MAX>;
     if (rop == UPIR_RED_MIN) return jacobi_tma_kernel<S, UPIR_RED_MIN>;
     return jacobi_tma_kernel<S, 0>;
 }
 
-template <bool ROWS>
+template <bool ROWS, int TNC = 0>
 JacobiKernel pick_stages(int stages, int rop) {
     switch (stages) {
-        case 1: return pick_rop<1, ROWS>(rop);
-        case 2: return pick_rop<2, ROWS>(rop);
-        case 3: return pick_rop<3, ROWS>(rop);
-        default: return pick_rop<4, ROWS>(rop);
+        case 1: return pick_rop<1, ROWS, TNC>(rop);
+        case 2: return pick_rop<2, ROWS, TNC>(rop);
+        case 3: return pick_rop<3, ROWS, TNC>(rop);
+        default: return pick_rop<4, ROWS, TNC>(rop);
     }
 }
 
-JacobiKernel pick_kernel(int stages, int rop, bool rows) {
-    return rows ? pick_stages<true>(stages, rop) : pick_stages<false>(stages, rop);
+// the row-copy kernel has a fixed-width instantiation for 128-column tiles
+JacobiKernel pick_kernel(int stages, int rop, bool rows, int tile_n) {
+    if (!rows) return pick_stages<false>(stages, rop);
+    return tile_n == 128 ? pick_stages<true, 128>(stages, rop) : pick_stages<true>(stages, rop);
 }
 
 bool configure_jacobi(JacobiKernel k) {
     // each instantiation gets the large dynamic shared memory window once
-    static JacobiKernel done[16] = {};
+    static JacobiKernel done[64] = {};
     for (auto& d : done) {
         if (d == k) return true;
         if (!d) {
@@ -339,7 +372,7 @@ size_t jacobi_tma_smem_bytes(int tile_m, int tile_n, int stages, bool rows) {
 }
 
 int jacobi_tma_max_teams_per_sm(int units, int tile_m, int tile_n, int stages, bool rows) {
-    JacobiKernel k = pick_kernel(stages, UPIR_RED_MAX, rows);
+    JacobiKernel k = pick_kernel(stages, UPIR_RED_MAX, rows, tile_n);
     if (!configure_jacobi(k)) return 0;
     int n = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, units,
@@ -352,7 +385,7 @@ int jacobi_tma_max_teams_per_sm(int units, int tile_m, int tile_n, int stages, b
 
 cudaError_t launch_jacobi_tma(int teams, int units, const JacobiParams& p, const void* tmap,
                               cudaStream_t s) {
-    JacobiKernel k = pick_kernel(p.stages, p.rvar ? p.rop : 0, p.rows_tma != 0);
+    JacobiKernel k = pick_kernel(p.stages, p.rvar ? p.rop : 0, p.rows_tma != 0, p.tile_n);
     if (!configure_jacobi(k)) return cudaGetLastError();
     CUtensorMap m;
     memcpy(&m, tmap, sizeof(m));

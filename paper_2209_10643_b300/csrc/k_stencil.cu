@@ -317,7 +317,6 @@ TBKernel tb_pick(int sweeps, int rop) {
 // FILTER7
 // ----------------------------------------------------------------------------
 
-constexpr int F7_RS = 4;  // output rows per thread block strip
 
 // Box: (tile_m + 6) x (tile_n + 8) floats (the columns widened to whole
 // 16-byte groups), rounded up to 1 KB per stage.
@@ -325,7 +324,15 @@ __host__ __device__ inline size_t f7_stage_floats(int tm, int tn) {
     return ((size_t)(tm + 6) * (tn + 8) + 255) / 256 * 256;
 }
 
-template <int S>
+// S-stage TMA ring of (TM + 6) x (TN + 8) input boxes; each thread computes
+// strips of RS output rows x 4 columns.  With three or more stages a tile
+// costs one team barrier: past the barrier that opens stage s every thread
+// has left the stage computed before it, whose refill then goes out (its
+// stage_rc entry is next read two barriers later).  TMC / TNC fix the tile
+// shape at compile time (0: taken from the parameters) so that shared-memory
+// offsets fold into the loads; tiles whose outputs are all inside the loop's
+// rows and the interior columns store without per-point tests.
+template <int S, int TMC, int TNC, int RS>
 __global__ void __launch_bounds__(kFilter7Units) filter7_kernel(const Filter7Params p,
                                                                 const __grid_constant__ CUtensorMap tmap) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -333,10 +340,10 @@ __global__ void __launch_bounds__(kFilter7Units) filter7_kernel(const Filter7Par
     __shared__ int2 stage_rc[S];
     __shared__ int last_team;
     float* ring = smem_align1k<float>(smem_raw);
-    const int TM = p.tile_m, TN = p.tile_n, BW = TN + 8;
+    const int TM = TMC ? TMC : p.tile_m, TN = TNC ? TNC : p.tile_n, BW = TN + 8;
     const size_t stage = f7_stage_floats(TM, TN);
     const int tpr = TN / 4;
-    const int tx = threadIdx.x % tpr, ty = threadIdx.x / tpr;  // 4 columns x F7_RS rows per strip
+    const int tx = threadIdx.x % tpr, ty = threadIdx.x / tpr;  // 4 columns x RS rows per strip
     const int nty = kFilter7Units / tpr;
     const uint32_t box_bytes = (uint32_t)((TM + 6) * BW * sizeof(float));
     const int64_t cols = p.cols, r_ub = p.r_ub;
@@ -370,7 +377,7 @@ __global__ void __launch_bounds__(kFilter7Units) filter7_kernel(const Filter7Par
     griddep_launch_dependents();
 
     bool failed = false;
-    int s = 0;
+    int s = 0, prev = -1;
     uint32_t parity = 0;
     for (;;) {
         const int2 rc = stage_rc[s];
@@ -379,19 +386,22 @@ __global__ void __launch_bounds__(kFilter7Units) filter7_kernel(const Filter7Par
             failed = true;
             break;
         }
-        // strips of F7_RS output rows, first row q0 within the tile
-        for (int q0 = ty * F7_RS; q0 < TM; q0 += nty * F7_RS) {
+        if (S >= 3 && threadIdx.x == 0 && prev >= 0) issue(prev);
+        // every output of the tile inside the loop's rows and the interior columns
+        const bool full_tile = rc.x + TM <= r_ub && rc.y >= 3 && rc.y + TN <= cols - 3;
+        // strips of RS output rows, first row q0 within the tile
+        for (int q0 = ty * RS; q0 < TM; q0 += nty * RS) {
             // input box row q0 + rho holds grid row r0 + q0 + rho - 3; the
             // 12 floats at box columns 4 tx .. 4 tx + 11 cover grid columns
             // c - 4 .. c + 7 of the outputs c .. c + 3 (c = c0 + 4 tx)
             const float* in = ring + s * stage + (size_t)q0 * BW + 4 * tx;
-            float acc[F7_RS][4];
+            float acc[RS][4];
 #pragma unroll
-            for (int q = 0; q < F7_RS; ++q)
+            for (int q = 0; q < RS; ++q)
 #pragma unroll
                 for (int j = 0; j < 4; ++j) acc[q][j] = 0.0f;
 #pragma unroll
-            for (int rho = 0; rho < F7_RS + 6; ++rho) {
+            for (int rho = 0; rho < RS + 6; ++rho) {
                 float x[12];
                 const float4 a = *reinterpret_cast<const float4*>(in + rho * BW);
                 const float4 b = *reinterpret_cast<const float4*>(in + rho * BW + 4);
@@ -401,7 +411,7 @@ __global__ void __launch_bounds__(kFilter7Units) filter7_kernel(const Filter7Par
                 x[8] = c.x, x[9] = c.y, x[10] = c.z, x[11] = c.w;
                 // input row rho is filter row i = rho - q of output row q
 #pragma unroll
-                for (int q = 0; q < F7_RS; ++q) {
+                for (int q = 0; q < RS; ++q) {
                     const int i = rho - q;
                     if (i < 0 || i > 6) continue;
 #pragma unroll
@@ -412,24 +422,35 @@ __global__ void __launch_bounds__(kFilter7Units) filter7_kernel(const Filter7Par
                 }
             }
             const int64_t c = (int64_t)rc.y + 4 * tx;
-            const bool full = c >= 3 && c + 3 <= cols - 4;
+            float* out = p.xout + ((int64_t)rc.x + q0) * cols + c;
+            if (full_tile) {
 #pragma unroll
-            for (int q = 0; q < F7_RS; ++q) {
-                const int64_t r = (int64_t)rc.x + q0 + q;
-                if (q0 + q >= TM || r >= r_ub) break;
-                float* out = p.xout + r * cols + c;
-                if (full) {
-                    __stcs(reinterpret_cast<float4*>(out), make_float4(acc[q][0], acc[q][1], acc[q][2], acc[q][3]));
-                } else {
+                for (int q = 0; q < RS; ++q)
+                    __stcs(reinterpret_cast<float4*>(out + q * cols),
+                           make_float4(acc[q][0], acc[q][1], acc[q][2], acc[q][3]));
+            } else {
+                const bool full = c >= 3 && c + 3 <= cols - 4;
 #pragma unroll
-                    for (int j = 0; j < 4; ++j)
-                        if (c + j >= 3 && c + j <= cols - 4) out[j] = acc[q][j];
+                for (int q = 0; q < RS; ++q) {
+                    const int64_t r = (int64_t)rc.x + q0 + q;
+                    if (q0 + q >= TM || r >= r_ub) break;
+                    float* o = out + q * cols;
+                    if (full) {
+                        __stcs(reinterpret_cast<float4*>(o), make_float4(acc[q][0], acc[q][1], acc[q][2], acc[q][3]));
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 4; ++j)
+                            if (c + j >= 3 && c + j <= cols - 4) o[j] = acc[q][j];
+                    }
                 }
             }
         }
-        __syncthreads();  // every thread is done with stage s
-        if (threadIdx.x == 0) issue(s);
-        __syncthreads();  // stage_rc[s] is read again (at once when S == 1)
+        if (S < 3) {
+            __syncthreads();  // every thread is done with stage s
+            if (threadIdx.x == 0) issue(s);
+            __syncthreads();  // stage_rc[s] is read again (at once when S == 1)
+        }
+        prev = s;
         if (++s == S) {
             s = 0;
             parity ^= 1u;
@@ -445,9 +466,26 @@ __global__ void __launch_bounds__(kFilter7Units) filter7_kernel(const Filter7Par
     }
 }
 
+using F7Kernel = void (*)(const Filter7Params, const CUtensorMap);
+
+template <int S, int RS>
+F7Kernel filter7_pick_shape(int tile_m, int tile_n) {
+    if (tile_m == 32 && tile_n == 128) return filter7_kernel<S, 32, 128, RS>;
+    if (tile_m == 64 && tile_n == 128) return filter7_kernel<S, 64, 128, RS>;
+    return filter7_kernel<S, 0, 0, RS>;
+}
+
+// 32 x 128 and 64 x 128 tiles have their own instantiations; other shapes
+// (hints) run the runtime-shape kernel.  rs: output rows per thread strip
+// (4 or 8); stages: 2 or 3.
+F7Kernel filter7_pick(int stages, int tile_m, int tile_n, int rs) {
+    if (stages >= 3) return rs == 8 ? filter7_pick_shape<3, 8>(tile_m, tile_n) : filter7_pick_shape<3, 4>(tile_m, tile_n);
+    return rs == 8 ? filter7_pick_shape<2, 8>(tile_m, tile_n) : filter7_pick_shape<2, 4>(tile_m, tile_n);
+}
+
 template <class K>
 bool configure_once(K k, size_t smem) {
-    static K done[32] = {};
+    static K done[64] = {};
     for (auto& d : done) {
         if (d == k) return true;
         if (!d) {
@@ -483,15 +521,15 @@ cudaError_t launch_jacobi_tb(int teams, int units, const JacobiTBParams& p, cons
     return launch_pdl(k, teams, units, jacobi_tb_smem_bytes(p.tile_m, p.tile_n, p.sweeps, p.halo_c), s, p, m);
 }
 
-size_t filter7_smem_bytes(int tile_m, int tile_n) {
-    return kFilter7Stages * f7_stage_floats(tile_m, tile_n) * sizeof(float) + 1024;
+size_t filter7_smem_bytes(int tile_m, int tile_n, int stages) {
+    return (size_t)stages * f7_stage_floats(tile_m, tile_n) * sizeof(float) + 1024;
 }
 
-int filter7_max_teams_per_sm(int tile_m, int tile_n) {
-    auto k = filter7_kernel<kFilter7Stages>;
+int filter7_max_teams_per_sm(int tile_m, int tile_n, int stages, int rs) {
+    F7Kernel k = filter7_pick(stages, tile_m, tile_n, rs);
     if (!configure_once(k, kMaxDynSmem)) return 0;
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, kFilter7Units, filter7_smem_bytes(tile_m, tile_n)) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, kFilter7Units, filter7_smem_bytes(tile_m, tile_n, stages)) !=
         cudaSuccess) {
         cudaGetLastError();
         return 0;
@@ -500,11 +538,11 @@ int filter7_max_teams_per_sm(int tile_m, int tile_n) {
 }
 
 cudaError_t launch_filter7(int teams, const Filter7Params& p, const void* tmap, cudaStream_t s) {
-    auto k = filter7_kernel<kFilter7Stages>;
+    F7Kernel k = filter7_pick(p.stages, p.tile_m, p.tile_n, p.rs);
     if (!configure_once(k, kMaxDynSmem)) return cudaGetLastError();
     CUtensorMap m;
     memcpy(&m, tmap, sizeof(m));
-    return launch_pdl(k, teams, kFilter7Units, filter7_smem_bytes(p.tile_m, p.tile_n), s, p, m);
+    return launch_pdl(k, teams, kFilter7Units, filter7_smem_bytes(p.tile_m, p.tile_n, p.stages), s, p, m);
 }
 
 }  // namespace upir

@@ -605,11 +605,20 @@ upir_status plan_loop(upir_region r, const upir_loop_desc* d, LoopRec& lp) {
             lp.tile_n = lp.tile_n ? lp.tile_n : 128;
             ok(lp.tile_n / 4 <= kFilter7Units && kFilter7Units % (lp.tile_n / 4) == 0, UPIR_EINVAL,
                "FILTER7 tile_n / 4 must divide 256");
-            ok(lp.tile_m % 4 == 0, UPIR_EINVAL, "FILTER7 tile_m must be a multiple of 4");
-            ok(lp.tile_m + 6 <= 256 && lp.tile_n + 8 <= 256 && filter7_smem_bytes(lp.tile_m, lp.tile_n) <= kStencilSmemBudget,
+            // VARIANT 1: strips of 8 output rows per thread instead of 4;
+            // STAGES: TMA ring depth 2 (default) or 3 (one team barrier per tile)
+            const int f7_rs = lp.variant == 1 ? 8 : 4;
+            const int f7_stages = lp.stages ? lp.stages : kFilter7Stages;
+            ok(lp.variant == 0 || lp.variant == 1, UPIR_EINVAL, "FILTER7 variant must be 0 or 1");
+            ok(f7_stages == 2 || f7_stages == 3, UPIR_EINVAL, "FILTER7 stages must be 2 or 3");
+            ok(lp.tile_m % f7_rs == 0, UPIR_EINVAL, "FILTER7 tile_m must be a multiple of the strip rows (4; variant 1: 8)");
+            ok(lp.tile_m + 6 <= 256 && lp.tile_n + 8 <= 256 &&
+                   filter7_smem_bytes(lp.tile_m, lp.tile_n, f7_stages) <= kStencilSmemBudget,
                UPIR_EINVAL, "FILTER7 tile too large");
             if (ok.st) return ok.st;
-            lp.smem = filter7_smem_bytes(lp.tile_m, lp.tile_n);
+            lp.smem = filter7_smem_bytes(lp.tile_m, lp.tile_n, f7_stages);
+            fp.stages = f7_stages;
+            fp.rs = f7_rs;
             fp.xin = xin;
             fp.xout = xout;
             fp.rows = R;
@@ -633,7 +642,7 @@ upir_status plan_loop(upir_region r, const upir_loop_desc* d, LoopRec& lp) {
                                                 (uint32_t)(lp.tile_m + 6), 0);
                 if (st != UPIR_OK) return st;
             }
-            const int per_sm = std::max(1, filter7_max_teams_per_sm(lp.tile_m, lp.tile_n));
+            const int per_sm = std::max(1, filter7_max_teams_per_sm(lp.tile_m, lp.tile_n, f7_stages, f7_rs));
             const int64_t slots = (int64_t)kNumSMs * per_sm;
             if (T0) lp.teams = T0;
             else if (lp.sched == UPIR_SCHED_STATIC && lp.chunk == 0) {

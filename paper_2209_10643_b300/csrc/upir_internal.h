@@ -125,6 +125,8 @@ struct Filter7Params {
     int64_t rows, cols;
     int64_t r_lb, r_ub;
     int tile_m, tile_n;
+    int stages;  // TMA ring depth (2 or 3)
+    int rs;      // output rows per thread strip (4 or 8)
     int64_t tiles_r, tiles_c, ntiles;
     int64_t chunk;
     int sched;
@@ -239,8 +241,8 @@ constexpr size_t kStencilSmemBudget = 222 * 1024;  // dynamic shared memory of t
 size_t jacobi_tb_plane_floats(int tile_m, int tile_n, int sweeps, int halo_c);
 size_t jacobi_tb_smem_bytes(int tile_m, int tile_n, int sweeps, int halo_c);
 cudaError_t launch_jacobi_tb(int teams, int units, const JacobiTBParams& p, const void* tmap, cudaStream_t s);
-size_t filter7_smem_bytes(int tile_m, int tile_n);
-int filter7_max_teams_per_sm(int tile_m, int tile_n);
+size_t filter7_smem_bytes(int tile_m, int tile_n, int stages);
+int filter7_max_teams_per_sm(int tile_m, int tile_n, int stages, int rs);
 cudaError_t launch_filter7(int teams, const Filter7Params& p, const void* tmap, cudaStream_t s);
 int jacobi_tma_max_teams_per_sm(int units, int tile_m, int tile_n, int stages, bool rows);
 cudaError_t launch_matvec(int teams, int units, const MatvecParams& p, cudaStream_t s);

@@ -1,7 +1,14 @@
-"""End to end on a small scale: autotune training regions, train the MLP on
-the GPU with the library's kernels, and rank unseen regions' schedules.  The
-trained model must beat the method without it (the paper's default CUDA
-geometry) in mean regret against the exhaustive autotuner."""
+"""The learned schedule cost model end to end: autotune training regions
+exhaustively, train the MLP on the GPU with the library's kernels, and rank
+the candidate schedules of unseen regions against the exhaustive autotuner.
+
+- small scale: the trained model beats the method without it (the paper's
+  default CUDA geometry) in mean regret;
+- the target scale: over 300 unseen regions (240 drawn like the batched-region
+  workload, 60 FP32 GEMM loops) the model's mean regret is at most 10 %, and
+  every loop kind, GEMM included, is ranked.  Each candidate's label is the
+  median of five timed runs, so that measurement noise cannot carry the mean
+  over the bound."""
 import pytest
 
 pytestmark = pytest.mark.gpu
@@ -13,9 +20,24 @@ def test_cost_model_beats_the_default_geometry():
     from paper_2209_10643_b300 import costmodel as CM
     ctx = U.upir_init(0)
     try:
-        rep = CM.run_protocol(ctx, n_train=150, n_eval=60, epochs=150, eval_t_hi=2e6, reps=2)
+        rep = CM.run_protocol(ctx, n_train=150, n_eval=60, epochs=150, eval_t_hi=2e6, reps=2,
+                              n_train_gemm=20, n_eval_gemm=10)
     finally:
         U.upir_finalize(ctx)
-    assert rep["regions"] == 60
+    assert rep["regions"] == 70
     assert rep["loss_last"] < rep["loss_first"]
     assert rep["model_regret"]["mean"] < rep["heuristic_regret"]["mean"]
+
+
+def test_cost_model_regret_within_ten_percent():
+    from paper_2209_10643_b300 import costmodel as CM
+    ctx = U.upir_init(0)
+    try:
+        rep = CM.run_protocol(ctx, n_train=800, n_eval=240, epochs=300, reps=5,
+                              n_train_gemm=120, n_eval_gemm=60)
+    finally:
+        U.upir_finalize(ctx)
+    assert rep["regions"] == 300
+    assert set(rep["model_regret_by_op"]) == {"axpy", "jacobi", "matvec", "gemm"}
+    assert rep["model_regret_by_op"]["gemm"]["regions"] == 60
+    assert rep["model_regret"]["mean"] <= 0.10, rep["model_regret"]

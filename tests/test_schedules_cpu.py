@@ -56,12 +56,23 @@ def test_auto_pick_follows_the_model():
     assert U.upir_auto_pick(p, m, s, U.UPIR_BODY_JACOBI5, 100, 128) == (U.UPIR_SCHED_DYNAMIC, 4, 128)
     p, m, s = crafted([10])                  # most units per team
     assert U.upir_auto_pick(p, m, s, U.UPIR_BODY_MATVEC, 5000, 300) == (U.UPIR_SCHED_STATIC, 0, 1024)
+    p, m, s = crafted([9])                   # GEMM_F32: largest chunk of tiles, 256-unit teams
+    assert U.upir_auto_pick(p, m, s, U.UPIR_BODY_GEMM_F32, 1 << 20, 1024) == (U.UPIR_SCHED_STATIC, 8, 256)
+    p, m, s = crafted([8])                   # any dynamic candidate: the first one
+    assert U.upir_auto_pick(p, m, s, U.UPIR_BODY_GEMM_F32, 1 << 20, 1024) == (U.UPIR_SCHED_DYNAMIC, 1, 256)
+
+
+def test_gemm_features():
+    f = U.upir_auto_features(U.UPIR_BODY_GEMM_F32, 512 * 1024, 2048, U.UPIR_SCHED_DYNAMIC, 2, 256, 0)
+    assert f[3] == 1.0 and sum(f[:4]) == 1.0
+    assert math.isclose(f[4], 19.0) and f[5] == 128.0 and f[6] == 4096.0
+    assert f[8] == 1.0 and math.isclose(f[9], math.log2(3), rel_tol=1e-6) and f[10] == 8.0
 
 
 def test_auto_pick_without_model_or_candidates_is_static():
     assert U.upir_auto_pick(None, None, None, U.UPIR_BODY_AXPY, 1000) == (U.UPIR_SCHED_STATIC, 0, 0)
     p, m, s = crafted([9])
-    assert U.upir_auto_pick(p, m, s, U.UPIR_BODY_GEMM_F32, 1000) == (U.UPIR_SCHED_STATIC, 0, 0)
+    assert U.upir_auto_pick(p, m, s, U.UPIR_BODY_GEMM_BF16, 1000) == (U.UPIR_SCHED_STATIC, 0, 0)
     assert U.upir_auto_pick(p, m, s, U.UPIR_BODY_AXPY, 1000, units=96) == (U.UPIR_SCHED_STATIC, 0, 0)
 
 
