@@ -406,10 +406,11 @@ upir_status plan_loop(upir_region r, const upir_loop_desc* d, LoopRec& lp) {
                 // teams of 512 units on 64 x 128 tiles: four rows per thread
                 // and 1024 threads per SM (4096^2 grid, 100 sweeps: 2.139 ms;
                 // 256 units 2.157 ms, 1024 units 2.616 ms).  Row copies: two
-                // stages (4095^2 grid: 28.9 us per sweep; 256 units, 32 rows
-                // and three stages 32.0 us)
-                if (!U0 && !auto_units) lp.units = 512;
-                lp.tile_m = lp.tile_m ? lp.tile_m : 64;
+                // stages, teams of 256 units on 32 x 128 tiles, four teams
+                // per SM (4095^2 grid: 25.9 us per sweep; 512 units on
+                // 64-row tiles 26.7 us; three stages 28.1 us)
+                if (!U0 && !auto_units) lp.units = rows_tma ? 256 : 512;
+                lp.tile_m = lp.tile_m ? lp.tile_m : (rows_tma ? 32 : 64);
                 lp.tile_n = lp.tile_n ? lp.tile_n : 128;
                 lp.tile_n = (int)std::min<int64_t>(lp.tile_n, 4 * (int64_t)lp.units);
                 jp.stages = lp.stages ? lp.stages : (rows_tma ? 2 : 3);

@@ -217,6 +217,23 @@ def test_filter7_ranges_schedules_tiles(s, lb, ub, sched, chunk, teams, hints):
                  lb=lb, ub=ub)
 
 
+F7_VARIANTS = [
+    # (tile_m, tile_n, stages, variant): fixed-shape kernels, 3-stage ring,
+    # 8-row strips (variant 1), runtime-shape kernel
+    (32, 128, 2, 0), (64, 128, 2, 0), (32, 128, 3, 0), (32, 128, 2, 1), (64, 128, 3, 1),
+    (16, 64, 2, 0), (40, 64, 3, 0), (24, 32, 2, 1)]
+
+
+@pytest.mark.parametrize("tm,tn,stages,variant", F7_VARIANTS)
+@pytest.mark.parametrize("rows,cols,lb,ub", [(200, 196, 3, 197), (301, 520, 40, 290)])
+def test_filter7_variants_bit_exact(s, tm, tn, stages, variant, rows, cols, lb, ub):
+    x = I.jacobi_grid(max(rows, cols), seed=17)[:rows, :cols].copy()
+    w = filter_weights(18)
+    hints = ((U.UPIR_HINT_TILE_M, tm), (U.UPIR_HINT_TILE_N, tn), (U.UPIR_HINT_STAGES, stages),
+             (U.UPIR_HINT_VARIANT, variant))
+    check_filter(x, w, run_filter(s, x, w, lb=lb, ub=ub, hints=hints), lb=lb, ub=ub)
+
+
 def test_filter7_full_size_4096_sampled_rows(s):
     x = I.jacobi_grid(4096, seed=14)
     w = filter_weights(15)
