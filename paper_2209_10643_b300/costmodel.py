@@ -12,7 +12,10 @@ Features (12): op one-hot (AXPY, JACOBI5, MATVEC, GEMM), log2 trip count,
 bytes per iteration, flops per iteration, schedule one-hot (static, dynamic),
 log2(chunk + 1), log2 units per team, log2 teams.  A GEMM loop's iterations
 are its output elements (bytes per iteration K / 16: the 128 x 128 tile
-kernel's operand reads per output; flops 2 K).
+kernel's operand reads per output; flops 2 K).  Units and teams are the
+geometry the planner launches the candidate with; schedule(auto) computes the
+same teams for every candidate by planning the loop without device scratch,
+so the features the model is trained on are the features it is asked about.
 """
 from __future__ import annotations
 
@@ -92,29 +95,25 @@ class Problem:
         if op == OP_AXPY:
             n = spec["n"]
             hx, hy, hd = w(pool.x, n), w(pool.y, n), w(pool.var, 1)
-            self.trip, self.bpi, self.fpi = n, 12.0, 4.0
             self.loop = dict(lb=0, ub=n, body=U.UPIR_BODY_AXPY, bufs=[hx, hy], scalars=[2.5],
                              reductions=[(U.UPIR_RED_ADD, U.UPIR_F32, U.UPIR_TERM_XY, hd, 0)])
         elif op == OP_JACOBI:
             side = spec["side"]
             h0, h1, hr = w(pool.u0, side * side), w(pool.u1, side * side), w(pool.var, 1, 1)
-            self.trip, self.bpi, self.fpi = (side - 2) ** 2, 8.0, 6.0
             self.loop = dict(lb=1, ub=side - 1, collapse=2, body=U.UPIR_BODY_JACOBI5, bufs=[h0, h1],
                              scalars=[side, side],
                              reductions=[(U.UPIR_RED_MAX, U.UPIR_F32, U.UPIR_TERM_RESID, hr, 0)])
         elif op == OP_MATVEC:
             rows, cols = spec["rows"], spec["cols"]
             ha, hx, hy = w(pool.a, rows * cols), w(pool.x, cols), w(pool.y, rows)
-            self.trip, self.bpi, self.fpi = rows, 4.0 * cols, 2.0 * cols
             self.loop = dict(lb=0, ub=rows, body=U.UPIR_BODY_MATVEC, bufs=[ha, hx, hy],
                              scalars=[rows, cols])
         else:
             m, n, k = spec["m"], spec["n"], spec["k"]
             ha, hb, hc = w(pool.a, m * k), w(pool.u0, k * n), w(pool.x, m * n)
-            self.trip, self.bpi, self.fpi = m * n, k / 16.0, 2.0 * k
             self.loop = dict(lb=0, ub=m, collapse=2, body=U.UPIR_BODY_GEMM_F32, bufs=[ha, hb, hc],
                              scalars=[m, n, k])
-        self.op = op
+        self.op, self.trip, self.bpi, self.fpi = spec_shape(spec)
 
     def _h(self, h):
         self.handles.append(h)
@@ -131,7 +130,8 @@ class Problem:
         return r
 
     def measure(self, cand: dict, reps: int = 3) -> tuple[float, np.ndarray]:
-        """Median device time (ms) of the loop under `cand`, and its features."""
+        """Median device time (ms) of the loop under `cand`, and its features
+        (with the units and teams the planner launched it with)."""
         r = self.region(cand)
         teams, units = U.upir_region_loop_geometry(r, 0)
         U.upir_region_submit(r, 0)  # warm-up
@@ -336,6 +336,73 @@ def regret_report(results, model: GpuMLP, mean, std) -> dict:
             "heuristic_regret": stats(h) if h.size else None}
 
 
+def spec_shape(spec: dict) -> tuple[int, int, float, float]:
+    """(op, trip, bytes per iteration, flops per iteration) of a region spec,
+    as ``Problem`` and the runtime's features count them."""
+    op = spec["op"]
+    if op == OP_AXPY:
+        return op, spec["n"], 12.0, 4.0
+    if op == OP_JACOBI:
+        return op, (spec["side"] - 2) ** 2, 8.0, 6.0
+    if op == OP_MATVEC:
+        return op, spec["rows"], 4.0 * spec["cols"], 2.0 * spec["cols"]
+    return op, spec["m"] * spec["n"], spec["k"] / 16.0, 2.0 * spec["k"]
+
+
+class Trained:
+    """A trained model with the feature statistics and target offset it was
+    trained with."""
+
+    def __init__(self, model: "GpuMLP", mean, std, tmean: float):
+        self.model, self.mean, self.std, self.tmean = model, mean, std, tmean
+
+    def predict_us(self, specs: list[dict]) -> np.ndarray:
+        """Predicted time (microseconds) of each region under its best
+        candidate schedule: the time schedule(auto) expects for it."""
+        rows, owner = [], []
+        for k, sp in enumerate(specs):
+            op, trip, bpi, fpi = spec_shape(sp)
+            for c in candidates(op):
+                rows.append(features(op, trip, bpi, fpi, c["sched"], c["chunk"], c["units"], c["teams"]))
+                owner.append(k)
+        pred = self.model.predict(standardize(np.stack(rows), self.mean, self.std)[0]).cpu().numpy() + self.tmean
+        best = np.full(len(specs), np.inf)
+        np.minimum.at(best, np.array(owner), pred)
+        return np.exp2(best)
+
+
+def pool_for(ctx: int, specs: list[dict]) -> Pool:
+    """A pool large enough for every spec of ``specs``."""
+    max_vec = max([sp.get("n", 0) for sp in specs] + [sp["m"] * sp["n"] for sp in specs if "m" in sp] + [16384])
+    max_grid = max([sp.get("side", 0) ** 2 for sp in specs] + [sp["k"] * sp["n"] for sp in specs if "m" in sp] + [1])
+    max_mat = max([sp.get("rows", 0) * sp.get("cols", 0) for sp in specs] +
+                  [sp["m"] * sp["k"] for sp in specs if "m" in sp] + [1])
+    return Pool(ctx, max_vec, max_grid, max_mat)
+
+
+def train(ctx: int, pool: Pool, train_specs: list[dict], epochs: int = 300, reps: int = 3):
+    """Exhaustive autotuning of the training regions, then the MLP trained
+    on the GPU.  Returns the trained model, the training log and timings."""
+    import time
+
+    import upir_inputs as I
+
+    t0 = time.perf_counter()
+    results = sweep(pool, train_specs, reps)
+    t1 = time.perf_counter()
+    f, t = dataset(results)
+    fs, mean, std = standardize(f)
+    tmean = float(t.mean())
+    model = GpuMLP(ctx, I.mlp_init(seed=9))
+    losses = model.train(fs, t - tmean, epochs=epochs)
+    pred = model.predict(fs).cpu().numpy() + tmean
+    rmse = float(np.sqrt(np.mean((pred - t) ** 2)))
+    t2 = time.perf_counter()
+    log = {"variants": int(f.shape[0]), "losses": losses, "rmse_log2": rmse,
+           "seconds": {"autotune_train": t1 - t0, "train": t2 - t1}}
+    return Trained(model, mean, std, tmean), log
+
+
 def run_protocol(ctx: int, n_train: int = 800, n_eval: int = 1000, epochs: int = 300, seed_eval: int = 7,
                  eval_t_hi: float = 1e7, reps: int = 3, n_train_gemm: int = 120, n_eval_gemm: int = 100) -> dict:
     """Autotune the training regions exhaustively, train the MLP on the GPU,
@@ -347,38 +414,24 @@ def run_protocol(ctx: int, n_train: int = 800, n_eval: int = 1000, epochs: int =
 
     import upir_inputs as I
 
-    t0 = time.perf_counter()
     train_specs = training_specs(n_train, gemm=n_train_gemm)
     eval_specs = I.batched_region_specs(n_eval, seed=seed_eval, t_hi=eval_t_hi) + \
         gemm_specs(n_eval_gemm, seed_eval + 5)
-    every = train_specs + eval_specs
-    max_vec = max([sp.get("n", 0) for sp in every] + [sp["m"] * sp["n"] for sp in every if "m" in sp] + [16384])
-    max_grid = max([sp.get("side", 0) ** 2 for sp in every] + [sp["k"] * sp["n"] for sp in every if "m" in sp])
-    max_mat = max([sp.get("rows", 0) * sp.get("cols", 0) for sp in every] +
-                  [sp["m"] * sp["k"] for sp in every if "m" in sp])
-    pool = Pool(ctx, max_vec, max_grid, max_mat)
-    train = sweep(pool, train_specs, reps)
-    t1 = time.perf_counter()
-    f, t = dataset(train)
-    fs, mean, std = standardize(f)
-    tmean = float(t.mean())
-    model = GpuMLP(ctx, I.mlp_init(seed=9))
-    losses = model.train(fs, t - tmean, epochs=epochs)
-    pred = model.predict(fs).cpu().numpy() + tmean
-    rmse = float(np.sqrt(np.mean((pred - t) ** 2)))
+    pool = pool_for(ctx, train_specs + eval_specs)
+    tr, log = train(ctx, pool, train_specs, epochs, reps)
     t2 = time.perf_counter()
     ev = sweep(pool, eval_specs, reps)
     t3 = time.perf_counter()
 
-    rep = regret_report(ev, model, mean, std)
+    rep = regret_report(ev, tr.model, tr.mean, tr.std)
     fe, te = dataset(ev)
-    pe = model.predict(standardize(fe, mean, std)[0]).cpu().numpy() + tmean
+    pe = tr.model.predict(standardize(fe, tr.mean, tr.std)[0]).cpu().numpy() + tr.tmean
     rep.update({
         "train_regions": len(train_specs), "train_gemm_regions": n_train_gemm,
-        "eval_gemm_regions": n_eval_gemm, "train_variants": int(f.shape[0]),
+        "eval_gemm_regions": n_eval_gemm, "train_variants": log["variants"],
         "eval_variants": int(fe.shape[0]), "epochs": epochs,
-        "loss_first": losses[0], "loss_last": losses[-1],
-        "train_rmse_log2": rmse, "eval_rmse_log2": float(np.sqrt(np.mean((pe - te) ** 2))),
-        "seconds": {"autotune_train": t1 - t0, "train": t2 - t1, "autotune_eval": t3 - t2},
+        "loss_first": log["losses"][0], "loss_last": log["losses"][-1],
+        "train_rmse_log2": log["rmse_log2"], "eval_rmse_log2": float(np.sqrt(np.mean((pe - te) ** 2))),
+        "seconds": dict(log["seconds"], autotune_eval=t3 - t2),
     })
     return rep

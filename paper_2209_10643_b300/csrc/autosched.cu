@@ -118,10 +118,13 @@ int64_t loop_trip(int op, int64_t trip, int64_t cols) {
 
 }  // namespace
 
-// The cost model's pick for a loop; `units` / `teams` fixed by the region
-// (0: free).  Bodies without candidates take STATIC with chunk 0.
+// The cost model's pick for a loop; `units` fixed by the region (0: free).
+// teams_of(candidate) gives the teams feature of a candidate (the teams the
+// planner launches it with), or < 0 for a candidate that cannot run the loop.
+// Bodies without candidates take STATIC with chunk 0.
+template <class TeamsOf>
 void auto_pick(const float* params, const float* mean, const float* sdev, int body, int64_t trip, int64_t cols,
-               int units, int teams, int* sched, int64_t* chunk, int* units_out) {
+               int units, TeamsOf teams_of, int* sched, int64_t* chunk, int* units_out) {
     *sched = UPIR_SCHED_STATIC;
     *chunk = 0;
     *units_out = 0;
@@ -132,6 +135,8 @@ void auto_pick(const float* params, const float* mean, const float* sdev, int bo
     bool have = false;
     for (const Cand& c : cands) {
         if (units && c.units != units) continue;
+        const int teams = teams_of(c);
+        if (teams < 0) continue;
         float f[NI];
         features(op, loop_trip(op, trip, cols), cols, c.sched, c.chunk, c.units, teams, f);
         for (int i = 0; i < NI; ++i) {
@@ -147,6 +152,27 @@ void auto_pick(const float* params, const float* mean, const float* sdev, int bo
             *units_out = units ? 0 : c.units;
         }
     }
+}
+
+// The teams the planner launches a loop with under one candidate schedule:
+// the loop is planned on a scratch region with the candidate's schedule,
+// chunk and units and no device scratch; -1 when the candidate cannot run it.
+// The context's last error message is left as it was.
+int planned_teams(upir_region r, const upir_loop_desc* d, const Cand& c) {
+    upir_ctx ctx = r->ctx;
+    const std::string saved = ctx->err;
+    upir_region_s tmp;
+    tmp.ctx = ctx;
+    tmp.teams = r->teams;
+    tmp.units = r->units ? r->units : c.units;
+    upir_loop_desc dd = *d;
+    dd.sched = c.sched;
+    dd.chunk = c.chunk;
+    LoopRec lp;
+    lp.dry = true;
+    const upir_status st = plan_loop(&tmp, &dd, lp);
+    ctx->err = saved;
+    return st == UPIR_OK ? lp.teams : -1;
 }
 
 void auto_schedule(upir_ctx ctx, upir_region r, const upir_loop_desc* d, int64_t trip, int* sched, int64_t* chunk,
@@ -165,7 +191,7 @@ void auto_schedule(upir_ctx ctx, upir_region r, const upir_loop_desc* d, int64_t
         return;
     }
     auto_pick(ctx->cm_params.data(), ctx->cm_mean.data(), ctx->cm_std.data(), d->body, trip, cols, r->units,
-              r->teams, sched, chunk, units_out);
+              [&](const Cand& c) { return planned_teams(r, d, c); }, sched, chunk, units_out);
 }
 
 }  // namespace upir
@@ -216,7 +242,8 @@ extern "C" upir_status upir_auto_pick(const float* params, const float* feat_mea
     if (!sched || !chunk || !units_out || trip < 0) return UPIR_EINVAL;
     int s = 0, u = 0;
     int64_t c = 0;
-    auto_pick(params, feat_mean, feat_std, body, trip, cols, units, teams, &s, &c, &u);
+    auto_pick(params, feat_mean, feat_std, body, trip, cols, units, [teams](const Cand&) { return teams; }, &s, &c,
+              &u);
     *sched = s;
     *chunk = c;
     *units_out = u;

@@ -51,6 +51,7 @@ struct LoopRec {
     int kind = LK_ELEM;
     bool skip = false;       // zero-trip loop: nothing to launch
     bool holds_refs = false;
+    bool dry = false;        // planning only (schedule(auto) scoring): no device scratch
     void* scratch = nullptr;
     size_t scratch_bytes = 0;
     // Scratch bytes [counter_off, counter_off + counter_bytes) hold counters

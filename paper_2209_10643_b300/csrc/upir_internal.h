@@ -14,6 +14,7 @@ constexpr int kGroup = 1024;             // blocks per first-level group of a st
 constexpr int kFinSeg = 2048;            // partial slots folded by one finalize block
 constexpr int UPIR_ERR_WAIT_TIMEOUT = 1;  // device error word: a bounded wait ran out
 constexpr int kNumSMs = 148;
+constexpr double kL2Bytes = 126.0 * 1024 * 1024;  // last-level cache of the GPU
 
 // One reduction partial: FP32 (sum, compensation) and an int64 value.
 struct __align__(16) Partial {

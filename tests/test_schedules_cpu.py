@@ -14,7 +14,9 @@ def test_candidate_lists():
     ax = U.upir_auto_candidates(U.UPIR_BODY_AXPY)
     ja = U.upir_auto_candidates(U.UPIR_BODY_JACOBI5)
     mv = U.upir_auto_candidates(U.UPIR_BODY_MATVEC)
-    assert (len(ax), len(ja), len(mv)) == (28, 15, 20)
+    gm = U.upir_auto_candidates(U.UPIR_BODY_GEMM_F32)
+    assert (len(ax), len(ja), len(mv), len(gm)) == (28, 15, 20, 6)
+    assert all(un == 256 for _, _, un in gm)
     assert U.upir_auto_candidates(U.UPIR_BODY_GEMM_BF16) == []
     for lst in (ax, ja, mv):
         assert len(set(lst)) == len(lst)
@@ -26,7 +28,8 @@ def test_candidate_lists():
 @pytest.mark.parametrize("op,body,trip,cols,bpi,fpi,ftrip", [
     (CM.OP_AXPY, U.UPIR_BODY_AXPY, 1 << 20, 0, 12.0, 4.0, 1 << 20),
     (CM.OP_JACOBI, U.UPIR_BODY_JACOBI5, 510, 512, 8.0, 6.0, 510 * 510),
-    (CM.OP_MATVEC, U.UPIR_BODY_MATVEC, 3000, 700, 2800.0, 1400.0, 3000)])
+    (CM.OP_MATVEC, U.UPIR_BODY_MATVEC, 3000, 700, 2800.0, 1400.0, 3000),
+    (CM.OP_GEMM, U.UPIR_BODY_GEMM_F32, 512 * 640, 384, 24.0, 768.0, 512 * 640)])
 def test_runtime_features_match_the_cost_models(op, body, trip, cols, bpi, fpi, ftrip):
     for sched, chunk, units, teams in [(0, 0, 256, 0), (1, 4096, 1024, 37), (0, 7, 128, 1)]:
         want = CM.features(op, ftrip, bpi, fpi, sched, chunk, units, teams)
