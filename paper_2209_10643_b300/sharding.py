@@ -12,6 +12,8 @@ Two ways to use N ranks:
     rows, then exchanges one halo row with each neighbour; the per-sweep
     max residuals are combined with one allreduce(max);
   - matvec: a block of rows of A per rank, x replicated, y gathered;
+  - GEMM: 2D output tiles on a grid of ranks, the A and B panels broadcast
+    along process rows and columns one K panel at a time;
   - AXPY + sum: a block of iterations per rank, the per-rank FP32 sums
     gathered and folded in rank order (deterministic for a given N);
   - batches: regions assigned by longest-processing-time over their
@@ -357,3 +359,139 @@ def exchange_in_process(plans: list, bufs: list) -> None:
         last = a.local_rows - 2
         bufs[r + 1][0].copy_(bufs[r][last])
         bufs[r][last + 1].copy_(bufs[r + 1][1])
+
+
+# ------------------------------------------------------------------- GEMM --
+
+def rank_grid(world: int) -> tuple[int, int]:
+    """(process rows, process columns) for ``world`` ranks: a square grid
+    when ``world`` is a square, else one column (row panels)."""
+    q = int(round(world ** 0.5))
+    return (q, q) if q * q == world else (world, 1)
+
+
+class GemmPanels:
+    """C = A B over a pr x pc grid of ranks, 2D output tiles with A and B
+    broadcast one panel at a time (SUMMA).
+
+    Rank r = i pc + j owns C's block (rows block i of [0, M), columns block
+    j of [0, N)).  K is split into q = pc panels (q = 1 on a one-column
+    grid).  The inputs start distributed as 2D blocks: rank (i, j) holds
+    A[rows_i, panel_j] and B[panel_i, cols_j] (on a one-column grid, A's row
+    block and all of B).  Step p broadcasts A[rows_i, panel_p] from rank
+    (i, p) along process row i and B[panel_p, cols_j] from rank (p, j) along
+    process column j; every rank adds A_ip B_pj into its block.  The panels
+    are added in order p = 0, 1, ..., so a rank's result does not depend on
+    message timing."""
+
+    def __init__(self, M: int, N: int, K: int, world: int, rank: int):
+        self.M, self.N, self.K, self.world, self.rank = M, N, K, world, rank
+        self.pr, self.pc = rank_grid(world)
+        self.i, self.j = divmod(rank, self.pc)
+        self.rows = block_range(0, M, self.pr, self.i)
+        self.cols = block_range(0, N, self.pc, self.j)
+        self.q = self.pc
+        self.row_groups = self.col_groups = None
+
+    def panel(self, p: int) -> tuple[int, int]:
+        return block_range(0, self.K, self.q, p)
+
+    def make_groups(self) -> None:
+        """Process-row and process-column groups (every rank creates every
+        group, in the same order)."""
+        dist = _dist()
+        if dist is None or self.world == 1:
+            return
+        rows = [dist.new_group([i * self.pc + j for j in range(self.pc)]) for i in range(self.pr)]
+        cols = [dist.new_group([i * self.pc + j for i in range(self.pr)]) for j in range(self.pc)]
+        self.row_groups, self.col_groups = rows, cols
+
+    def a_local(self, A):
+        k0, k1 = self.panel(self.j)
+        return A[self.rows[0]:self.rows[1], k0:k1]
+
+    def b_local(self, B):
+        k0, k1 = self.panel(self.i) if self.q > 1 else (0, self.K)
+        return B[k0:k1, self.cols[0]:self.cols[1]]
+
+    def run(self, gemm_acc: Callable, a_mine, b_mine, c_local, new_panel: Callable) -> None:
+        """``gemm_acc(a_p, b_p, c, first)`` computes c = a_p b_p (first) or
+        c += a_p b_p; ``new_panel(shape, like)`` makes a receive buffer.  On a
+        one-column grid there is one panel and no message."""
+        dist = _dist()
+        if self.q == 1 or dist is None:
+            gemm_acc(a_mine, b_mine, c_local, True)
+            return
+        for p in range(self.q):
+            k0, k1 = self.panel(p)
+            a_p = a_mine if p == self.j else new_panel((self.rows[1] - self.rows[0], k1 - k0), a_mine)
+            b_p = b_mine if p == self.i else new_panel((k1 - k0, self.cols[1] - self.cols[0]), b_mine)
+            dist.broadcast(a_p, self.i * self.pc + p, group=self.row_groups[self.i])
+            dist.broadcast(b_p, p * self.pc + self.j, group=self.col_groups[self.j])
+            gemm_acc(a_p, b_p, c_local, p == 0)
+
+    def gather(self, c_local):
+        """The full C on every rank (test and check helper, not a step)."""
+        import torch
+
+        dist = _dist()
+        if dist is None or self.world == 1:
+            return c_local.clone()
+        bm = block_range(0, self.M, self.pr, 0)[1]
+        bn = block_range(0, self.N, self.pc, 0)[1]
+        piece = torch.zeros((bm, bn), dtype=c_local.dtype, device=c_local.device)
+        piece[:c_local.shape[0], :c_local.shape[1]] = c_local
+        parts = [torch.empty_like(piece) for _ in range(self.world)]
+        dist.all_gather(parts, piece)
+        out = torch.empty((self.M, self.N), dtype=c_local.dtype, device=c_local.device)
+        for r in range(self.world):
+            i, j = divmod(r, self.pc)
+            r0, r1 = block_range(0, self.M, self.pr, i)
+            c0, c1 = block_range(0, self.N, self.pc, j)
+            out[r0:r1, c0:c1] = parts[r][:r1 - r0, :c1 - c0]
+        return out
+
+
+class UpirGemmAcc:
+    """The per-rank step of ``GemmPanels`` on the GPU, through the region
+    runtime: c = a b by the FP32 GEMM loop, or for a later panel t = a b
+    followed by c += t as an AXPY loop with a = 1 (one rounding per element,
+    the panels added in order).  Tensors are FP32, row-major, contiguous, on
+    the device of the context, whose stream must be torch's current stream."""
+
+    def __init__(self, ctx: int):
+        import paper_2209_10643_b300 as U
+
+        self.U, self.ctx, self.tmp = U, ctx, None
+
+    def _map(self, t):
+        return self.U.upir_data_map_device(self.ctx, t.data_ptr(), t.numel() * 4)
+
+    def __call__(self, a, b, c, first: bool) -> None:
+        import torch
+
+        U = self.U
+        m, k = a.shape
+        n = b.shape[1]
+        out = c
+        if not first:
+            if self.tmp is None or self.tmp.numel() < m * n:
+                self.tmp = torch.empty(m * n, dtype=torch.float32, device=c.device)
+            out = self.tmp[:m * n].view(m, n)
+        ha, hb, ho = self._map(a), self._map(b), self._map(out)
+        hs = [ha, hb, ho]
+        r = U.upir_spmd_region(self.ctx, 0, 0)
+        try:
+            U.upir_loop_checked(self.ctx, r, U.make_loop_desc(lb=0, ub=m, collapse=2, body=U.UPIR_BODY_GEMM_F32,
+                                                              bufs=[ha, hb, ho], scalars=[m, n, k]))
+            if not first:
+                hc = self._map(c)
+                hs.append(hc)
+                U.upir_loop_checked(self.ctx, r, U.make_loop_desc(lb=0, ub=m * n, body=U.UPIR_BODY_AXPY,
+                                                                  bufs=[ho, hc], scalars=[1.0]))
+            U.upir_region_submit(r, 0)
+            U.upir_ctx_wait(self.ctx)
+        finally:
+            U.upir_region_destroy(r)
+            for h in hs:
+                U.upir_data_unmap(self.ctx, h)

@@ -59,3 +59,28 @@ def test_row_blocks_on_gpu_equal_single_rank_oracle(ctx, world, rows, cols, swee
     um, rm = O.jacobi_run(u0, sweeps, mirror_f32=True)
     assert np.array_equal(full.view(np.uint32), um.view(np.uint32))
     assert np.array_equal(resid.view(np.uint32), rm.view(np.uint32))
+
+
+@pytest.mark.parametrize("world,m,n,k", [(4, 300, 260, 200), (2, 130, 96, 64), (9, 200, 136, 96)])
+def test_gemm_panels_on_gpu_equal_oracle(ctx, world, m, n, k):
+    """The 2D-tile GEMM partition with every rank's panel steps on the GPU
+    (the FP32 GEMM loop for the first panel, the GEMM into a temporary and an
+    AXPY with a = 1 for the others), the panel broadcasts replaced by slicing
+    the full operands in one process; C within the FP32 GEMM tolerance."""
+    from paper_2209_10643_b300.sharding import GemmPanels, UpirGemmAcc
+    a, b = I.gemm_inputs(m, n, k)
+    acc = UpirGemmAcc(ctx)
+    c = np.zeros((m, n), np.float32)
+    for r in range(world):
+        plan = GemmPanels(m, n, k, world, r)
+        (r0, r1), (c0, c1) = plan.rows, plan.cols
+        cd = torch.zeros((r1 - r0, c1 - c0), dtype=torch.float32, device="cuda")
+        for p in range(plan.q):
+            k0, k1 = plan.panel(p) if plan.q > 1 else (0, k)
+            ap = torch.from_numpy(a[r0:r1, k0:k1].copy()).cuda()
+            bp = torch.from_numpy(b[k0:k1, c0:c1].copy()).cuda()
+            torch.cuda.current_stream().synchronize()
+            acc(ap, bp, cd, p == 0)
+        c[r0:r1, c0:c1] = cd.cpu().numpy()
+    want = O.gemm(a, b)
+    assert np.linalg.norm(c - want) <= 1e-5 * np.linalg.norm(want)

@@ -1,12 +1,13 @@
-"""Multi-rank logic on CPU process groups (gloo, world sizes 2 and 3, and 5
-where some ranks own no rows).
+"""Multi-rank logic on CPU process groups (gloo, world sizes 2, 3 and 4, and
+5 where some ranks own no rows).
 
 Each rank computes its share with the oracle; the gathered results must equal
 the single-rank oracle: the Jacobi field and every per-sweep residual bit for
 bit (§5: a reduction's partials combined across the teams of an SPMD region,
-§3.1), matvec rows exactly on integer data and to FP64 rounding on random
-data, AXPY's y bit for bit and its sum within the FP32 tolerance, and every
-region of a batch run exactly once."""
+§3.1), matvec rows and the GEMM's 2D output tiles (panels broadcast along
+process rows and columns) exactly on integer data and to FP64 rounding on
+random data, AXPY's y bit for bit and its sum within the FP32 tolerance, and
+every region of a batch run exactly once."""
 import os
 import socket
 
@@ -18,8 +19,8 @@ import torch.multiprocessing as mp
 
 import upir_inputs as I
 from oracle import upir_oracle as O
-from paper_2209_10643_b300.sharding import (AxpyBlocks, JacobiRowBlocks, MatvecRowBlocks,
-                                            aggregate_throughput, block_range, region_bytes,
+from paper_2209_10643_b300.sharding import (AxpyBlocks, GemmPanels, JacobiRowBlocks, MatvecRowBlocks,
+                                            aggregate_throughput, block_range, rank_grid, region_bytes,
                                             shard_lpt)
 
 
@@ -261,3 +262,57 @@ def test_batch_lpt_runs_every_region_once(world):
         else:
             want = float(np.sum(O.matvec(arr["A"], arr["x"])))
         assert merged[i] == want
+
+
+# ------------------------------------------------------------------ GEMM --
+
+def test_rank_grid_and_panels():
+    assert [rank_grid(w) for w in (1, 2, 3, 4, 6, 9)] == [(1, 1), (2, 1), (3, 1), (2, 2), (6, 1), (3, 3)]
+    g = [GemmPanels(10, 7, 9, 4, r) for r in range(4)]
+    assert [(x.i, x.j, x.rows, x.cols) for x in g] == [(0, 0, (0, 5), (0, 4)), (0, 1, (0, 5), (4, 7)),
+                                                      (1, 0, (5, 10), (0, 4)), (1, 1, (5, 10), (4, 7))]
+    assert [g[0].panel(p) for p in range(2)] == [(0, 5), (5, 9)]
+
+
+def _gemm_worker(rank, world, port, out, m, n, k, integer):
+    _init(rank, world, port)
+    try:
+        if integer:
+            a = I.small_int_matrix(m, k, -5, 5, seed=21)
+            b = I.small_int_matrix(k, n, -5, 5, seed=22)
+        else:
+            a, b = I.gemm_inputs(m, n, k)
+        plan = GemmPanels(m, n, k, world, rank)
+        plan.make_groups()
+        a_mine = torch.from_numpy(plan.a_local(a).astype(np.float64).copy())
+        b_mine = torch.from_numpy(plan.b_local(b).astype(np.float64).copy())
+        c = torch.zeros((plan.rows[1] - plan.rows[0], plan.cols[1] - plan.cols[0]), dtype=torch.float64)
+
+        def gemm_acc(ap, bp, cc, first):
+            prod = torch.from_numpy(O.gemm(ap.numpy(), bp.numpy()))
+            if first:
+                cc.copy_(prod)
+            else:
+                cc.add_(prod)
+
+        plan.run(gemm_acc, a_mine, b_mine, c, lambda shape, like: torch.empty(shape, dtype=like.dtype))
+        out[rank] = plan.gather(c).numpy().copy()
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world,m,n,k,integer", [(4, 37, 29, 23, True), (4, 40, 33, 50, False),
+                                                 (2, 21, 19, 17, True), (3, 30, 20, 10, False)])
+def test_gemm_panels_equal_single_rank_oracle(world, m, n, k, integer):
+    out = _spawn(_gemm_worker, world, m, n, k, integer)
+    if integer:
+        a = I.small_int_matrix(m, k, -5, 5, seed=21)
+        b = I.small_int_matrix(k, n, -5, 5, seed=22)
+    else:
+        a, b = I.gemm_inputs(m, n, k)
+    want = O.gemm(a, b)
+    for r in range(world):
+        if integer:
+            assert np.array_equal(out[r], want), r
+        else:
+            assert np.max(np.abs(out[r] - want)) <= 1e-12 * np.max(np.abs(want)), r
