@@ -966,6 +966,8 @@ def run_sharded(args) -> None:
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     rt = Runtime(local_rank)
+    if world > 1:
+        dist.barrier()  # a collective of every rank before the first point-to-point batch
     plan = JacobiRowBlocks(N_GRID, N_GRID, world, rank)
     u0 = I.jacobi_grid(N_GRID, seed=1)
     a = torch.from_numpy(plan.slab(u0).copy()).cuda()
