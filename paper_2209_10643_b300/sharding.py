@@ -15,7 +15,8 @@ Two ways to use N ranks:
   - GEMM: 2D output tiles on a grid of ranks, the A and B panels broadcast
     along process rows and columns one K panel at a time;
   - AXPY + sum: a block of iterations per rank, the per-rank FP32 sums
-    gathered and folded in rank order (deterministic for a given N);
+    gathered in rank order and folded by the runtime's own compensated
+    reduction (deterministic for a given N);
   - batches: regions assigned by longest-processing-time over their
     predicted (cost-model) or algorithmic costs, no exchange.
 
@@ -255,50 +256,74 @@ class MatvecRowBlocks:
 
 # ------------------------------------------------------------ AXPY + sum --
 
-def two_sum_f32(a, b):
-    """Knuth's TwoSum on FP32 torch scalars: s + e == a + b exactly."""
-    s = a + b
-    bp = s - a
-    ap = s - bp
-    return s, (a - ap) + (b - bp)
-
-
 class AxpyBlocks:
     """AXPY + reduction(+) split into a block of iterations per rank.
 
     Each rank runs the loop on its block and reduces into its own FP32
-    variable; ``combine_sum`` gathers the N per-rank sums and folds them in
-    rank order with compensation (TwoSum), so the result does not depend on
-    message timing, and adds the variable's value from before the loop
-    once.  Integer reductions combine exactly with one allreduce(sum)."""
+    variable (starting from 0); ``combine_sum`` gathers the N per-rank sums
+    in rank order and hands them to ``fold(parts, init)``, which adds them in
+    that order, with compensation, to the variable's value from before the
+    loop: the result does not depend on message timing.  On GPUs the fold is
+    the runtime's own reduction (``UpirSumFold``).  Integer reductions
+    combine exactly with one allreduce(sum)."""
 
     def __init__(self, n: int, world: int, rank: int, group=None):
         self.n, self.world, self.rank, self.group = n, world, rank, group
         self.lo, self.hi = block_range(0, n, world, rank)
 
-    def combine_sum(self, local_sum, init: float = 0.0):
-        """local_sum: a one-element FP32 tensor holding this rank's sum with
-        no initial value added.  Returns the one-element FP32 total."""
+    def combine_sum(self, local_sum, init: float, fold: Callable):
+        """local_sum: a one-element FP32 tensor holding this rank's sum.
+        Returns fold(the N sums as one tensor in rank order, init)."""
         import torch
 
         dist = _dist()
         if dist is None or self.world == 1:
-            parts = [local_sum]
+            parts = local_sum.reshape(1)
         else:
-            parts = [torch.empty_like(local_sum) for _ in range(self.world)]
-            dist.all_gather(parts, local_sum, group=self.group)
-        s = torch.tensor([init], dtype=torch.float32, device=local_sum.device)
-        c = torch.zeros_like(s)
-        for p in parts:
-            s, e = two_sum_f32(s, p.to(torch.float32))
-            c = c + e
-        return s + c
+            parts = torch.empty(self.world, dtype=local_sum.dtype, device=local_sum.device)
+            dist.all_gather(list(parts.split(1)), local_sum.reshape(1), group=self.group)
+        return fold(parts, init)
 
     def combine_int(self, local):
         dist = _dist()
         if dist is not None and self.world > 1:
             dist.all_reduce(local, op=dist.ReduceOp.SUM, group=self.group)
         return local
+
+
+class UpirSumFold:
+    """The fold of ``AxpyBlocks.combine_sum`` on the GPU, through the region
+    runtime: the N per-rank sums as the y of an AXPY loop with a = 0 (which
+    leaves them unchanged) whose reduction(+) of y, compensated and in a
+    fixed order, lands in a one-element variable holding ``init``."""
+
+    def __init__(self, ctx: int):
+        import paper_2209_10643_b300 as U
+
+        self.U, self.ctx = U, ctx
+
+    def __call__(self, parts, init: float):
+        import torch
+
+        U = self.U
+        n = parts.numel()
+        zeros = torch.zeros(n, dtype=torch.float32, device=parts.device)
+        var = torch.full((1,), float(init), dtype=torch.float32, device=parts.device)
+        y = parts.to(torch.float32).contiguous().clone()
+        torch.cuda.current_stream().synchronize()
+        hs = [U.upir_data_map_device(self.ctx, t.data_ptr(), t.numel() * 4) for t in (zeros, y, var)]
+        r = U.upir_spmd_region(self.ctx, 0, 0)
+        try:
+            U.upir_loop_checked(self.ctx, r, U.make_loop_desc(
+                lb=0, ub=n, body=U.UPIR_BODY_AXPY, bufs=hs[:2], scalars=[0.0],
+                reductions=[(U.UPIR_RED_ADD, U.UPIR_F32, U.UPIR_TERM_Y, hs[2], 0)]))
+            U.upir_region_submit(r, 0)
+            U.upir_ctx_wait(self.ctx)
+        finally:
+            U.upir_region_destroy(r)
+            for h in hs:
+                U.upir_data_unmap(self.ctx, h)
+        return var
 
 
 # ------------------------------------------------- the GPU side of a rank --

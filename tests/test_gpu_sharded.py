@@ -84,3 +84,23 @@ def test_gemm_panels_on_gpu_equal_oracle(ctx, world, m, n, k):
         c[r0:r1, c0:c1] = cd.cpu().numpy()
     want = O.gemm(a, b)
     assert np.linalg.norm(c - want) <= 1e-5 * np.linalg.norm(want)
+
+
+@pytest.mark.parametrize("world", [1, 2, 3, 8])
+def test_rank_partials_folded_by_the_runtime(ctx, world):
+    """The cross-rank fold of per-rank FP32 sums (the AXPY partition) runs as
+    the runtime's own compensated reduction: the ranks' sums of an AXPY
+    problem, folded with a prior value, match the oracle's sum of the whole
+    problem within the FP32 tolerance."""
+    from paper_2209_10643_b300.sharding import AxpyBlocks, UpirSumFold
+    n = 100_003
+    x, y = I.axpy_inputs(n, seed=31)
+    want_y = O.axpy(2.5, x, y)
+    parts = []
+    for r in range(world):
+        lo, hi = AxpyBlocks(n, world, r).lo, AxpyBlocks(n, world, r).hi
+        parts.append(np.float32(O.reduce_f64(O.RED_ADD, 0.0, want_y[lo:hi])))
+    fold = UpirSumFold(ctx)
+    got = float(fold(torch.tensor(parts, dtype=torch.float32, device="cuda"), -3.25).item())
+    want = O.reduce_f64(O.RED_ADD, -3.25, want_y)
+    assert abs(got - want) <= 1e-5 * abs(want)

@@ -193,7 +193,11 @@ def _axpy_worker(rank, world, port, out, n):
         lo, hi = plan.lo, plan.hi
         yb = O.axpy(2.5, x[lo:hi], y[lo:hi])
         local = torch.tensor([np.float32(O.reduce_f64(O.RED_ADD, 0.0, yb))], dtype=torch.float32)
-        total = plan.combine_sum(local, init=0.75)
+        def fold(parts, init):
+            # the oracle's sum of the rank-ordered partials and the prior value
+            return torch.tensor([np.float32(O.reduce_f64(O.RED_ADD, init, parts.numpy()))])
+
+        total = plan.combine_sum(local, 0.75, fold)
         imod = torch.tensor([O.reduce_i64(O.RED_ADD, 0, O.imod_terms(lo, 1, hi - lo, 3, 1000))],
                             dtype=torch.int64)
         plan.combine_int(imod)
