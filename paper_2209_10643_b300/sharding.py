@@ -147,9 +147,10 @@ class JacobiRowBlocks:
         return local[1:self.local_rows - 1] if self.local_rows else local[0:0]
 
     def exchange(self, buf) -> None:
-        """Halo exchange on a local slab (a 2D torch tensor): own first row to
-        the rank above and own last row to the rank below, the neighbours'
-        rows into the halo rows.  All messages of a step are posted together."""
+        """Halo exchange on a local slab (a contiguous 2D torch tensor): own
+        first row to the rank above and own last row to the rank below, the
+        neighbours' rows received in place into the halo rows.  All messages
+        of a step are posted together."""
         dist = _dist()
         if dist is None or self.local_rows == 0:
             return
@@ -334,10 +335,11 @@ class UpirJacobiSweeper:
     slab's own rows, its residual into element k of the residual vector),
     recorded once and submitted as a CUDA graph per sweep.
 
-    ``ta``, ``tb`` (the two slabs, local_rows x cols FP32) and ``tres`` (FP32
-    [sweeps]) are device tensors; the context's stream must be torch's
-    current stream when the exchange runs, so that the halo messages are
-    ordered after the sweep that wrote the rows and before the next one."""
+    ``ta``, ``tb`` (the two slabs, local_rows x cols FP32, contiguous) and
+    ``tres`` (FP32 [sweeps]) are device tensors that must outlive the sweeper
+    (their memory is mapped, not copied); the context's stream must be
+    torch's current stream when the exchange runs, so that the halo messages
+    are ordered after the sweep that wrote the rows and before the next one."""
 
     def __init__(self, ctx: int, plan: JacobiRowBlocks, ta, tb, tres, sweeps: int, graph: bool = True):
         import paper_2209_10643_b300 as U
