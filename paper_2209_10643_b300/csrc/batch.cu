@@ -118,7 +118,12 @@ upir_status build_persistent(upir_batch b) {
         else if (R.op == BOP_JACOBI) {
             R.tiles_c = ceil_div(R.cols, kBatchJacCols);
             R.tiles = ceil_div(R.trip, b->jac_rows) * R.tiles_c;
-        } else R.tiles = ceil_div(R.trip, b->mv_rows);
+        } else {
+            // rows of at most 64 columns go one per unit (a team takes 256 of
+            // them); wider rows one per warp, mv_rows to an item
+            R.tile_rows = R.cols <= kBatchNarrowCols ? kBatchUnits : b->mv_rows;
+            R.tiles = ceil_div(R.trip, R.tile_rows);
+        }
         R.slot0 = nslots;
         if (R.op == BOP_AXPY && R.fop) nslots += R.tiles;
         nitems += R.tiles;

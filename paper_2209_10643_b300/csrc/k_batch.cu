@@ -250,12 +250,26 @@ __device__ __forceinline__ void matvec_tile(const BatchParams& P, const BatchReg
     const float* const x = R.in1;
     float* const y = R.out;
     const int64_t cols = R.cols;
-    const int64_t r0 = R.lb + t * P.mv_rows;
-    const int64_t r1 = min(r0 + (int64_t)P.mv_rows, R.lb + R.trip);
+    const int64_t r0 = R.lb + t * R.tile_rows;
+    const int64_t r1 = min(r0 + (int64_t)R.tile_rows, R.lb + R.trip);
     // the tile's rows of A are requested into L2 at once, so that a warp's
     // dot product, a chain of a few load rounds per row, waits on L2 rather
     // than on DRAM
     if (threadIdx.x == 0 && r1 > r0) prefetch_l2_range(A + r0 * cols, (size_t)(r1 - r0) * cols * sizeof(float));
+    if (cols <= kBatchNarrowCols) {
+        // narrow rows: one per unit, its dot product a chain of fused
+        // multiply-adds in column order (a warp per row would leave most of
+        // its lanes idle and pay a butterfly per row)
+        const int64_t r = r0 + threadIdx.x;
+        if (r < r1) {
+            const float* a = A + r * cols;
+            float acc = 0.0f;
+#pragma unroll 4
+            for (int64_t j = 0; j < cols; ++j) acc = __fmaf_rn(__ldg(a + j), __ldg(x + j), acc);
+            y[r] = acc;
+        }
+        return;
+    }
     for (int64_t r = r0 + warp; r < r1; r += nw) {
         const float v = row_dot(A + r * cols, x, cols, lane);
         if (lane == 0) y[r] = v;

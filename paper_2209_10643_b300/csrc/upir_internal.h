@@ -190,7 +190,7 @@ struct BatchRegion {
     int op;             // BatchOp
     int fop;            // reduction operator of the FP32 clause, 0 if none
     int fterm;          // AXPY: TERM_Y or TERM_XY
-    int pad;
+    int tile_rows;      // MATVEC: rows per work item
     const float* in0;   // AXPY x | JACOBI u_in | MATVEC A
     const float* in1;   // MATVEC x
     float* out;         // AXPY y | JACOBI u_out | MATVEC y
@@ -221,6 +221,7 @@ struct BatchParams {
 constexpr int kBatchUnits = 256;
 constexpr int kBatchJacCols = 128;
 constexpr int kBatchMaxJacRows = 32;
+constexpr int kBatchNarrowCols = 64;  // MATVEC rows this narrow take one unit each
 
 // Host-side launchers (one per kernel family).
 // fop / iop: the loop's FP32 / int64 reduction operator, 0 when it has none.
