@@ -306,7 +306,8 @@ def _gemm_worker(rank, world, port, out, m, n, k, integer):
 
 
 @pytest.mark.parametrize("world,m,n,k,integer", [(4, 37, 29, 23, True), (4, 40, 33, 50, False),
-                                                 (2, 21, 19, 17, True), (3, 30, 20, 10, False)])
+                                                 (2, 21, 19, 17, True), (3, 30, 20, 10, False),
+                                                 (4, 1, 3, 1, True), (3, 2, 4, 5, True)])
 def test_gemm_panels_equal_single_rank_oracle(world, m, n, k, integer):
     out = _spawn(_gemm_worker, world, m, n, k, integer)
     if integer:
