@@ -460,25 +460,29 @@ upir_status upir_ctx_set_run_schedule(upir_ctx ctx, int32_t sched, int64_t chunk
  * `feat_std` the 12 feature means and standard deviations the inputs are
  * standardised with (std <= 0 counts as 1).  All host pointers, copied.  The
  * features of a candidate are: body one-hot (AXPY, JACOBI5, MATVEC, GEMM),
- * log2 trip (JACOBI5: interior points), bytes and flops per iteration (AXPY
- * 12, 4; JACOBI5 8, 6; MATVEC 4 cols, 2 cols), schedule one-hot (static,
- * dynamic), log2(chunk + 1), log2 units, log2 teams (0: planner-sized).  The
- * prediction uses bfloat16-rounded weights and FP32 arithmetic on the host.
- * params NULL removes the model. */
+ * log2 trip (JACOBI5: interior points; GEMM_F32: output elements), bytes and
+ * flops per iteration (AXPY 12, 4; JACOBI5 8, 6; MATVEC 4 cols, 2 cols;
+ * GEMM_F32 K / 16, 2 K), schedule one-hot (static, dynamic), log2(chunk + 1),
+ * log2 units, log2 teams: the teams the planner launches the candidate with
+ * (found by planning the loop without device scratch when it is recorded).
+ * The prediction uses bfloat16-rounded weights and FP32 arithmetic on the
+ * host.  params NULL removes the model. */
 upir_status upir_ctx_set_cost_model(upir_ctx ctx, const float* params, const float* feat_mean,
                                     const float* feat_std);
 
 /* Host-only helpers of the auto schedule (no GPU needed).
  * upir_auto_candidates: the candidate (sched, chunk, units) triples the cost
- *   model ranks for a body (AXPY, JACOBI5, MATVEC; none for the others);
+ *   model ranks for a body (AXPY, JACOBI5, MATVEC, GEMM_F32; none for the
+ *   others);
  *   *count gets their number, at most `cap` are written (arrays may be NULL).
  * upir_auto_features: the 12 features of one candidate; trip is the loop's
  *   trip count (rows for JACOBI5 and MATVEC; output elements, rows x N, for
  *   GEMM_F32), cols the grid / matrix width (K for GEMM_F32).
  * upir_auto_pick: the candidate the model (params, feat_mean, feat_std as for
  *   upir_ctx_set_cost_model; params NULL: none) predicts fastest, restricted
- *   to `units` when non-zero; *units_out is its units (0 when fixed or when no
- *   candidate applies, the schedule then being STATIC with chunk 0).
+ *   to `units` when non-zero, every candidate scored with the same `teams`
+ *   feature (no loop is planned here); *units_out is its units (0 when fixed
+ *   or when no candidate applies, the schedule then being STATIC with chunk 0).
  * EINVAL for bad pointers or sizes. */
 upir_status upir_auto_candidates(int32_t body, int32_t* sched, int64_t* chunk, int32_t* units, int32_t cap,
                                  int32_t* count);

@@ -151,3 +151,14 @@ def test_grid_8192_beyond_l2(s):
     um, rm = O.jacobi_run(u0, 4, mirror_f32=True)
     assert np.array_equal(u.view(np.uint32), um.view(np.uint32))
     assert np.array_equal(res.view(np.uint32), rm.view(np.uint32))
+
+
+def test_beyond_l2_tiles_on_ragged_grid(s):
+    """5124 x 5128 (the two grids outgrow the L2, so the planner takes 64 x 64
+    tiles; neither side a multiple of the tile): 3 sweeps bit-exact against
+    the FP32 mirror."""
+    u0 = I.jacobi_grid(5124, 5128, seed=9)
+    u, res = run_sweeps(s, u0, 3)
+    um, rm = O.jacobi_run(u0, 3, mirror_f32=True)
+    assert np.array_equal(u.view(np.uint32), um.view(np.uint32))
+    assert np.array_equal(res.view(np.uint32), rm.view(np.uint32))
