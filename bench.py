@@ -817,9 +817,10 @@ def extra_batch(rt: Runtime, count: int = 512, check: bool = True) -> dict:
 
 
 def extra_costmodel(rt: Runtime) -> dict:
-    """Learned schedule cost model: trained on ~17k timed variants of 800
-    AXPY/Jacobi/matvec regions, ranking the candidate schedules of 1000 unseen
-    regions drawn like the batched-region workload (seed 7)."""
+    """Learned schedule cost model: trained on ~20k timed variants of 950
+    AXPY/Jacobi/matvec regions and 120 FP32 GEMM loops, ranking the candidate
+    schedules of 1000 unseen regions drawn like the batched-region workload
+    (seed 7) and of 100 unseen GEMM loops."""
     from paper_2209_10643_b300 import costmodel as CM
     return CM.run_protocol(rt.ctx)
 

@@ -403,7 +403,7 @@ def train(ctx: int, pool: Pool, train_specs: list[dict], epochs: int = 300, reps
     return Trained(model, mean, std, tmean), log
 
 
-def run_protocol(ctx: int, n_train: int = 800, n_eval: int = 1000, epochs: int = 300, seed_eval: int = 7,
+def run_protocol(ctx: int, n_train: int = 950, n_eval: int = 1000, epochs: int = 300, seed_eval: int = 7,
                  eval_t_hi: float = 1e7, reps: int = 3, n_train_gemm: int = 120, n_eval_gemm: int = 100) -> dict:
     """Autotune the training regions exhaustively, train the MLP on the GPU,
     then rank the candidate schedules of unseen regions (drawn like the
