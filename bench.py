@@ -430,8 +430,47 @@ def extra_axpy(rt: Runtime, n: int, pk: dict) -> dict:
                                   12 * n, pk))
     else:
         out["frac_hbm"] = out["GB/s"] / pk["hbm_gbs"]
+        out.update(axpy_stream(rt, n, pk))
     for h in (hx, hy, hf, hi):
         U.upir_data_unmap(rt.ctx, h)
+    return out
+
+
+def axpy_stream(rt: Runtime, n: int, pk: dict, count: int = 20) -> dict:
+    """A stream of ``count`` independent single-loop AXPY regions of the same
+    size, each on its own x, y and reduction variables (together more than
+    the L2 holds, so each loop reads cold data), recorded as one graph and
+    timed with one event pair: the per-region time when regions follow one
+    another, next to the latency of one region alone."""
+    U = rt.U
+    loops = []
+    for k in range(count):
+        x, y = I.axpy_inputs(n, seed=100 + k)
+        fs, si = np.zeros(1, np.float32), np.zeros(1, np.int64)
+        hx, hy = rt.map(x, U.UPIR_MAP_TO, True), rt.map(y, U.UPIR_MAP_TOFROM, True)
+        hf, hi = rt.map(fs, U.UPIR_MAP_TOFROM, True), rt.map(si, U.UPIR_MAP_TOFROM, True)
+        loops.append(dict(lb=0, ub=n, body=U.UPIR_BODY_AXPY, bufs=[hx, hy], scalars=[2.5, 3, 1000],
+                          reductions=[(U.UPIR_RED_ADD, U.UPIR_F32, U.UPIR_TERM_Y, hf, 0),
+                                      (U.UPIR_RED_ADD, U.UPIR_I64, U.UPIR_TERM_IMOD, hi, 0)]))
+    out = {}
+    # with the implicit barrier after each loop, and with nowait (independent
+    # loops: the next may start while this one finishes)
+    for key, nowait in (("stream", 0), ("stream_nowait", 1)):
+        r = rt.region([dict(lp, nowait=nowait if k < count - 1 else 0) for k, lp in enumerate(loops)])
+        U.upir_region_submit(r, U.UPIR_SUBMIT_GRAPH)
+        ms, _ = timed_whole(rt, lambda: U.upir_region_submit(r, U.UPIR_SUBMIT_GRAPH), 20)
+        U.upir_region_destroy(r)
+        per = ms / count
+        gbs = 12 * n / (per / 1e3) / 1e9
+        out.update({f"{key}_us_per_region": per * 1e3, f"{key}_GB/s": gbs, f"{key}_frac_hbm": gbs / pk["hbm_gbs"]})
+    for h in rt.handles:
+        U.upir_data_unmap(rt.ctx, h)
+    rt.handles.clear()
+    out.update({"stream_regions": count,
+                "stream_timing": f"{count} independent single-loop regions on their own buffers "
+                                 f"({count * 8 * n / 1e6:.0f} MB, more than the L2) recorded as the loops of one "
+                                 "region, one CUDA graph, one event pair around it, L2 flushed first; "
+                                 "stream_nowait: the loops marked nowait"})
     return out
 
 

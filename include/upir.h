@@ -334,7 +334,9 @@ typedef enum {
  * worker asks next.  W = teams * units for element bodies; the MATVEC worker is
  * a warp and the tiled JACOBI5 / GEMM worker is a team (the loop is tiled and
  * the tile loop workshared).  nowait drops the implicit barrier at the loop's
- * end (§5); on one stream the next loop still starts after this one.
+ * end (§5): the next loop may run beside this one; it completes only after
+ * this one, so the implicit barrier after it (or any later barrier) covers
+ * both.
  * Validation is eager: upir_loop() checks every field, buffer size and index
  * range against the mapped buffers and returns EINVAL/ENOTMAPPED/EUNSUPPORTED
  * without recording anything on error. */

@@ -439,6 +439,16 @@ __device__ __forceinline__ void griddep_wait() {
     asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 
+// The start of a loop's kernel.  mode 1: the implicit barrier after the
+// previous loop, every thread waits for it.  mode 2: the previous loop was
+// nowait, so this one may run beside it; one thread still waits for it, so
+// this loop completes only after the previous one, and the implicit barrier
+// after this loop covers both (a barrier waits for all earlier work).
+// mode 0: nothing to wait for.
+__device__ __forceinline__ void griddep_wait_prior(int mode) {
+    if (mode == 1 || (mode == 2 && blockIdx.x == 0 && threadIdx.x == 0)) griddep_wait();
+}
+
 __device__ __forceinline__ void griddep_launch_dependents() {
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }

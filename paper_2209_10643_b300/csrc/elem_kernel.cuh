@@ -250,7 +250,7 @@ __global__ void __launch_bounds__(1024, 1) elem_kernel(const ElemParams p) {
     constexpr bool HR = FOP != 0 || IOP != 0;
     const int64_t W = (int64_t)gridDim.x * blockDim.x;
     const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p.wait_prior) griddep_wait();
+    griddep_wait_prior(p.wait_prior);
     griddep_launch_dependents();
     if (!DYN) {
         Terms t{facc_identity(FOP), iacc_identity(IOP), 0};

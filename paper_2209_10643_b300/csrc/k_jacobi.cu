@@ -69,7 +69,7 @@ __global__ void __launch_bounds__(1024) jacobi_tma_kernel(const JacobiParams p,
         fence_mbar_init();
     }
     // the previous sweep's output is this sweep's input: wait for it
-    if (p.wait_prior) griddep_wait();
+    griddep_wait_prior(p.wait_prior);
     if (threadIdx.x == 0) {
 #pragma unroll
         for (int s = 0; s < S; ++s) issue_next(s);
@@ -217,7 +217,7 @@ __global__ void __launch_bounds__(1024) jacobi_rows_kernel(const JacobiParams p,
         fence_mbar_init();
     }
     // the previous sweep's output is this sweep's input: wait for it
-    if (p.wait_prior) griddep_wait();
+    griddep_wait_prior(p.wait_prior);
     if (threadIdx.x == 0) {
 #pragma unroll
         for (int s = 0; s < S; ++s) take_next(s);

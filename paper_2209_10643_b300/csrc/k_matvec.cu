@@ -16,7 +16,7 @@ __global__ void __launch_bounds__(1024) matvec_kernel(const MatvecParams p) {
     const int64_t wpb = blockDim.x >> 5;
     const int64_t W = (int64_t)gridDim.x * wpb;
     const int64_t w = (int64_t)blockIdx.x * wpb + (threadIdx.x >> 5);
-    if (p.wait_prior) griddep_wait();
+    griddep_wait_prior(p.wait_prior);
     griddep_launch_dependents();
     auto rows = [&](int64_t k0, int64_t k1) {
         for (int64_t k = k0; k < k1; ++k) {

@@ -183,7 +183,7 @@ __global__ void __launch_bounds__(1024, 1) jacobi_tb_kernel(const JacobiTBParams
         mbar_init(&bar[1], 1);
         fence_mbar_init();
     }
-    if (p.wait_prior) griddep_wait();
+    griddep_wait_prior(p.wait_prior);
     if (threadIdx.x == 0) issue(0);
     __syncthreads();
     griddep_launch_dependents();
@@ -368,7 +368,7 @@ __global__ void __launch_bounds__(kFilter7Units) filter7_kernel(const Filter7Par
         for (int s = 0; s < S; ++s) mbar_init(&bar[s], 1);
         fence_mbar_init();
     }
-    if (p.wait_prior) griddep_wait();
+    griddep_wait_prior(p.wait_prior);
     if (threadIdx.x == 0) {
 #pragma unroll
         for (int s = 0; s < S; ++s) issue(s);

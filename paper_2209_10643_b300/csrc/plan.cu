@@ -328,8 +328,9 @@ upir_status plan_loop(upir_region r, const upir_loop_desc* d, LoopRec& lp) {
     };
 
     const int U0 = r->units, T0 = r->teams;
-    // implicit barrier after the previous loop of the region unless it was nowait
-    const int wait_prior = (r->loops.empty() || !r->loops.back()->nowait) ? 1 : 0;
+    // implicit barrier after the previous loop of the region (1), or, when
+    // that loop was nowait, run beside it but complete only after it (2)
+    const int wait_prior = (r->loops.empty() || !r->loops.back()->nowait) ? 1 : 2;
     lp.units = U0 ? U0 : (auto_units ? auto_units : 256);
     lp.kind = LK_ELEM;
     ElemParams& ep = lp.ep;

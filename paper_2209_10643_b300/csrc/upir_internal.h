@@ -72,7 +72,7 @@ struct ElemParams {
     unsigned long long imod_minv;            // floor(2^64 / m) for Barrett reduction (m >= 2)
     int imod32;                              // m < 2^28: eight terms sum in 32 bits
     SchedConst sk;
-    int wait_prior;                          // wait for the previous kernel (implicit barrier)
+    int wait_prior;                          // 1: implicit barrier; 2: previous loop nowait (griddep_wait_prior)
     int fuse_fin;                            // the last team finishes the reductions (few partials)
     RedVars rv;
     Scratch sc;

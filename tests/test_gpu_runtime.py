@@ -294,3 +294,58 @@ def test_allocator_failure_is_reported_without_leaks():
     assert len(live) == 3
     U.lib.upir_finalize(ctx)  # frees the rest
     assert len(live) == 0
+
+
+def test_nowait_loops_and_the_barrier_after_them(s):
+    """§5 nowait: a loop marked nowait may run beside the next one, but the
+    implicit barrier after that next loop covers both.  Loop 1 (nowait) is a
+    long AXPY on y1, loop 2 a short independent one, loop 3 reads y1 (an
+    AXPY with x = y1): it must see loop 1's finished update.  Then eight
+    independent nowait AXPY loops with their own reductions, each checked."""
+    n1, n2 = 1 << 25, 1024
+    x1, y1 = I.axpy_inputs(n1, seed=41)
+    x2, y2 = I.axpy_inputs(n2, seed=42)
+    y3 = np.zeros(n1, np.float32)
+    y1_0, y2_0 = y1.copy(), y2.copy()
+    h = [s.map(a, U.UPIR_MAP_TOFROM) for a in (x1, y1, x2, y2, y3)]
+    loops = [axpy_loop(h[0], h[1], n1), axpy_loop(h[2], h[3], n2), axpy_loop(h[1], h[4], n1, a=1.0)]
+    loops[0]["nowait"] = 1
+    for flags in (0, U.UPIR_SUBMIT_GRAPH):
+        y1[:] = y1_0
+        y2[:] = y2_0
+        y3[:] = 0.0
+        for hh in h:
+            U.upir_data_update(s.ctx, hh, U.UPIR_MAP_TO)
+        s.run(loops, flags=flags)
+        for hh in h:
+            U.upir_data_update(s.ctx, hh, U.UPIR_MAP_FROM)
+        want1 = O.axpy(2.5, x1, y1_0)
+        assert np.array_equal(y1, want1)
+        assert np.array_equal(y2, O.axpy(2.5, x2, y2_0))
+        assert np.array_equal(y3, O.axpy(1.0, want1, np.zeros(n1, np.float32)))
+    for hh in h:
+        s.unmap(hh)
+
+    n = 300_007
+    sets = []
+    for k in range(8):
+        x, y = I.axpy_inputs(n, seed=50 + k)
+        sm = np.zeros(1, np.float32)
+        im = np.zeros(1, np.int64)
+        sets.append((x, y, y.copy(), sm, im, [s.map(x, U.UPIR_MAP_TO), s.map(y, U.UPIR_MAP_TOFROM),
+                                               s.map(sm, U.UPIR_MAP_TOFROM), s.map(im, U.UPIR_MAP_TOFROM)]))
+    loops = []
+    for k, (x, y, y0, sm, im, hs) in enumerate(sets):
+        lp = axpy_loop(hs[0], hs[1], n, reds=[(U.UPIR_RED_ADD, U.UPIR_F32, U.UPIR_TERM_Y, hs[2], 0),
+                                              (U.UPIR_RED_ADD, U.UPIR_I64, U.UPIR_TERM_IMOD, hs[3], 0)])
+        lp["nowait"] = 1 if k < 7 else 0
+        loops.append(lp)
+    s.run(loops, flags=U.UPIR_SUBMIT_GRAPH)
+    for x, y, y0, sm, im, hs in sets:
+        for hh in hs:
+            s.unmap(hh)
+        want = O.axpy(2.5, x, y0)
+        assert np.array_equal(y, want)
+        ref = O.reduce_f64(O.RED_ADD, 0.0, want)
+        assert abs(float(sm[0]) - ref) <= 1e-5 * abs(ref)
+        assert int(im[0]) == O.imod_sum_closed_form(n, 3, 1000)
