@@ -181,11 +181,17 @@ class JacobiRowBlocks:
         max residual of sweep k into ``res[k]`` (a rank without rows is not
         called and leaves -inf there).  Returns the slab holding the result."""
         src, dst = buf_a, buf_b
-        for k in range(sweeps):
-            if self.local_rows:
-                sweep(src, dst, k)
-            self.exchange(dst)
-            src, dst = dst, src
+        if self.up is None and self.down is None and self.local_rows and hasattr(sweep, "all_sweeps"):
+            # no neighbour to exchange with: every sweep in one submission
+            sweep.all_sweeps()
+            if sweeps % 2:
+                src, dst = dst, src
+        else:
+            for k in range(sweeps):
+                if self.local_rows:
+                    sweep(src, dst, k)
+                self.exchange(dst)
+                src, dst = dst, src
         self.combine_residuals(res)
         return src
 
@@ -345,7 +351,7 @@ class UpirJacobiSweeper:
         import paper_2209_10643_b300 as U
 
         self.U, self.ctx, self.graph = U, ctx, graph
-        self.handles, self.regions = [], []
+        self.handles, self.regions, self.whole = [], [], None
         if not plan.local_rows:
             return
         nb = plan.local_rows * plan.cols * 4
@@ -353,22 +359,36 @@ class UpirJacobiSweeper:
         hb = U.upir_data_map_device(ctx, tb.data_ptr(), nb)
         hr = U.upir_data_map_device(ctx, tres.data_ptr(), 4 * sweeps)
         self.handles = [ha, hb, hr]
+        descs = []
         for k in range(sweeps):
             src, dst = (ha, hb) if k % 2 == 0 else (hb, ha)
-            r = U.upir_spmd_region(ctx, 0, 0)
-            U.upir_loop_checked(ctx, r, U.make_loop_desc(
+            descs.append(U.make_loop_desc(
                 lb=1, ub=plan.local_rows - 1, collapse=2, body=U.UPIR_BODY_JACOBI5, bufs=[src, dst],
                 scalars=[plan.local_rows, plan.cols],
                 reductions=[(U.UPIR_RED_MAX, U.UPIR_F32, U.UPIR_TERM_RESID, hr, k)]))
+        for d in descs:
+            r = U.upir_spmd_region(ctx, 0, 0)
+            U.upir_loop_checked(ctx, r, d)
             self.regions.append(r)
+        # every sweep in one region, for a rank with no neighbour (one rank)
+        if plan.up is None and plan.down is None:
+            self.whole = U.upir_spmd_region(ctx, 0, 0)
+            for d in descs:
+                U.upir_loop_checked(ctx, self.whole, d)
 
     def __call__(self, src, dst, k: int) -> None:
         self.U.upir_region_submit(self.regions[k], self.U.UPIR_SUBMIT_GRAPH if self.graph else 0)
 
+    def all_sweeps(self) -> None:
+        if self.whole is None:
+            raise RuntimeError("all_sweeps: this rank exchanges halo rows between sweeps")
+        self.U.upir_region_submit(self.whole, self.U.UPIR_SUBMIT_GRAPH if self.graph else 0)
+
     def close(self) -> None:
         self.U.upir_ctx_wait(self.ctx)
-        for r in self.regions:
+        for r in self.regions + ([self.whole] if self.whole else []):
             self.U.upir_region_destroy(r)
+        self.whole = None
         for h in self.handles:
             self.U.upir_data_unmap(self.ctx, h)
         self.regions, self.handles = [], []

@@ -104,3 +104,25 @@ def test_rank_partials_folded_by_the_runtime(ctx, world):
     got = float(fold(torch.tensor(parts, dtype=torch.float32, device="cuda"), -3.25).item())
     want = O.reduce_f64(O.RED_ADD, -3.25, want_y)
     assert abs(got - want) <= 1e-5 * abs(want)
+
+
+@pytest.mark.parametrize("sweeps", [5, 6])
+def test_single_rank_run_submits_every_sweep_at_once(ctx, sweeps):
+    """A rank with no neighbour runs its sweeps as one submission
+    (``JacobiRowBlocks.run`` through the sweeper's whole region); field and
+    residuals bit-exact against the oracle, for odd and even sweep counts."""
+    u0 = I.jacobi_grid(260, 392, seed=13)
+    plan = JacobiRowBlocks(260, 392, 1, 0)
+    a = torch.from_numpy(plan.slab(u0).copy()).cuda()
+    b = a.clone()
+    res = torch.full((sweeps,), -np.inf, dtype=torch.float32, device="cuda")
+    torch.cuda.current_stream().synchronize()
+    sw = UpirJacobiSweeper(ctx, plan, a, b, res, sweeps)
+    try:
+        final = plan.run(sw, a, b, sweeps, res)
+        U.upir_ctx_wait(ctx)
+    finally:
+        sw.close()
+    um, rm = O.jacobi_run(u0, sweeps, mirror_f32=True)
+    assert np.array_equal(final.cpu().numpy().view(np.uint32), um.view(np.uint32))
+    assert np.array_equal(res.cpu().numpy().view(np.uint32), rm.view(np.uint32))
