@@ -283,7 +283,7 @@ def headline(rt: Runtime, steps: int, warmup: int, pk: dict, device: int):
         U.upir_data_unmap(rt.ctx, h)
 
     # end to end through the public API with host buffers (pinned)
-    e2e = jacobi_e2e(rt, u0, max(3, min(steps, 16)))
+    e2e = jacobi_e2e(rt, u0, max(3, min(steps, 32)))
     return {
         "value": value, "ms_per_step": statistics.mean(step_ms), "clocks": clk.summary(),
         "gpu_launches": steps * SWEEPS,
