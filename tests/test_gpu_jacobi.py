@@ -62,6 +62,10 @@ def test_hand_worked_5x5():
     (131, 260, 5, ()),                                  # several tiles, ragged in both directions
     (37, 61, 4, ()),                                    # cols % 4 != 0: one copy per halo row
     (131, 259, 5, ()), (70, 1022, 3, ()), (45, 129, 4, ((U.UPIR_HINT_TILE_M, 5), (U.UPIR_HINT_TILE_N, 12))),
+    # row copies ending 3 and 2 elements short of a 16-byte boundary at the
+    # grid's end (the last elements come by plain loads), three and four stages
+    (33, 67, 4, ((U.UPIR_HINT_TILE_M, 8), (U.UPIR_HINT_TILE_N, 32), (U.UPIR_HINT_STAGES, 3))),
+    (34, 67, 3, ((U.UPIR_HINT_TILE_M, 3), (U.UPIR_HINT_TILE_N, 64), (U.UPIR_HINT_STAGES, 4))),
     (33, 61, 3, ((U.UPIR_HINT_VARIANT, 1),)),           # per-point variant forced on an unaligned width
     (200, 516, 3, ((U.UPIR_HINT_TILE_M, 7), (U.UPIR_HINT_TILE_N, 20))),
     (300, 300, 3, ((U.UPIR_HINT_VARIANT, 1),)),         # per-point variant forced
