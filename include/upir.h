@@ -310,10 +310,12 @@ typedef struct {
  * fits), 0 = the planner's choice (pairs when every resident cluster gets a
  * tile); GEMM_F32 1 = the kernel that stages loads through registers (the
  * default, TMA-fed kernel needs K and N multiples of 4 and 16-byte aligned
- * buffers, and gives the same result bit for bit); FILTER7 1 = each thread
- * computes strips of 8 output rows instead of 4 (TILE_M then a multiple of
- * 8; the same result bit for bit).  UPIR_HINT_STAGES also sets FILTER7's
- * TMA ring depth (2, the default, or 3). */
+ * buffers, and gives the same result bit for bit); FILTER7: each thread
+ * computes strips of 4 output rows (0, 2) or 8 (1, 3; TILE_M then a multiple
+ * of 8), two rows of a strip sharing one paired FMA (fma.rn.f32x2, each half
+ * rounded once; 0, 1) or one FMA per output (2, 3), all four with the same
+ * result bit for bit.  UPIR_HINT_STAGES also sets FILTER7's TMA ring depth
+ * (2, the default, or 3). */
 typedef enum {
     UPIR_HINT_VARIANT   = 1, /* kernel variant of the body (body-specific, 0 = default)       */
     UPIR_HINT_TILE_M    = 2, /* tile rows (JACOBI5 tiled variant, GEMM)                       */

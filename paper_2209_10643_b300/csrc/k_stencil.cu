@@ -332,8 +332,26 @@ __host__ __device__ inline size_t f7_stage_floats(int tm, int tn) {
 // shape at compile time (0: taken from the parameters) so that shared-memory
 // offsets fold into the loads; tiles whose outputs are all inside the loop's
 // rows and the interior columns store without per-point tests.
-template <int S, int TMC, int TNC, int RS>
-__global__ void __launch_bounds__(kFilter7Units) filter7_kernel(const Filter7Params p,
+// acc (low half: output row 2p of a pair, high half: row 2p + 1) plus the
+// weight pair w2 times x in both halves, one rounding per half (the paired
+// form of fmaf; subnormals kept)
+__device__ __forceinline__ void fma2_bcast(float& lo, float& hi, unsigned long long w2, float x) {
+    asm("{\n\t.reg .b64 xx, acc;\n\t"
+        "mov.b64 xx, {%2, %2};\n\t"
+        "mov.b64 acc, {%0, %1};\n\t"
+        "fma.rn.f32x2 acc, %3, xx, acc;\n\t"
+        "mov.b64 {%0, %1}, acc;\n\t}"
+        : "+f"(lo), "+f"(hi)
+        : "f"(x), "l"(w2));
+}
+
+// teams per SM each form is built for: four with 4-row strips (64
+// registers), three with scalar 8-row strips, two with paired 8-row strips
+template <int RS, bool PAIR>
+constexpr int f7_min_teams() { return RS == 4 ? 4 : (PAIR ? 2 : 3); }
+
+template <int S, int TMC, int TNC, int RS, bool PAIR>
+__global__ void __launch_bounds__(kFilter7Units, f7_min_teams<RS, PAIR>()) filter7_kernel(const Filter7Params p,
                                                                 const __grid_constant__ CUtensorMap tmap) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bar[S];
@@ -409,16 +427,37 @@ __global__ void __launch_bounds__(kFilter7Units) filter7_kernel(const Filter7Par
                 x[0] = a.x, x[1] = a.y, x[2] = a.z, x[3] = a.w;
                 x[4] = b.x, x[5] = b.y, x[6] = b.z, x[7] = b.w;
                 x[8] = c.x, x[9] = c.y, x[10] = c.z, x[11] = c.w;
-                // input row rho is filter row i = rho - q of output row q
+                if (!PAIR) {
+                    // input row rho is filter row i = rho - q of output row q
 #pragma unroll
-                for (int q = 0; q < RS; ++q) {
-                    const int i = rho - q;
-                    if (i < 0 || i > 6) continue;
+                    for (int q = 0; q < RS; ++q) {
+                        const int i = rho - q;
+                        if (i < 0 || i > 6) continue;
 #pragma unroll
-                    for (int jj = 0; jj < 7; ++jj)
+                        for (int jj = 0; jj < 7; ++jj)
 #pragma unroll
-                        for (int j = 0; j < 4; ++j)
-                            acc[q][j] = __fmaf_rn(p.w[i * 7 + jj], x[1 + j + jj], acc[q][j]);
+                            for (int j = 0; j < 4; ++j)
+                                acc[q][j] = __fmaf_rn(p.w[i * 7 + jj], x[1 + j + jj], acc[q][j]);
+                    }
+                } else {
+                    // output rows 2pp and 2pp + 1 take input row rho as filter
+                    // rows i = rho - 2pp and i - 1: one paired FMA for both
+                    // while both are in the window, the lone row at its ends
+#pragma unroll
+                    for (int pp = 0; pp < RS / 2; ++pp) {
+                        const int i = rho - 2 * pp;
+                        if (i < 0 || i > 7) continue;
+#pragma unroll
+                        for (int jj = 0; jj < 7; ++jj)
+#pragma unroll
+                            for (int j = 0; j < 4; ++j) {
+                                float& lo = acc[2 * pp][j];
+                                float& hi = acc[2 * pp + 1][j];
+                                if (i == 0) lo = __fmaf_rn(p.w[jj], x[1 + j + jj], lo);
+                                else if (i == 7) hi = __fmaf_rn(p.w[42 + jj], x[1 + j + jj], hi);
+                                else fma2_bcast(lo, hi, p.w2[(i - 1) * 7 + jj], x[1 + j + jj]);
+                            }
+                    }
                 }
             }
             const int64_t c = (int64_t)rc.y + 4 * tx;
@@ -468,19 +507,24 @@ __global__ void __launch_bounds__(kFilter7Units) filter7_kernel(const Filter7Par
 
 using F7Kernel = void (*)(const Filter7Params, const CUtensorMap);
 
-template <int S, int RS>
+template <int S, int RS, bool PAIR>
 F7Kernel filter7_pick_shape(int tile_m, int tile_n) {
-    if (tile_m == 32 && tile_n == 128) return filter7_kernel<S, 32, 128, RS>;
-    if (tile_m == 64 && tile_n == 128) return filter7_kernel<S, 64, 128, RS>;
-    return filter7_kernel<S, 0, 0, RS>;
+    if (tile_m == 32 && tile_n == 128) return filter7_kernel<S, 32, 128, RS, PAIR>;
+    if (tile_m == 64 && tile_n == 128) return filter7_kernel<S, 64, 128, RS, PAIR>;
+    return filter7_kernel<S, 0, 0, RS, PAIR>;
+}
+
+template <int S, bool PAIR>
+F7Kernel filter7_pick_rs(int tile_m, int tile_n, int rs) {
+    return rs == 8 ? filter7_pick_shape<S, 8, PAIR>(tile_m, tile_n) : filter7_pick_shape<S, 4, PAIR>(tile_m, tile_n);
 }
 
 // 32 x 128 and 64 x 128 tiles have their own instantiations; other shapes
 // (hints) run the runtime-shape kernel.  rs: output rows per thread strip
-// (4 or 8); stages: 2 or 3.
-F7Kernel filter7_pick(int stages, int tile_m, int tile_n, int rs) {
-    if (stages >= 3) return rs == 8 ? filter7_pick_shape<3, 8>(tile_m, tile_n) : filter7_pick_shape<3, 4>(tile_m, tile_n);
-    return rs == 8 ? filter7_pick_shape<2, 8>(tile_m, tile_n) : filter7_pick_shape<2, 4>(tile_m, tile_n);
+// (4 or 8); stages: 2 or 3; pair: paired-row FMAs.
+F7Kernel filter7_pick(int stages, int tile_m, int tile_n, int rs, int pair) {
+    if (pair) return stages >= 3 ? filter7_pick_rs<3, true>(tile_m, tile_n, rs) : filter7_pick_rs<2, true>(tile_m, tile_n, rs);
+    return stages >= 3 ? filter7_pick_rs<3, false>(tile_m, tile_n, rs) : filter7_pick_rs<2, false>(tile_m, tile_n, rs);
 }
 
 template <class K>
@@ -525,8 +569,8 @@ size_t filter7_smem_bytes(int tile_m, int tile_n, int stages) {
     return (size_t)stages * f7_stage_floats(tile_m, tile_n) * sizeof(float) + 1024;
 }
 
-int filter7_max_teams_per_sm(int tile_m, int tile_n, int stages, int rs) {
-    F7Kernel k = filter7_pick(stages, tile_m, tile_n, rs);
+int filter7_max_teams_per_sm(int tile_m, int tile_n, int stages, int rs, int pair) {
+    F7Kernel k = filter7_pick(stages, tile_m, tile_n, rs, pair);
     if (!configure_once(k, kMaxDynSmem)) return 0;
     int n = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, kFilter7Units, filter7_smem_bytes(tile_m, tile_n, stages)) !=
@@ -538,7 +582,7 @@ int filter7_max_teams_per_sm(int tile_m, int tile_n, int stages, int rs) {
 }
 
 cudaError_t launch_filter7(int teams, const Filter7Params& p, const void* tmap, cudaStream_t s) {
-    F7Kernel k = filter7_pick(p.stages, p.tile_m, p.tile_n, p.rs);
+    F7Kernel k = filter7_pick(p.stages, p.tile_m, p.tile_n, p.rs, p.pair);
     if (!configure_once(k, kMaxDynSmem)) return cudaGetLastError();
     CUtensorMap m;
     memcpy(&m, tmap, sizeof(m));

@@ -618,13 +618,18 @@ upir_status plan_loop(upir_region r, const upir_loop_desc* d, LoopRec& lp) {
             lp.tile_n = lp.tile_n ? lp.tile_n : 128;
             ok(lp.tile_n / 4 <= kFilter7Units && kFilter7Units % (lp.tile_n / 4) == 0, UPIR_EINVAL,
                "FILTER7 tile_n / 4 must divide 256");
-            // VARIANT 1: strips of 8 output rows per thread instead of 4;
-            // STAGES: TMA ring depth 2 (default) or 3 (one team barrier per tile)
-            const int f7_rs = lp.variant == 1 ? 8 : 4;
+            // Two output rows per paired FMA (fma.rn.f32x2) with strips of 4
+            // output rows per thread by default (4096^2: 36.8-37.3 us against
+            // 39.6-40.7 us with one FMA per output; a third fewer
+            // instructions, the FMA pipe then the busiest unit).  VARIANT 1:
+            // paired, 8-row strips; 2: one FMA per output, 4-row strips; 3:
+            // one FMA per output, 8-row strips.  STAGES: TMA ring depth 2
+            // (default) or 3 (one team barrier per tile)
+            const int f7_rs = (lp.variant == 1 || lp.variant == 3) ? 8 : 4;
+            const int f7_pair = lp.variant <= 1 ? 1 : 0;
             const int f7_stages = lp.stages ? lp.stages : kFilter7Stages;
-            ok(lp.variant == 0 || lp.variant == 1, UPIR_EINVAL, "FILTER7 variant must be 0 or 1");
             ok(f7_stages == 2 || f7_stages == 3, UPIR_EINVAL, "FILTER7 stages must be 2 or 3");
-            ok(lp.tile_m % f7_rs == 0, UPIR_EINVAL, "FILTER7 tile_m must be a multiple of the strip rows (4; variant 1: 8)");
+            ok(lp.tile_m % f7_rs == 0, UPIR_EINVAL, "FILTER7 tile_m must be a multiple of the strip rows (4; variants 1 and 3: 8)");
             ok(lp.tile_m + 6 <= 256 && lp.tile_n + 8 <= 256 &&
                    filter7_smem_bytes(lp.tile_m, lp.tile_n, f7_stages) <= kStencilSmemBudget,
                UPIR_EINVAL, "FILTER7 tile too large");
@@ -632,6 +637,7 @@ upir_status plan_loop(upir_region r, const upir_loop_desc* d, LoopRec& lp) {
             lp.smem = filter7_smem_bytes(lp.tile_m, lp.tile_n, f7_stages);
             fp.stages = f7_stages;
             fp.rs = f7_rs;
+            fp.pair = f7_pair;
             fp.xin = xin;
             fp.xout = xout;
             fp.rows = R;
@@ -649,13 +655,19 @@ upir_status plan_loop(upir_region r, const upir_loop_desc* d, LoopRec& lp) {
             fp.err_word = ctx->err_word;
             fp.wait_prior = wait_prior;
             for (int k = 0; k < 49; ++k) fp.w[k] = (float)lp.scalars[2 + k];
+            for (int k = 0; k < 42; ++k) {
+                uint32_t lo, hi;
+                memcpy(&lo, &fp.w[k + 7], 4);  // w[i][j], i = k / 7 + 1
+                memcpy(&hi, &fp.w[k], 4);      // w[i - 1][j]
+                fp.w2[k] = (unsigned long long)hi << 32 | lo;
+            }
             if (lp.trip) {
                 upir_status st = encode_tmap_2d(ctx, &lp.tmap[0], xin, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4,
                                                 (uint64_t)C, (uint64_t)R, (uint32_t)(lp.tile_n + 8),
                                                 (uint32_t)(lp.tile_m + 6), 0);
                 if (st != UPIR_OK) return st;
             }
-            const int per_sm = std::max(1, filter7_max_teams_per_sm(lp.tile_m, lp.tile_n, f7_stages, f7_rs));
+            const int per_sm = std::max(1, filter7_max_teams_per_sm(lp.tile_m, lp.tile_n, f7_stages, f7_rs, f7_pair));
             const int64_t slots = (int64_t)kNumSMs * per_sm;
             if (T0) lp.teams = T0;
             else if (lp.sched == UPIR_SCHED_STATIC && lp.chunk == 0) {

@@ -128,6 +128,7 @@ struct Filter7Params {
     int tile_m, tile_n;
     int stages;  // TMA ring depth (2 or 3)
     int rs;      // output rows per thread strip (4 or 8)
+    int pair;    // 1: two output rows per paired FMA (fma.rn.f32x2)
     int64_t tiles_r, tiles_c, ntiles;
     int64_t chunk;
     int sched;
@@ -137,6 +138,9 @@ struct Filter7Params {
     int wait_prior;
     Scratch sc;
     float w[49];  // weights, row-major over the window
+    // weight pairs of the paired-row form: element (i - 1) * 7 + j holds
+    // w[i][j] in its low half and w[i - 1][j] in its high half, i = 1..6
+    unsigned long long w2[42];
 };
 
 struct MatvecParams {
@@ -244,7 +248,7 @@ size_t jacobi_tb_plane_floats(int tile_m, int tile_n, int sweeps, int halo_c);
 size_t jacobi_tb_smem_bytes(int tile_m, int tile_n, int sweeps, int halo_c);
 cudaError_t launch_jacobi_tb(int teams, int units, const JacobiTBParams& p, const void* tmap, cudaStream_t s);
 size_t filter7_smem_bytes(int tile_m, int tile_n, int stages);
-int filter7_max_teams_per_sm(int tile_m, int tile_n, int stages, int rs);
+int filter7_max_teams_per_sm(int tile_m, int tile_n, int stages, int rs, int pair);
 cudaError_t launch_filter7(int teams, const Filter7Params& p, const void* tmap, cudaStream_t s);
 int jacobi_tma_max_teams_per_sm(int units, int tile_m, int tile_n, int stages, bool rows);
 cudaError_t launch_matvec(int teams, int units, const MatvecParams& p, cudaStream_t s);

@@ -219,9 +219,13 @@ def test_filter7_ranges_schedules_tiles(s, lb, ub, sched, chunk, teams, hints):
 
 F7_VARIANTS = [
     # (tile_m, tile_n, stages, variant): fixed-shape kernels, 3-stage ring,
-    # 8-row strips (variant 1), runtime-shape kernel
+    # runtime-shape kernel; two output rows per paired FMA with 4- and 8-row
+    # strips (variants 0 and 1), one FMA per output with 4- and 8-row strips
+    # (variants 2 and 3)
     (32, 128, 2, 0), (64, 128, 2, 0), (32, 128, 3, 0), (32, 128, 2, 1), (64, 128, 3, 1),
-    (16, 64, 2, 0), (40, 64, 3, 0), (24, 32, 2, 1)]
+    (16, 64, 2, 0), (40, 64, 3, 0), (24, 32, 2, 1),
+    (32, 128, 2, 2), (32, 128, 3, 2), (64, 128, 2, 2), (32, 128, 2, 3), (16, 64, 2, 2), (40, 64, 3, 2),
+    (24, 32, 2, 3), (64, 128, 3, 3)]
 
 
 @pytest.mark.parametrize("tm,tn,stages,variant", F7_VARIANTS)
