@@ -324,14 +324,17 @@ __host__ __device__ inline size_t f7_stage_floats(int tm, int tn) {
     return ((size_t)(tm + 6) * (tn + 8) + 255) / 256 * 256;
 }
 
-// S-stage TMA ring of (TM + 6) x (TN + 8) input boxes; each thread computes
-// strips of RS output rows x 4 columns.  With three or more stages a tile
-// costs one team barrier: past the barrier that opens stage s every thread
-// has left the stage computed before it, whose refill then goes out (its
-// stage_rc entry is next read two barriers later).  TMC / TNC fix the tile
-// shape at compile time (0: taken from the parameters) so that shared-memory
-// offsets fold into the loads; tiles whose outputs are all inside the loop's
-// rows and the interior columns store without per-point tests.
+// S-stage TMA ring (S >= 2) of (TM + 6) x (TN + 8) input boxes; each thread
+// computes strips of RS output rows x 4 columns.  A tile costs one team
+// barrier: past the barrier that opens stage s every thread has left the
+// stage computed before it, whose refill then goes out.  The end of the
+// team's tiles also completes its stage's barrier (an arrival without bytes),
+// so every thread reads a stage's tile record only after that barrier, and
+// the record's next write (the stage's refill) comes a barrier later.
+// TMC / TNC fix the tile shape at compile time (0: taken from the
+// parameters) so that shared-memory offsets fold into the loads; tiles whose
+// outputs are all inside the loop's rows and the interior columns store
+// without per-point tests.
 // acc (low half: output row 2p of a pair, high half: row 2p + 1) plus the
 // weight pair w2 times x in both halves, one rounding per half (the paired
 // form of fmaf; subnormals kept)
@@ -366,11 +369,13 @@ __global__ void __launch_bounds__(kFilter7Units, f7_min_teams<RS, PAIR>()) filte
     const uint32_t box_bytes = (uint32_t)((TM + 6) * BW * sizeof(float));
     const int64_t cols = p.cols, r_ub = p.r_ub;
 
+    static_assert(S >= 2, "the ring refills a stage while the team computes another");
     TileIter it = tile_iter_begin(p);
     auto issue = [&](int s) {
         const int64_t t = tile_iter_next(it, p);
         if (t < 0) {
             stage_rc[s] = make_int2(-1, -1);
+            mbar_arrive(&bar[s]);  // completes the phase: the team sees the end
             return;
         }
         const int tr = (int)(t / p.tiles_c), tc = (int)(t - (int64_t)tr * p.tiles_c);
@@ -398,13 +403,13 @@ __global__ void __launch_bounds__(kFilter7Units, f7_min_teams<RS, PAIR>()) filte
     int s = 0, prev = -1;
     uint32_t parity = 0;
     for (;;) {
-        const int2 rc = stage_rc[s];
-        if (rc.x < 0) break;
         if (!__syncthreads_and(mbar_wait_bounded(&bar[s], parity, p.spin_limit, p.err_word))) {
             failed = true;
             break;
         }
-        if (S >= 3 && threadIdx.x == 0 && prev >= 0) issue(prev);
+        const int2 rc = stage_rc[s];
+        if (rc.x < 0) break;
+        if (threadIdx.x == 0 && prev >= 0) issue(prev);
         // every output of the tile inside the loop's rows and the interior columns
         const bool full_tile = rc.x + TM <= r_ub && rc.y >= 3 && rc.y + TN <= cols - 3;
         // strips of RS output rows, first row q0 within the tile
@@ -483,11 +488,6 @@ __global__ void __launch_bounds__(kFilter7Units, f7_min_teams<RS, PAIR>()) filte
                     }
                 }
             }
-        }
-        if (S < 3) {
-            __syncthreads();  // every thread is done with stage s
-            if (threadIdx.x == 0) issue(s);
-            __syncthreads();  // stage_rc[s] is read again (at once when S == 1)
         }
         prev = s;
         if (++s == S) {
