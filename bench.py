@@ -596,12 +596,18 @@ def extra_jacobi_grid(rt: Runtime, pk: dict, n: int = 4095, sweeps: int = 20) ->
             "algorithmic_GB/s": gbs, "frac_hbm": gbs / pk["hbm_gbs"]}
 
 
+def rng_weights7() -> np.ndarray:
+    """The size-7 filter's weights in the bench: seeded uniform [0, 1),
+    normalised to sum 1."""
+    w = np.random.default_rng(15).random((7, 7)).astype(np.float32)
+    return (w / w.sum()).astype(np.float32)
+
+
 def extra_filter7(rt: Runtime, pk: dict) -> dict:
     """The size-7 filter (7 x 7 window, FMA chain) over a 4096^2 grid."""
     U = rt.U
     x = I.jacobi_grid(N_GRID, seed=14)
-    w = np.random.default_rng(15).random((7, 7)).astype(np.float32)
-    w = (w / w.sum()).astype(np.float32)
+    w = rng_weights7()
     out = np.zeros_like(x)
     hx, ho = rt.map(x, U.UPIR_MAP_TO), rt.map(out, U.UPIR_MAP_TOFROM)
     r = rt.region([dict(lb=3, ub=N_GRID - 3, step=1, collapse=2, body=U.UPIR_BODY_FILTER7, bufs=[hx, ho],
@@ -967,6 +973,83 @@ def with_cpu(fn, cpu_fn, cpu: bool):
     return run
 
 
+# Execution times the paper reports for the UPIR compiler's offloaded kernels
+# (§6, the AXPY, matrix multiplication, matrix-vector multiplication and
+# size-7 stencil figures: one V100, mean of 10 runs, the timed span not
+# stated); context beside this machine's times, not targets.
+PAPER_V100_MS = {
+    "axpy": {10240: 13.85, 102400: 14.61, 1024000: 21.54, 10240000: 74.75, 102400000: 702.39},
+    "matmul": {64: 13.91, 128: 17.49, 256: 27.6, 512: 135.03, 1024: 976.88},
+    "matvec": {1024: 17.88, 2048: 20.7, 4096: 44.2, 8192: 145.74, 16384: 583.45},
+    "stencil": {64: 13.69, 128: 15.14, 256: 15.7, 512: 20.32, 1024: 28.72, 2048: 56.47},
+}
+
+
+def extra_paper_workloads(rt: Runtime, runs: int = 10, warmup: int = 2) -> dict:
+    """The paper's four evaluation kernels at its problem sizes, each run end
+    to end through the C ABI from ordinary (pageable) host arrays: map the
+    inputs to the device and the output back, record the one-loop region,
+    submit it, unmap (the output comes back) and wait; host wall clock around
+    all of it, the mean of ``runs`` runs after ``warmup``, as the paper times
+    its kernels (10 runs)."""
+    U = rt.U
+    ctx = rt.ctx
+    TO, FROM, TOFROM = U.UPIR_MAP_TO, U.UPIR_MAP_FROM, U.UPIR_MAP_TOFROM
+    w7 = rng_weights7()
+
+    def one(arrays, loop_of):
+        hs = [U.upir_data_map(ctx, a.ctypes.data, a.nbytes, kind) for a, kind in arrays]
+        r = rt.region([loop_of(hs)])
+        U.upir_region_submit(r, 0)
+        U.upir_region_destroy(r)
+        for h in hs:
+            U.upir_data_unmap(ctx, h)
+        U.upir_ctx_wait(ctx)
+
+    def timed(arrays, loop_of):
+        for _ in range(warmup):
+            one(arrays, loop_of)
+        t = []
+        for _ in range(runs):
+            t0 = time.perf_counter()
+            one(arrays, loop_of)
+            t.append((time.perf_counter() - t0) * 1e3)
+        return round(statistics.fmean(t), 4)
+
+    out = {"protocol": f"host wall clock around map, region, submit, unmap and wait; mean of {runs} runs "
+                       f"after {warmup}; pageable numpy host arrays",
+           "paper_v100_ms": {k: {str(n): v for n, v in d.items()} for k, d in PAPER_V100_MS.items()}}
+    res = {}
+    for n in PAPER_V100_MS["axpy"]:
+        x, y = I.axpy_inputs(n, seed=0)
+        res.setdefault("axpy", {})[str(n)] = timed(
+            [(x, TO), (y, TOFROM)],
+            lambda hs, n=n: dict(lb=0, ub=n, body=U.UPIR_BODY_AXPY, bufs=hs, scalars=[2.0, 3, 1000]))
+    for n in PAPER_V100_MS["matmul"]:
+        a, b = I.gemm_inputs(n, n, n)
+        c = np.zeros((n, n), np.float32)
+        res.setdefault("matmul", {})[str(n)] = timed(
+            [(a, TO), (b, TO), (c, FROM)],
+            lambda hs, n=n: dict(lb=0, ub=n, collapse=2, body=U.UPIR_BODY_GEMM_F32, bufs=hs, scalars=[n, n, n]))
+    for n in PAPER_V100_MS["matvec"]:
+        a, xv = I.matvec_inputs(n, n)
+        yv = np.zeros(n, np.float32)
+        res.setdefault("matvec", {})[str(n)] = timed(
+            [(a, TO), (xv, TO), (yv, FROM)],
+            lambda hs, n=n: dict(lb=0, ub=n, body=U.UPIR_BODY_MATVEC, bufs=hs, scalars=[n, n]))
+    for n in PAPER_V100_MS["stencil"]:
+        xg = I.jacobi_grid(n, seed=14)
+        og = np.zeros_like(xg)
+        res.setdefault("stencil", {})[str(n)] = timed(
+            [(xg, TO), (og, TOFROM)],
+            lambda hs, n=n: dict(lb=3, ub=n - 3, step=1, collapse=2, body=U.UPIR_BODY_FILTER7, bufs=hs,
+                                 scalars=[n, n] + [float(v) for v in w7.ravel()]))
+    out["ms"] = res
+    out["paper_over_this"] = {k: {m: round(PAPER_V100_MS[k][int(m)] / v, 1) for m, v in d.items()}
+                              for k, d in res.items()}
+    return out
+
+
 def extra_workloads(rt: Runtime, pk: dict, cpu: bool = True) -> dict:
     return {"axpy_2^20": with_cpu(lambda: extra_axpy(rt, 1 << 20, pk), cpu_baseline_axpy, cpu),
             "axpy_2^26": lambda: extra_axpy(rt, 1 << 26, pk),
@@ -981,7 +1064,8 @@ def extra_workloads(rt: Runtime, pk: dict, cpu: bool = True) -> dict:
             "gemm_f32_4096": with_cpu(lambda: extra_gemm_f32(rt), cpu_baseline_gemm, cpu),
             "gemm_tc_4096": lambda: extra_gemm_tc(rt, pk),
             "batch_512_regions": lambda: extra_batch(rt, check=cpu),
-            "cost_model": lambda: extra_costmodel(rt)}
+            "cost_model": lambda: extra_costmodel(rt),
+            "paper_workloads": lambda: extra_paper_workloads(rt)}
 
 
 def run_ours(args) -> None:
