@@ -624,7 +624,7 @@ upir_status plan_loop(upir_region r, const upir_loop_desc* d, LoopRec& lp) {
             // instructions, the FMA pipe then the busiest unit).  VARIANT 1:
             // paired, 8-row strips; 2: one FMA per output, 4-row strips; 3:
             // one FMA per output, 8-row strips.  STAGES: TMA ring depth 2
-            // (default) or 3 (one team barrier per tile)
+            // (default) or 3; either takes one team barrier per tile
             const int f7_rs = (lp.variant == 1 || lp.variant == 3) ? 8 : 4;
             const int f7_pair = lp.variant <= 1 ? 1 : 0;
             const int f7_stages = lp.stages ? lp.stages : kFilter7Stages;
