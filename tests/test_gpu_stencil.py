@@ -209,7 +209,11 @@ def test_filter7_single_taps_and_signed_weights(s):
 
 @pytest.mark.parametrize("lb,ub,sched,chunk,teams,hints", [
     (3, 4, 0, 0, 0, ()), (10, 77, 0, 0, 0, ()), (3, 197, 0, 2, 3, ()), (5, 190, 1, 1, 0, ()),
-    (3, 197, 1, 3, 6, ()), (3, 197, 0, 0, 0, ((U.UPIR_HINT_TILE_M, 8), (U.UPIR_HINT_TILE_N, 32)))])
+    (3, 197, 1, 3, 6, ()), (3, 197, 0, 0, 0, ((U.UPIR_HINT_TILE_M, 8), (U.UPIR_HINT_TILE_N, 32))),
+    # one team walking every tile, and two teams on one-tile chunks with a
+    # three-stage ring (long runs of refills of each stage)
+    (3, 197, 0, 0, 1, ((U.UPIR_HINT_TILE_M, 8), (U.UPIR_HINT_TILE_N, 32))),
+    (3, 197, 0, 1, 2, ((U.UPIR_HINT_TILE_M, 8), (U.UPIR_HINT_TILE_N, 32), (U.UPIR_HINT_STAGES, 3)))])
 def test_filter7_ranges_schedules_tiles(s, lb, ub, sched, chunk, teams, hints):
     x = I.jacobi_grid(200, seed=12)[:, :196].copy()
     w = filter_weights(13)
