@@ -19,8 +19,8 @@
  * Memory ownership.  The caller owns every host buffer it maps; a host buffer
  * must stay valid until the matching upir_data_unmap() returns.  Device memory
  * of mapped buffers and of the runtime's workspace belongs to the library and is
- * obtained through the allocator given to upir_init() (cudaMallocAsync /
- * cudaFreeAsync on the context stream when none is given).  Device memory handed
+ * obtained through the allocator given to upir_init() (cudaMalloc / cudaFree
+ * when none is given).  Device memory handed
  * in with upir_data_map_device() stays owned by the caller.
  *
  * Work is enqueued on the context's CUDA stream and runs in submission order.
@@ -72,7 +72,7 @@ typedef struct {
 
 /* Create a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t to
  * enqueue on (NULL: the context creates and owns its own non-blocking stream).
- * `allocator` may be NULL (cudaMallocAsync/cudaFreeAsync).  The context owns a
+ * `allocator` may be NULL (cudaMalloc/cudaFree).  The context owns a
  * small device workspace (reduction partials, counters, the device error word).
  * Errors: EINVAL (out == NULL, bad device), ECUDA, ENOMEM. */
 upir_status upir_init(upir_ctx* out, int32_t device, void* cuda_stream,
