@@ -406,7 +406,8 @@ upir_status upir_batch_destroy(upir_batch batch);
 
 /* Autotune the tile shapes of a PERSISTENT batch: every candidate (AXPY
  * iterations per tile 4096..32768, Jacobi rows per tile 8..32, matvec rows
- * per tile 8..32) is run `reps` times after one warm-up and timed with CUDA
+ * per tile 8..32 for rows wider than 64 columns, narrower rows going 256 to a
+ * tile whatever the choice) is run `reps` times after one warm-up and timed with CUDA
  * events; the shapes with the least median time are kept.  The batch really
  * runs each time, so loops that update in place (AXPY) see every run.
  * tiles_out (may be NULL) receives the chosen {axpy_tile, jacobi_rows,
