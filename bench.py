@@ -43,6 +43,9 @@ import upir_inputs as I  # noqa: E402
 N_GRID = 4096
 SWEEPS = 100
 JACOBI_BYTES_PER_SWEEP = 8 * (N_GRID - 2) ** 2
+# the headline metric and the workload it is measured on (both arms)
+METRIC = "Parallel-loop HBM GB/s vs peak; batched regions/s fused vs per-region launch"
+WORKLOAD = f"jacobi5_{N_GRID}x{N_GRID}_{SWEEPS}sweeps_maxresidual"
 # DRAM bytes (read + write) of one launch of the sweep kernel on this grid, from
 # an ncu capture of the current kernel and launch (cold launch, 3-stage ring,
 # 64 x 128 tiles, one team barrier per tile, 512-unit teams)
@@ -1093,11 +1096,11 @@ def run_ours(args) -> None:
     cpu = cpu_baseline_jacobi() if (rank == 0 and world == 1 and not args.no_cpu) else None
     if rank == 0:
         line = {
-            "metric": "Parallel-loop HBM GB/s vs peak; batched regions/s fused vs per-region launch",
+            "metric": METRIC,
             "value": round(h["value"], 2), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(h["ms_per_step"], 4), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "jacobi5_4096x4096_100sweeps_maxresidual",
+            "config": {"workload": WORKLOAD,
                        "grid": [N_GRID, N_GRID], "sweeps": SWEEPS, "schedule": "static",
                        "parallelism": f"independent problem per rank x{world}",
                        "l2": "flushed before each step (256 MiB write, then 256 MiB read); working set 134 MB > 126 MB L2",
@@ -1168,11 +1171,11 @@ def run_sharded(args) -> None:
     if rank == 0:
         value = total / secs / 1e9
         line = {
-            "metric": "Parallel-loop HBM GB/s vs peak; batched regions/s fused vs per-region launch",
+            "metric": METRIC,
             "value": round(value, 2), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True,
             "scaling": "strong", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "jacobi5_4096x4096_100sweeps_maxresidual", "grid": [N_GRID, N_GRID],
+            "config": {"workload": WORKLOAD, "grid": [N_GRID, N_GRID],
                        "sweeps": SWEEPS, "parallelism": f"row blocks x{world}, one halo row per neighbour "
                                                           "per sweep, allreduce(max) of the residuals",
                        "l2": "flushed before each step (256 MiB write, then 256 MiB read)",
@@ -1205,11 +1208,11 @@ def run_reference(args) -> None:
         ts.append(time.perf_counter() - t0)
     dt = sum(ts)
     value = args.steps * per * JACOBI_BYTES_PER_SWEEP / dt / 1e9
-    line = {"impl": "reference", "metric": "Parallel-loop HBM GB/s vs peak; batched regions/s fused vs per-region launch",
+    line = {"impl": "reference", "metric": METRIC,
             "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "jacobi5_4096x4096_100sweeps_maxresidual", "grid": [N_GRID, N_GRID],
+            "config": {"workload": WORKLOAD, "grid": [N_GRID, N_GRID],
                        "sweeps_per_step": per, "parallelism": "host oracle, rank 0 only"},
             "cpu_baseline": {"value": value, "unit": "GB/s", "cores": 1, "kind": "oracle",
                              "sample": f"{per} FP64 sweeps of the {N_GRID}x{N_GRID} grid per step"},
