@@ -34,7 +34,7 @@ def test_reference_line_has_the_contract_keys():
         assert k in line, k
     assert line["impl"] == "reference"
     assert line["metric"] == bench.METRIC and line["unit"] == "GB/s" and line["higher_is_better"] is True
-    assert line["config"]["workload"] == bench.WORKLOAD
+    assert line["config"] == bench.headline_config(1)  # the same config as the GPU arm prints
     assert line["steps"] == 1 and line["n_gpus"] == 1 and line["value"] > 0 and line["vs_baseline"] is None
     cb = line["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == line["value"] and cb["sample"]
