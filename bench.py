@@ -57,9 +57,12 @@ def headline_config(world: int) -> dict:
 
 
 # DRAM bytes (read + write) of one launch of the sweep kernel on this grid, from
-# an ncu capture of the current kernel and launch (cold launch, 3-stage ring,
-# 64 x 128 tiles, one team barrier per tile, 512-unit teams)
-JACOBI_TRAFFIC_BYTES = 70_514_688 + 11_719_168
+# an ncu capture of the current kernel in the middle of the 100-sweep graph
+# (caches not flushed between launches, so each sweep finds what the previous
+# one left in L2): mean of three consecutive launches, 28.3 MB read and
+# 62.8 MB written (the sweep's output reaches DRAM once; most of its input
+# does not come from there)
+JACOBI_TRAFFIC_BYTES = 28_279_467 + 62_779_221
 L2_FLUSH_BYTES = 256 << 20
 L2_BYTES = 126 << 20  # the GPU's L2
 
@@ -305,9 +308,11 @@ def headline(rt: Runtime, steps: int, warmup: int, pk: dict, device: int):
                      "peak_source": pk["source"] + " (burst copy)",
                      "algorithmic_bytes_per_launch": JACOBI_BYTES_PER_SWEEP,
                      "avg_launch_us": avg_kernel_s * 1e6, "traffic": JACOBI_TRAFFIC_BYTES,
-                     # the same launch counted in DRAM bytes (part of the 134 MB
-                     # ping-pong pair stays in the 126 MB L2 between sweeps)
-                     "traffic_frac": JACOBI_TRAFFIC_BYTES / avg_kernel_s / 1e9 / pk["hbm_gbs"]},
+                     # the same launch counted in DRAM bytes (a sweep reads most
+                     # of its input from the 126 MB L2, where the previous sweep,
+                     # walking its tiles the other way, left it)
+                     "traffic_frac": (JACOBI_TRAFFIC_BYTES / avg_kernel_s / 1e9 / pk["hbm_gbs"]
+                                      if JACOBI_TRAFFIC_BYTES else None)},
         "per_launch": {"ms_per_step": lms, "avg_launch_us_with_events": per_launch_us,
                        "value": SWEEPS * JACOBI_BYTES_PER_SWEEP / (lms / 1e3) / 1e9},
         "e2e": e2e, "residual_last": float(res[-1]),
@@ -636,9 +641,11 @@ def extra_filter7(rt: Runtime, pk: dict) -> dict:
     tf = 2 * 49 * pts / (ms / 1e3) / 1e12
     props = rt.torch.cuda.get_device_properties(0)
     fp32_peak = props.multi_processor_count * 128 * 2 * 2.032e9 / 1e12
+    ref = cublas_sgemm_rate(rt)
     return {"grid": [N_GRID, N_GRID], "teams": tm, "units": tn, "us": ms * 1e3, "GB/s": gbs,
             "frac_hbm": gbs / pk["hbm_gbs"], "TFLOP/s": tf, "fp32_fma_peak_tflops": fp32_peak,
-            "frac_fp32_peak": tf / fp32_peak}
+            "frac_fp32_peak": tf / fp32_peak, "cublas_sgemm_TFLOP/s": ref["TFLOP/s"],
+            "frac_of_cublas_sgemm": tf / ref["TFLOP/s"]}
 
 
 def extra_pipeline(rt: Runtime, count: int = 6) -> dict:
@@ -735,8 +742,37 @@ def extra_gemm_f32(rt: Runtime) -> dict:
     props = torch.cuda.get_device_properties(0)
     fp32_peak = props.multi_processor_count * 128 * 2 * 2.032e9 / 1e12
     tf = 2 * m * n * k / (ms / 1e3) / 1e12
+    ref = cublas_sgemm_rate(rt)
     return {"shape": [m, n, k], "ms": ms, "TFLOP/s": tf, "fp32_simt_peak_tflops": fp32_peak,
-            "frac_fp32_peak": tf / fp32_peak}
+            "frac_fp32_peak": tf / fp32_peak, "cublas_sgemm": ref,
+            "frac_of_cublas_sgemm": tf / ref["TFLOP/s"]}
+
+
+_SGEMM_RATE = {}
+
+
+def cublas_sgemm_rate(rt: Runtime) -> dict:
+    """A measured FP32 FMA rate to set the FP32-bound kernels against: the
+    library SGEMM (cuBLAS through torch.matmul, FP32 compute with TF32 off)
+    on 4096^3, timed like the kernels (L2 flushed, one event pair per call,
+    mean of 10).  Computed once per process."""
+    if _SGEMM_RATE:
+        return _SGEMM_RATE
+    torch = rt.torch
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    try:
+        g = torch.Generator(device="cuda").manual_seed(3)
+        a = torch.randn(4096, 4096, device="cuda", generator=g)
+        b = torch.randn(4096, 4096, device="cuda", generator=g)
+        c = torch.empty(4096, 4096, device="cuda")
+        ms, _ = timed_whole(rt, lambda: torch.matmul(a, b, out=c), 10)
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
+    _SGEMM_RATE.update({"ms": ms, "TFLOP/s": 2 * 4096 ** 3 / (ms / 1e3) / 1e12,
+                        "what": "cuBLAS SGEMM via torch.matmul, FP32 compute, TF32 off, 4096^3, "
+                                "L2 flushed, one event pair per call, mean of 10"})
+    return _SGEMM_RATE
 
 
 def extra_gemm_tc(rt: Runtime, pk: dict) -> dict:

@@ -323,8 +323,19 @@ typedef enum {
     UPIR_HINT_VEC       = 4, /* iterations per worker the planner aims for (1, 4, 8, 16, 32) */
     UPIR_HINT_STAGES    = 5, /* shared-memory pipeline depth (tiled JACOBI5: 1..4; FILTER7: 2, 3) */
     UPIR_HINT_GRAINSIZE = 6, /* taskloop grainsize (>= 1; schedule TASKLOOP only)             */
-    UPIR_HINT_NUM_TASKS = 7  /* taskloop num_tasks (>= 1; schedule TASKLOOP only)             */
+    UPIR_HINT_NUM_TASKS = 7, /* taskloop num_tasks (>= 1; schedule TASKLOOP only)             */
+    UPIR_HINT_TILE_ORDER = 8 /* tiled JACOBI5: 0 = planner's choice (below), 1 = ascending     */
 } upir_hint_key;
+
+/* UPIR_HINT_TILE_ORDER: under a blocked static schedule (chunk 0) each team
+ * owns a contiguous run of tiles; the order it walks them in is not part of
+ * the schedule (the sweep's iterations are independent and its max/min
+ * residual is exact in any order), so the result is the same bit for bit
+ * either way.  With 0 (the default) a tiled JACOBI5 loop whose input is the
+ * output of the loop just before it in the region (a tiled JACOBI5 loop that
+ * walked its tiles ascending) walks its own tiles descending: the sweep then
+ * starts on the rows the previous sweep wrote last, which are still in L2.
+ * 1 keeps every team ascending.  Other bodies ignore the hint. */
 
 /* The canonical loop with its worksharing parallelization (§3.2).
  * Iterations: iv = lb, lb+step, ... while iv < ub (step > 0) or iv > ub

@@ -30,7 +30,7 @@ UPIR_F32, UPIR_I64 = 0, 1
  UPIR_BODY_JACOBI5_TB, UPIR_BODY_FILTER7) = range(11)
 UPIR_TERM_Y, UPIR_TERM_XY, UPIR_TERM_IMOD, UPIR_TERM_IV, UPIR_TERM_RESID = range(5)
 (UPIR_HINT_VARIANT, UPIR_HINT_TILE_M, UPIR_HINT_TILE_N, UPIR_HINT_VEC, UPIR_HINT_STAGES, UPIR_HINT_GRAINSIZE,
- UPIR_HINT_NUM_TASKS) = range(1, 8)
+ UPIR_HINT_NUM_TASKS, UPIR_HINT_TILE_ORDER) = range(1, 9)
 UPIR_SYNC_BARRIER, UPIR_SYNC_TASKWAIT = 0, 1
 UPIR_SUBMIT_GRAPH = 1
 UPIR_BATCH_LAUNCHES, UPIR_BATCH_GRAPH, UPIR_BATCH_PERSISTENT = 0, 1, 2

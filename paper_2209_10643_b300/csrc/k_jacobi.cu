@@ -11,6 +11,12 @@
 // team; max/min are exact in any order, so the result does not depend on
 // which team finishes first.
 //
+// Under a blocked static schedule a sweep over the previous sweep's output
+// walks each team's run of tiles descending (the planner sets `reverse` on
+// every other sweep of such a chain): the tiles the previous sweep wrote
+// last, still in L2, are read first.  The order is not observable in the
+// result.
+//
 // Grids whose width is not a multiple of 4 have rows that do not start on a
 // 16-byte boundary, which a 2D tensor map cannot describe (its row pitch must
 // be a multiple of 16 bytes).  jacobi_rows_kernel views such a grid as one
@@ -27,6 +33,14 @@
 namespace upir {
 
 namespace {
+
+// Under a blocked static schedule the team owns tiles [f, f + n); walking
+// them descending maps the ascending sequence's tile t to 2 f + n - 1 - t.
+__device__ __forceinline__ int64_t tile_reverse_sum(const JacobiParams& p) {
+    const int64_t w = blockIdx.x;
+    const int64_t f = w * p.sk.base + min(w, p.sk.extra);
+    return 2 * f + p.sk.base + (w < p.sk.extra ? 1 : 0) - 1;
+}
 
 template <int S, int ROP>
 __global__ void __launch_bounds__(1024) jacobi_tma_kernel(const JacobiParams p,
@@ -48,9 +62,11 @@ __global__ void __launch_bounds__(1024) jacobi_tma_kernel(const JacobiParams p,
     float racc = ROP == UPIR_RED_MIN ? __int_as_float(0x7f800000) : -__int_as_float(0x7f800000);
 
     TileIter it = tile_iter_begin(p);
+    const int64_t rev_sum = tile_reverse_sum(p);
     // producer side (one thread): next tile -> (row, column), then its copy
     auto issue_next = [&](int s) {
-        const int64_t t = tile_iter_next(it, p);
+        int64_t t = tile_iter_next(it, p);
+        if (t >= 0 && p.reverse) t = rev_sum - t;
         if (t < 0) {
             stage_rc[s] = make_int2(-1, -1);
             return;
@@ -188,9 +204,11 @@ __global__ void __launch_bounds__(1024) jacobi_rows_kernel(const JacobiParams p,
     float racc = ROP == UPIR_RED_MIN ? __int_as_float(0x7f800000) : -__int_as_float(0x7f800000);
 
     TileIter it = tile_iter_begin(p);
+    const int64_t rev_sum = tile_reverse_sum(p);
     // thread 0: the team's next tile into stage s, arming the stage's barrier
     auto take_next = [&](int s) {
-        const int64_t t = tile_iter_next(it, p);
+        int64_t t = tile_iter_next(it, p);
+        if (t >= 0 && p.reverse) t = rev_sum - t;
         if (t < 0) {
             stage_rc[s] = make_int2(-1, -1);
             return;

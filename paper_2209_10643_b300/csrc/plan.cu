@@ -247,6 +247,7 @@ upir_status plan_loop(upir_region r, const upir_loop_desc* d, LoopRec& lp) {
         else if (k == UPIR_HINT_STAGES) ok(v >= 1 && v <= 4, UPIR_EINVAL, "stages hint must be in [1, 4]"), lp.stages = (int)v;
         else if (k == UPIR_HINT_GRAINSIZE) ok(v >= 1, UPIR_EINVAL, "grainsize hint must be >= 1"), lp.grainsize = v;
         else if (k == UPIR_HINT_NUM_TASKS) ok(v >= 1, UPIR_EINVAL, "num_tasks hint must be >= 1"), lp.num_tasks = v;
+        else if (k == UPIR_HINT_TILE_ORDER) ok(v == 0 || v == 1, UPIR_EINVAL, "tile order hint must be 0 or 1"), lp.tile_order = (int)v;
         else ok(false, UPIR_EINVAL, "unknown hint key");
     }
     if (ok.st) return ok.st;
@@ -408,14 +409,6 @@ upir_status plan_loop(upir_region r, const upir_loop_desc* d, LoopRec& lp) {
                 JacobiParams& jp = lp.jp;
                 memset(&jp, 0, sizeof(jp));
                 jp.rows_tma = rows_tma ? 1 : 0;
-                // teams of 512 units on 64 x 128 tiles: four rows per thread
-                // and 1024 threads per SM (4096^2 grid, 100 sweeps: 2.139 ms;
-                // 256 units 2.157 ms, 1024 units 2.616 ms).  Row copies: two
-                // stages, teams of 256 units on 32 x 128 tiles, four teams
-                // per SM (4095^2 grid: 25.9 us per sweep; 512 units on
-                // 64-row tiles 26.7 us; three stages 28.1 us)
-                if (!U0 && !auto_units) lp.units = rows_tma ? 256 : 512;
-                lp.tile_m = lp.tile_m ? lp.tile_m : (rows_tma ? 32 : 64);
                 // 2D boxes on a grid whose two buffers outgrow the L2 by more
                 // than a quarter stream every sweep from HBM; there 64-column
                 // tiles run faster (5120^2 .. 16384^2: 0.86-0.94 of HBM
@@ -423,6 +416,16 @@ upir_status plan_loop(upir_region r, const upir_loop_desc* d, LoopRec& lp) {
                 // part of the pair stays in L2, 128 columns are faster (21.4
                 // against 24.5 us per sweep)
                 const bool beyond_l2 = !rows_tma && 2.0 * 4.0 * (double)R * (double)C > 1.25 * kL2Bytes;
+                // 2D boxes: 64 x 128 tiles, three stages, two teams per SM;
+                // teams of 256 units (eight rows per thread) while the grids
+                // fit the L2 (4096^2 grid, 100 sweeps with alternating tile
+                // order: 20.48 us per sweep; 512 units 20.74 us, 384 units
+                // 20.43 us), 512 beyond it.  Row copies: two stages, teams of
+                // 256 units on 40 x 128 tiles (4095^2 grid: 24.7 us per
+                // sweep; 32 rows 25.0 us, 64 rows and 512 units 25.7 us,
+                // three stages 27.9 us)
+                if (!U0 && !auto_units) lp.units = (rows_tma || !beyond_l2) ? 256 : 512;
+                lp.tile_m = lp.tile_m ? lp.tile_m : (rows_tma ? 40 : 64);
                 lp.tile_n = lp.tile_n ? lp.tile_n : (beyond_l2 ? 64 : 128);
                 lp.tile_n = (int)std::min<int64_t>(lp.tile_n, 4 * (int64_t)lp.units);
                 jp.stages = lp.stages ? lp.stages : (rows_tma ? 2 : 3);
@@ -471,6 +474,18 @@ upir_status plan_loop(upir_region r, const upir_loop_desc* d, LoopRec& lp) {
                     lp.teams = (int)std::max<int64_t>(1, std::min<int64_t>(dyn_estimate(lp, jp.ntiles), slots));
                 }
                 jp.sk = make_sched_const(jp.ntiles, lp.chunk, lp.teams);
+                // a sweep over the previous sweep's output walks its tiles the
+                // other way, so that it starts where that sweep ended, when a
+                // good part of that sweep's data can still be in L2 (the two
+                // grids within three L2s; 4096^2: 20.9 against 21.5 us per
+                // sweep, 4095^2: 24.9 against 25.9 us, 6144^2: 52.7 against
+                // 53.6 us; 8192^2: 92.0 against 91.5 us, so not there)
+                const bool l2_reuse = 2.0 * 4.0 * (double)R * (double)C <= 3.0 * kL2Bytes;
+                if (lp.tile_order == 0 && l2_reuse && lp.sched == UPIR_SCHED_STATIC && lp.chunk == 0 &&
+                    !r->loops.empty()) {
+                    const LoopRec& prev = *r->loops.back();
+                    jp.reverse = prev.kind == LK_JACOBI_TMA && prev.jp.uout == uin && !prev.jp.reverse ? 1 : 0;
+                }
                 if (is_dyn(lp.sched)) {
                     build_chunk_table(lp, jp.ntiles, lp.teams);
                     upir_status st = alloc_scratch(ctx, lp, 0, 0, &jp.sc);

@@ -42,6 +42,7 @@ struct LoopRec {
     std::vector<double> scalars;
     std::vector<upir_reduction> reds;
     int variant = 0, tile_m = 0, tile_n = 0, vec = 0, stages = 0;  // 0: planner default
+    int tile_order = 0;  // UPIR_HINT_TILE_ORDER
     bool gemm_tma = false;  // GEMM_F32: the TMA-fed kernel (maps in tmap[0], tmap[1])
     int64_t grainsize = 0, num_tasks = 0;  // taskloop hints
     // guided / taskloop chunk starts (host copy; the device copy is in scratch)

@@ -166,3 +166,37 @@ def test_beyond_l2_tiles_on_ragged_grid(s):
     um, rm = O.jacobi_run(u0, 3, mirror_f32=True)
     assert np.array_equal(u.view(np.uint32), um.view(np.uint32))
     assert np.array_equal(res.view(np.uint32), rm.view(np.uint32))
+
+
+ASC = (U.UPIR_HINT_TILE_ORDER, 1)  # every team walks its tiles ascending
+
+
+@pytest.mark.parametrize("rows,cols,sweeps,teams,units", [
+    (131, 260, 5, 0, 0), (131, 259, 5, 0, 0),          # 2D boxes / row copies, ragged tiles
+    (300, 516, 4, 7, 256),                              # explicit teams: uneven runs of tiles
+    (150, 333, 3, 500, 256),                            # more teams than tiles: empty runs
+    (1030, 1030, 6, 0, 0), (1027, 1029, 6, 0, 0),
+])
+def test_alternating_tile_order_bit_exact(s, rows, cols, sweeps, teams, units):
+    """The planner's default walks every other sweep's tiles descending; the
+    field and residuals equal the ascending walk's and the FP32 mirror's bit
+    for bit."""
+    u0 = I.jacobi_grid(rows, cols, seed=12)
+    u, res = run_sweeps(s, u0, sweeps, teams=teams, units=units)
+    ua, ra = run_sweeps(s, u0, sweeps, teams=teams, units=units, hints=(ASC,))
+    um, rm = O.jacobi_run(u0, sweeps, mirror_f32=True)
+    for got, want in ((u, um), (ua, um), (res, rm), (ra, rm)):
+        assert np.array_equal(got.view(np.uint32), want.view(np.uint32))
+
+
+def test_tile_order_hint_values(s):
+    a = np.zeros((40, 64), np.float32)
+    ha, hb = s.map(a, U.UPIR_MAP_TO), s.map(a.copy(), U.UPIR_MAP_TOFROM)
+    r = U.upir_spmd_region(s.ctx, 0, 0)
+    with pytest.raises(U.UpirError) as e:
+        U.upir_loop_checked(s.ctx, r, U.make_loop_desc(**jacobi_loop(ha, hb, 40, 64,
+                                                                  hints=[(U.UPIR_HINT_TILE_ORDER, 2)])))
+    assert e.value.status == U.UPIR_EINVAL
+    U.upir_region_destroy(r)
+    s.unmap(ha)
+    s.unmap(hb)
