@@ -11,6 +11,11 @@
 // team; max/min are exact in any order, so the result does not depend on
 // which team finishes first.
 //
+// While the two grids fit the L2 (KEEP), the 2D-box kernel reads its input
+// with an evict-first L2 policy and stores its output with normal priority
+// (otherwise streaming stores): the L2 then keeps the output, which the next
+// sweep reads, rather than the input, which the next sweep overwrites.
+//
 // Under a blocked static schedule a sweep over the previous sweep's output
 // walks each team's run of tiles descending (the planner sets `reverse` on
 // every other sweep of such a chain): the tiles the previous sweep wrote
@@ -42,7 +47,7 @@ __device__ __forceinline__ int64_t tile_reverse_sum(const JacobiParams& p) {
     return 2 * f + p.sk.base + (w < p.sk.extra ? 1 : 0) - 1;
 }
 
-template <int S, int ROP>
+template <int S, int ROP, bool KEEP>
 __global__ void __launch_bounds__(1024) jacobi_tma_kernel(const JacobiParams p,
                                                          const __grid_constant__ CUtensorMap tmap) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -63,6 +68,7 @@ __global__ void __launch_bounds__(1024) jacobi_tma_kernel(const JacobiParams p,
 
     TileIter it = tile_iter_begin(p);
     const int64_t rev_sum = tile_reverse_sum(p);
+    const uint64_t in_policy = KEEP ? l2_evict_first_policy() : 0;
     // producer side (one thread): next tile -> (row, column), then its copy
     auto issue_next = [&](int s) {
         int64_t t = tile_iter_next(it, p);
@@ -75,7 +81,8 @@ __global__ void __launch_bounds__(1024) jacobi_tma_kernel(const JacobiParams p,
         const int r0 = (int)p.r_lb + tr * TM, c0 = tc * TN;
         stage_rc[s] = make_int2(r0, c0);
         mbar_arrive_expect_tx(&bar[s], box_bytes);
-        tma_load_2d(ring + s * stage_floats, &tmap, &bar[s], c0 - 4, r0 - 1);
+        if (KEEP) tma_load_2d_hint(ring + s * stage_floats, &tmap, &bar[s], c0 - 4, r0 - 1, in_policy);
+        else tma_load_2d(ring + s * stage_floats, &tmap, &bar[s], c0 - 4, r0 - 1);
     };
 
     if (threadIdx.x == 0) {
@@ -126,7 +133,8 @@ __global__ void __launch_bounds__(1024) jacobi_tma_kernel(const JacobiParams p,
                 v.z = __fmul_rn(0.25f, __fadd_rn(__fadd_rn(N.z, Sv.z), __fadd_rn(C.y, C.w)));
                 v.w = __fmul_rn(0.25f, __fadd_rn(__fadd_rn(N.w, Sv.w), __fadd_rn(C.z, Er)));
                 if (full) {
-                    __stcs(reinterpret_cast<float4*>(out), v);
+                    if (KEEP) *reinterpret_cast<float4*>(out) = v;
+                    else __stcs(reinterpret_cast<float4*>(out), v);
                     if (ROP) {
                         racc = fold(racc, fabsf(__fsub_rn(v.x, C.x)), ROP);
                         racc = fold(racc, fabsf(__fsub_rn(v.y, C.y)), ROP);
@@ -339,31 +347,38 @@ __global__ void __launch_bounds__(1024) jacobi_rows_kernel(const JacobiParams p,
 using JacobiKernel = void (*)(const JacobiParams, const CUtensorMap);
 
 template <int S, bool ROWS, int TNC = 0>
-JacobiKernel pick_rop(int rop) {
+JacobiKernel pick_rop(int rop, bool keep) {
     if (ROWS) {
         if (rop == UPIR_RED_MAX) return jacobi_rows_kernel<S, UPIR_RED_MAX, TNC>;
         if (rop == UPIR_RED_MIN) return jacobi_rows_kernel<S, UPIR_RED_MIN, TNC>;
         return jacobi_rows_kernel<S, 0, TNC>;
     }
-    if (rop == UPIR_RED_MAX) return jacobi_tma_kernel<S, UPIR_RED_MAX>;
-    if (rop == UPIR_RED_MIN) return jacobi_tma_kernel<S, UPIR_RED_MIN>;
-    return jacobi_tma_kernel<S, 0>;
+    if (keep) {
+        if (rop == UPIR_RED_MAX) return jacobi_tma_kernel<S, UPIR_RED_MAX, true>;
+        if (rop == UPIR_RED_MIN) return jacobi_tma_kernel<S, UPIR_RED_MIN, true>;
+        return jacobi_tma_kernel<S, 0, true>;
+    }
+    if (rop == UPIR_RED_MAX) return jacobi_tma_kernel<S, UPIR_RED_MAX, false>;
+    if (rop == UPIR_RED_MIN) return jacobi_tma_kernel<S, UPIR_RED_MIN, false>;
+    return jacobi_tma_kernel<S, 0, false>;
 }
 
 template <bool ROWS, int TNC = 0>
-JacobiKernel pick_stages(int stages, int rop) {
+JacobiKernel pick_stages(int stages, int rop, bool keep) {
     switch (stages) {
-        case 1: return pick_rop<1, ROWS, TNC>(rop);
-        case 2: return pick_rop<2, ROWS, TNC>(rop);
-        case 3: return pick_rop<3, ROWS, TNC>(rop);
-        default: return pick_rop<4, ROWS, TNC>(rop);
+        case 1: return pick_rop<1, ROWS, TNC>(rop, keep);
+        case 2: return pick_rop<2, ROWS, TNC>(rop, keep);
+        case 3: return pick_rop<3, ROWS, TNC>(rop, keep);
+        default: return pick_rop<4, ROWS, TNC>(rop, keep);
     }
 }
 
 // the row-copy kernel has a fixed-width instantiation for 128-column tiles
-JacobiKernel pick_kernel(int stages, int rop, bool rows, int tile_n) {
-    if (!rows) return pick_stages<false>(stages, rop);
-    return tile_n == 128 ? pick_stages<true, 128>(stages, rop) : pick_stages<true>(stages, rop);
+// keep: the 2D-box kernel reading its input evict-first and storing with
+// normal priority (the row-copy kernel ignores it)
+JacobiKernel pick_kernel(int stages, int rop, bool rows, int tile_n, bool keep) {
+    if (!rows) return pick_stages<false>(stages, rop, keep);
+    return tile_n == 128 ? pick_stages<true, 128>(stages, rop, false) : pick_stages<true>(stages, rop, false);
 }
 
 bool configure_jacobi(JacobiKernel k) {
@@ -390,7 +405,7 @@ size_t jacobi_tma_smem_bytes(int tile_m, int tile_n, int stages, bool rows) {
 }
 
 int jacobi_tma_max_teams_per_sm(int units, int tile_m, int tile_n, int stages, bool rows) {
-    JacobiKernel k = pick_kernel(stages, UPIR_RED_MAX, rows, tile_n);
+    JacobiKernel k = pick_kernel(stages, UPIR_RED_MAX, rows, tile_n, false);
     if (!configure_jacobi(k)) return 0;
     int n = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, units,
@@ -403,7 +418,7 @@ int jacobi_tma_max_teams_per_sm(int units, int tile_m, int tile_n, int stages, b
 
 cudaError_t launch_jacobi_tma(int teams, int units, const JacobiParams& p, const void* tmap,
                               cudaStream_t s) {
-    JacobiKernel k = pick_kernel(p.stages, p.rvar ? p.rop : 0, p.rows_tma != 0, p.tile_n);
+    JacobiKernel k = pick_kernel(p.stages, p.rvar ? p.rop : 0, p.rows_tma != 0, p.tile_n, p.keep_l2 != 0);
     if (!configure_jacobi(k)) return cudaGetLastError();
     CUtensorMap m;
     memcpy(&m, tmap, sizeof(m));

@@ -93,6 +93,7 @@ struct JacobiParams {
     int stages;   // shared-memory pipeline depth
     int rows_tma; // one copy per halo row from a 1D view of the grid (width not a multiple of 4)
     int reverse;  // blocked static schedule: the team walks its run of tiles descending
+    int keep_l2;  // 2D boxes: inputs read evict-first, outputs stored with normal priority
     long long spin_limit;
     int* err_word;
     SchedConst sk;
