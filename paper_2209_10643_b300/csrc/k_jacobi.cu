@@ -404,8 +404,8 @@ size_t jacobi_tma_smem_bytes(int tile_m, int tile_n, int stages, bool rows) {
     return stage_floats * sizeof(float) * stages + 1024;
 }
 
-int jacobi_tma_max_teams_per_sm(int units, int tile_m, int tile_n, int stages, bool rows) {
-    JacobiKernel k = pick_kernel(stages, UPIR_RED_MAX, rows, tile_n, false);
+int jacobi_tma_max_teams_per_sm(int units, int tile_m, int tile_n, int stages, bool rows, bool keep) {
+    JacobiKernel k = pick_kernel(stages, UPIR_RED_MAX, rows, tile_n, keep);
     if (!configure_jacobi(k)) return 0;
     int n = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, units,

@@ -469,7 +469,8 @@ upir_status plan_loop(upir_region r, const upir_loop_desc* d, LoopRec& lp) {
                 // persistent teams: as many as are resident at once, balanced so
                 // every team gets the same number of tiles (to within one)
                 const int per_sm =
-                    std::max(1, jacobi_tma_max_teams_per_sm(lp.units, lp.tile_m, lp.tile_n, jp.stages, rows_tma));
+                    std::max(1, jacobi_tma_max_teams_per_sm(lp.units, lp.tile_m, lp.tile_n, jp.stages, rows_tma,
+                                                              jp.keep_l2 != 0));
                 const int64_t slots = (int64_t)kNumSMs * per_sm;
                 if (T0) lp.teams = T0;
                 else if (lp.sched == UPIR_SCHED_STATIC && lp.chunk == 0) {

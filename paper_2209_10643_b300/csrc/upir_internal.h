@@ -252,7 +252,7 @@ cudaError_t launch_jacobi_tb(int teams, int units, const JacobiTBParams& p, cons
 size_t filter7_smem_bytes(int tile_m, int tile_n, int stages);
 int filter7_max_teams_per_sm(int tile_m, int tile_n, int stages, int rs, int pair);
 cudaError_t launch_filter7(int teams, const Filter7Params& p, const void* tmap, cudaStream_t s);
-int jacobi_tma_max_teams_per_sm(int units, int tile_m, int tile_n, int stages, bool rows);
+int jacobi_tma_max_teams_per_sm(int units, int tile_m, int tile_n, int stages, bool rows, bool keep);
 cudaError_t launch_matvec(int teams, int units, const MatvecParams& p, cudaStream_t s);
 int matvec_max_teams_per_sm(int units);
 cudaError_t launch_gemm_f32(int teams, int units, const GemmParams& p, cudaStream_t s);
