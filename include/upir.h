@@ -324,7 +324,7 @@ typedef enum {
     UPIR_HINT_STAGES    = 5, /* shared-memory pipeline depth (tiled JACOBI5: 1..4; FILTER7: 2, 3) */
     UPIR_HINT_GRAINSIZE = 6, /* taskloop grainsize (>= 1; schedule TASKLOOP only)             */
     UPIR_HINT_NUM_TASKS = 7, /* taskloop num_tasks (>= 1; schedule TASKLOOP only)             */
-    UPIR_HINT_TILE_ORDER = 8 /* tiled JACOBI5: 0 = planner's choice (below), 1 = ascending     */
+    UPIR_HINT_TILE_ORDER = 8 /* tiled JACOBI5: 0 = planner's choice, 1 = ascending, 2 = descending */
 } upir_hint_key;
 
 /* UPIR_HINT_TILE_ORDER: under a blocked static schedule (chunk 0) each team
@@ -335,7 +335,10 @@ typedef enum {
  * output of the loop just before it in the region (a tiled JACOBI5 loop that
  * walked its tiles ascending) walks its own tiles descending: the sweep then
  * starts on the rows the previous sweep wrote last, which are still in L2.
- * 1 keeps every team ascending.  Other bodies ignore the hint. */
+ * 1 keeps every team ascending; 2 makes every team walk descending (for a
+ * caller that runs each sweep as a region of its own and alternates the
+ * order itself).  Schedules other than blocked static walk ascending; other
+ * bodies ignore the hint. */
 
 /* The canonical loop with its worksharing parallelization (§3.2).
  * Iterations: iv = lb, lb+step, ... while iv < ub (step > 0) or iv > ub

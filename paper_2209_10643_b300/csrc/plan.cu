@@ -247,7 +247,7 @@ upir_status plan_loop(upir_region r, const upir_loop_desc* d, LoopRec& lp) {
         else if (k == UPIR_HINT_STAGES) ok(v >= 1 && v <= 4, UPIR_EINVAL, "stages hint must be in [1, 4]"), lp.stages = (int)v;
         else if (k == UPIR_HINT_GRAINSIZE) ok(v >= 1, UPIR_EINVAL, "grainsize hint must be >= 1"), lp.grainsize = v;
         else if (k == UPIR_HINT_NUM_TASKS) ok(v >= 1, UPIR_EINVAL, "num_tasks hint must be >= 1"), lp.num_tasks = v;
-        else if (k == UPIR_HINT_TILE_ORDER) ok(v == 0 || v == 1, UPIR_EINVAL, "tile order hint must be 0 or 1"), lp.tile_order = (int)v;
+        else if (k == UPIR_HINT_TILE_ORDER) ok(v >= 0 && v <= 2, UPIR_EINVAL, "tile order hint must be 0, 1 or 2"), lp.tile_order = (int)v;
         else ok(false, UPIR_EINVAL, "unknown hint key");
     }
     if (ok.st) return ok.st;
@@ -487,11 +487,12 @@ upir_status plan_loop(upir_region r, const upir_loop_desc* d, LoopRec& lp) {
                 // sweep, 4095^2: 24.9 against 25.9 us, 6144^2: 52.7 against
                 // 53.6 us; 8192^2: 92.0 against 91.5 us, so not there)
                 const bool l2_reuse = 2.0 * 4.0 * (double)R * (double)C <= 3.0 * kL2Bytes;
-                if (lp.tile_order == 0 && l2_reuse && lp.sched == UPIR_SCHED_STATIC && lp.chunk == 0 &&
-                    !r->loops.empty()) {
+                const bool blocked = lp.sched == UPIR_SCHED_STATIC && lp.chunk == 0;
+                if (lp.tile_order == 0 && l2_reuse && blocked && !r->loops.empty()) {
                     const LoopRec& prev = *r->loops.back();
                     jp.reverse = prev.kind == LK_JACOBI_TMA && prev.jp.uout == uin && !prev.jp.reverse ? 1 : 0;
                 }
+                if (lp.tile_order == 2 && blocked) jp.reverse = 1;
                 if (is_dyn(lp.sched)) {
                     build_chunk_table(lp, jp.ntiles, lp.teams);
                     upir_status st = alloc_scratch(ctx, lp, 0, 0, &jp.sc);

@@ -359,16 +359,20 @@ class UpirJacobiSweeper:
         hb = U.upir_data_map_device(ctx, tb.data_ptr(), nb)
         hr = U.upir_data_map_device(ctx, tres.data_ptr(), 4 * sweeps)
         self.handles = [ha, hb, hr]
-        descs = []
-        for k in range(sweeps):
+        def desc(k, hints=()):
             src, dst = (ha, hb) if k % 2 == 0 else (hb, ha)
-            descs.append(U.make_loop_desc(
+            return U.make_loop_desc(
                 lb=1, ub=plan.local_rows - 1, collapse=2, body=U.UPIR_BODY_JACOBI5, bufs=[src, dst],
                 scalars=[plan.local_rows, plan.cols],
-                reductions=[(U.UPIR_RED_MAX, U.UPIR_F32, U.UPIR_TERM_RESID, hr, k)]))
-        for d in descs:
+                reductions=[(U.UPIR_RED_MAX, U.UPIR_F32, U.UPIR_TERM_RESID, hr, k)], hints=list(hints))
+
+        descs = [desc(k) for k in range(sweeps)]
+        # a region per sweep: odd sweeps walk their tiles descending, so that
+        # each starts where the previous one ended (what the planner does by
+        # itself for consecutive sweeps inside one region)
+        for k in range(sweeps):
             r = U.upir_spmd_region(ctx, 0, 0)
-            U.upir_loop_checked(ctx, r, d)
+            U.upir_loop_checked(ctx, r, desc(k, [(U.UPIR_HINT_TILE_ORDER, 2)] if k % 2 else []))
             self.regions.append(r)
         # every sweep in one region, for a rank with no neighbour (one rank)
         if plan.up is None and plan.down is None:

@@ -169,6 +169,7 @@ def test_beyond_l2_tiles_on_ragged_grid(s):
 
 
 ASC = (U.UPIR_HINT_TILE_ORDER, 1)  # every team walks its tiles ascending
+DESC = (U.UPIR_HINT_TILE_ORDER, 2)  # every team walks its tiles descending
 
 
 @pytest.mark.parametrize("rows,cols,sweeps,teams,units", [
@@ -179,13 +180,14 @@ ASC = (U.UPIR_HINT_TILE_ORDER, 1)  # every team walks its tiles ascending
 ])
 def test_alternating_tile_order_bit_exact(s, rows, cols, sweeps, teams, units):
     """The planner's default walks every other sweep's tiles descending; the
-    field and residuals equal the ascending walk's and the FP32 mirror's bit
-    for bit."""
+    field and residuals equal those of the ascending and descending walks and
+    the FP32 mirror's bit for bit."""
     u0 = I.jacobi_grid(rows, cols, seed=12)
     u, res = run_sweeps(s, u0, sweeps, teams=teams, units=units)
     ua, ra = run_sweeps(s, u0, sweeps, teams=teams, units=units, hints=(ASC,))
+    ud, rd = run_sweeps(s, u0, sweeps, teams=teams, units=units, hints=(DESC,))
     um, rm = O.jacobi_run(u0, sweeps, mirror_f32=True)
-    for got, want in ((u, um), (ua, um), (res, rm), (ra, rm)):
+    for got, want in ((u, um), (ua, um), (ud, um), (res, rm), (ra, rm), (rd, rm)):
         assert np.array_equal(got.view(np.uint32), want.view(np.uint32))
 
 
@@ -195,7 +197,7 @@ def test_tile_order_hint_values(s):
     r = U.upir_spmd_region(s.ctx, 0, 0)
     with pytest.raises(U.UpirError) as e:
         U.upir_loop_checked(s.ctx, r, U.make_loop_desc(**jacobi_loop(ha, hb, 40, 64,
-                                                                  hints=[(U.UPIR_HINT_TILE_ORDER, 2)])))
+                                                                  hints=[(U.UPIR_HINT_TILE_ORDER, 3)])))
     assert e.value.status == U.UPIR_EINVAL
     U.upir_region_destroy(r)
     s.unmap(ha)
