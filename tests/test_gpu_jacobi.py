@@ -202,3 +202,15 @@ def test_tile_order_hint_values(s):
     U.upir_region_destroy(r)
     s.unmap(ha)
     s.unmap(hb)
+
+
+@pytest.mark.parametrize("n", [4500, 4600])
+def test_l2_policy_threshold_bit_exact(s, n):
+    """Grids on either side of the size up to which the 2D-box kernel keeps
+    its output in L2 (the two grids within 1.25 L2: 4500^2 is, 4600^2 is
+    not): three sweeps bit-exact against the FP32 mirror."""
+    u0 = I.jacobi_grid(n, seed=13)
+    u, res = run_sweeps(s, u0, 3)
+    um, rm = O.jacobi_run(u0, 3, mirror_f32=True)
+    assert np.array_equal(u.view(np.uint32), um.view(np.uint32))
+    assert np.array_equal(res.view(np.uint32), rm.view(np.uint32))
